@@ -1,0 +1,229 @@
+"""FP64 CPU oracle for the local-volatility Monte Carlo price and its
+pathwise adjoint -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use this package. The CUDA library never imports it and shares
+no code with it. The arithmetic lives in ``lv_oracle.c`` (plain C, binary64,
+libm); this module compiles it with gcc and marshals numpy arrays.
+
+Every function cites the passage of arXiv 2002.02481 it follows in
+``lv_oracle.c``. Readings where the paper is silent are listed there too.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lv_oracle.c")
+_HDR = os.path.join(_HERE, "lv_oracle.h")
+_LIB = os.path.join(_HERE, "_build", "liblv_oracle.so")
+
+NSCAL = 9
+SUM_V, SUM_V2, SUM_XBAR0, SUM_XBAR0_2, SUM_VTOT, SUM_VTOT_2, SUM_SN, KINK_COUNT, KINK_XBAR0 = range(9)
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+class _Surface(ctypes.Structure):
+    _fields_ = [("n_spot", ctypes.c_int32), ("n_time", ctypes.c_int32),
+                ("spot", ctypes.POINTER(ctypes.c_double)),
+                ("time", ctypes.POINTER(ctypes.c_double)),
+                ("sigma", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Option(ctypes.Structure):
+    _fields_ = [("S0", ctypes.c_double), ("r", ctypes.c_double), ("K", ctypes.c_double),
+                ("T", ctypes.c_double), ("n_steps", ctypes.c_int32), ("phi", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32)]
+
+
+class _Point(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("u", ctypes.c_double),
+                ("v", ctypes.c_double), ("w", ctypes.c_double * 4),
+                ("sigma", ctypes.c_double), ("dsigma_dS", ctypes.c_double)]
+
+
+def build(src: str = _SRC, out: str = _LIB, extra: tuple = ()) -> str:
+    """Compile the oracle (plain C11, no fast-math, no FMA contraction, so
+    x86-64 and aarch64 hosts evaluate the same expressions)."""
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+           "-pthread", "-I", _HERE, *extra, src, "-o", out + ".tmp", "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
+def _stale() -> bool:
+    if not os.path.exists(_LIB):
+        return True
+    t = os.path.getmtime(_LIB)
+    return t < os.path.getmtime(_SRC) or t < os.path.getmtime(_HDR)
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load (building first if needed) the oracle library, or a variant at
+    ``path`` (used by the planted-mistake tests)."""
+    global _lib
+    if path is not None:
+        return _declare(ctypes.CDLL(path))
+    with _lock:
+        if _lib is None:
+            if _stale():
+                build()
+            _lib = _declare(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
+    P = ctypes.POINTER
+    u32p, f64p = P(ctypes.c_uint32), P(ctypes.c_double)
+    lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    lib.orc_philox4x32_10.restype = None
+    lib.orc_uniform.argtypes = [ctypes.c_uint32]
+    lib.orc_uniform.restype = ctypes.c_double
+    lib.orc_normals.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, f64p]
+    lib.orc_normals.restype = None
+    lib.orc_sigma_eval.argtypes = [P(_Surface), ctypes.c_double, ctypes.c_double, P(_Point)]
+    lib.orc_sigma_eval.restype = None
+    lib.orc_run.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                            ctypes.c_double, ctypes.c_int32, f64p]
+    lib.orc_run.restype = ctypes.c_int
+    lib.orc_finalize.argtypes = [f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, f64p]
+    lib.orc_finalize.restype = ctypes.c_int
+    lib.orc_paths.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, f64p, f64p, f64p]
+    lib.orc_paths.restype = ctypes.c_int
+    lib.orc_bump.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                             ctypes.c_int32, f64p, f64p]
+    lib.orc_bump.restype = ctypes.c_int
+    return lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class _Args:
+    """Keeps the numpy buffers alive while C sees their pointers."""
+
+    def __init__(self, spot, time, sigma, S0, r, K, T, n_steps, seed, phi=1, stream_id=0):
+        self.spot, self.time = _f64(spot), _f64(time)
+        self.sigma = _f64(sigma).reshape(-1)
+        I, J = self.spot.shape[0], self.time.shape[0]
+        if self.sigma.shape[0] != I * J:
+            raise ValueError("sigma must hold n_spot * n_time values")
+        self.IJ = I * J
+        self.surf = _Surface(I, J, _ptr(self.spot), _ptr(self.time), _ptr(self.sigma))
+        self.opt = _Option(float(S0), float(r), float(K), float(T), int(n_steps), int(phi),
+                           int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id))
+
+
+def _check(st: int, what: str) -> None:
+    if st != 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def philox4x32_10(ctr, key, lib=None) -> np.ndarray:
+    lib = lib or load_library()
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def uniform(w: int, lib=None) -> float:
+    return float((lib or load_library()).orc_uniform(int(w) & 0xFFFFFFFF))
+
+
+def normals(seed: int, path: int, n_steps: int, stream_id: int = 0, lib=None) -> np.ndarray:
+    """Z_0 .. Z_{N-1} of one path."""
+    lib = lib or load_library()
+    z = np.zeros(n_steps, dtype=np.float64)
+    lib.orc_normals(int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id), int(path), int(n_steps), _ptr(z))
+    return z
+
+
+def sigma_eval(surface, S: float, t: float, lib=None) -> dict:
+    """Bilinear sigma, d sigma / d S, cell and node weights at (S, t)."""
+    lib = lib or load_library()
+    a = _Args(surface.spot, surface.time, surface.sigma, 1.0, 0.0, 1.0, 1.0, 1, 0)
+    p = _Point()
+    lib.orc_sigma_eval(ctypes.byref(a.surf), float(S), float(t), ctypes.byref(p))
+    return dict(i=p.i, j=p.j, u=p.u, v=p.v, w=list(p.w), sigma=p.sigma, dsigma_dS=p.dsigma_dS)
+
+
+def run_sums(surface, opt, path_begin: int = 0, path_end: Optional[int] = None,
+             greeks: bool = True, kink_tol: float = 0.0, n_threads: Optional[int] = None,
+             lib=None) -> np.ndarray:
+    """Raw sums over paths [path_begin, path_end): NSCAL scalars, vega[IJ],
+    kink_vega[IJ] (see lv_oracle.h for the layout)."""
+    lib = lib or load_library()
+    a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
+              opt.n_steps, opt.seed, opt.phi, opt.stream_id)
+    if path_end is None:
+        path_end = opt.n_paths
+    out = np.zeros(NSCAL + 2 * a.IJ, dtype=np.float64)
+    st = lib.orc_run(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(path_end),
+                     int(bool(greeks)), float(kink_tol), int(n_threads or default_threads()), _ptr(out))
+    _check(st, "run")
+    return out
+
+
+def finalize(sums: np.ndarray, n_paths: int, S0: float, IJ: int, lib=None) -> np.ndarray:
+    """[price, delta, stderr, vega_0 .. vega_{IJ-1}]."""
+    lib = lib or load_library()
+    s = _f64(sums)
+    res = np.zeros(3 + IJ, dtype=np.float64)
+    _check(lib.orc_finalize(_ptr(s), int(n_paths), float(S0), int(IJ), _ptr(res)), "finalize")
+    return res
+
+
+def price_greeks(surface, opt, n_threads: Optional[int] = None, lib=None) -> dict:
+    """Price, its standard error, delta and the vega grid [I, J]."""
+    s = run_sums(surface, opt, 0, opt.n_paths, True, 0.0, n_threads, lib)
+    IJ = surface.n_spot * surface.n_time
+    res = finalize(s, opt.n_paths, opt.S0, IJ, lib)
+    return dict(price=res[0], delta=res[1], stderr=res[2],
+                vega=res[3:].reshape(surface.n_spot, surface.n_time), sums=s)
+
+
+def paths(surface, opt, path_begin: int, m: int, lib=None):
+    """Per-path x_N, discounted payoff and d V / d x_0 for m paths."""
+    lib = lib or load_library()
+    a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
+              opt.n_steps, opt.seed, opt.phi, opt.stream_id)
+    xN, V, xb = (np.zeros(m) for _ in range(3))
+    _check(lib.orc_paths(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(m),
+                         _ptr(xN), _ptr(V), _ptr(xb)), "paths")
+    return xN, V, xb
+
+
+def bump(surface, opt, eps_sigma: float, eps_S0: float, n_paths: Optional[int] = None,
+         n_threads: Optional[int] = None, lib=None):
+    """Central bump-and-reprice with common random numbers (Sec. III):
+    (vega grid [I, J], delta)."""
+    lib = lib or load_library()
+    a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
+              opt.n_steps, opt.seed, opt.phi, opt.stream_id)
+    vega = np.zeros(a.IJ)
+    delta = ctypes.c_double(0.0)
+    _check(lib.orc_bump(ctypes.byref(a.surf), ctypes.byref(a.opt), int(n_paths or opt.n_paths),
+                        float(eps_sigma), float(eps_S0), int(n_threads or default_threads()),
+                        _ptr(vega), ctypes.byref(delta)), "bump")
+    return vega.reshape(surface.n_spot, surface.n_time), delta.value

@@ -1,0 +1,452 @@
+/*
+ * lv_oracle.c -- plain FP64 CPU oracle for the Dupire local-volatility Monte
+ * Carlo price and its pathwise adjoint (price, delta, one vega bucket per
+ * grid node).
+ *
+ * TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the benchmark's
+ * CPU-baseline leg call this file; the CUDA library never does, and it
+ * shares no code, header or table with it. It is written for a reader who
+ * checks it against the paper by eye: no blocking, no fusion, the whole
+ * trajectory of a path is stored and the reverse sweep walks it back.
+ *
+ * What it follows (sections of arXiv 2002.02481):
+ *   Sec. IV-A   dX/X = sigma(X, t) dW, discretised by an explicit Euler
+ *               scheme; sigma given on a grid {(x_i, t_j)} of I x J nodes and
+ *               interpolated between them.
+ *   Sec. IV-B   European call payoff; pseudo-random normals.
+ *   Sec. IV-C   price = mean over paths; sensitivities of that mean with
+ *               respect to every grid value by back-propagation (AAD).
+ *   Sec. IV-D   bilinear interpolation between the grid nodes.
+ *   Sec. III    central bump-and-reprice, p0 +/- eps/2, divided by eps.
+ *
+ * Readings where the paper is silent (each one is listed in the design
+ * notes of the repository):
+ *   - Euler on x = ln X with drift r - sigma^2/2 and discount e^{-rT}
+ *     (r = 0 is the paper's driftless SDE); sigma evaluated at the left
+ *     point t_n = n T / N of each step.
+ *   - Normals: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
+ *     (seed low 32 bits, seed high 32 bits), counter = (n / 4, path low 32
+ *     bits, (path bits 32..47) | stream_id << 16, 0). Each 32-bit word w
+ *     becomes u = ((w >> 9) + 1/2) 2^-23, which lies in (0, 1) and is exact
+ *     in binary32 and binary64. Box-Muller on word pairs (0,1) and (2,3):
+ *     Z_a = sqrt(-2 ln u_a) cos(2 pi u_b), Z_b = sqrt(-2 ln u_a) sin(2 pi u_b);
+ *     step n uses Z of word n mod 4.
+ *   - Bilinear in S (not ln S) and t. Cell i = the largest i <= I-2 with
+ *     s_i <= S (0 below the grid), u = (S - s_i)/(s_{i+1} - s_i) clamped to
+ *     [0, 1]; the same in time. Outside the grid sigma is flat and
+ *     d sigma/d S = 0. With one time node sigma does not depend on t.
+ *   - Payoff kink: the indicator 1{phi (S_N - K) > 0}, so a tie gives 0.
+ *   - Vega is d price / d sigma_ij per unit of sigma.
+ *
+ * Parity pins (tests/test_oracle_*.py): Philox against cuRAND's host
+ * generator; normal moments and a KS test; Black-Scholes price, delta and
+ * vega on a flat grid; the per-path vega-sum identity; the martingale
+ * property; pathwise put-call parity; adjoint against central differences of
+ * the forward estimator; adjoint against torch.autograd on an independent
+ * FP64 restatement of the forward.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "lv_oracle.h"
+
+/* ------------------------------------------------------------------ Philox */
+
+#define ORC_PI 3.14159265358979323846
+
+/* Philox4x32 round constants: the two multipliers and the two Weyl key
+ * increments (golden ratio and sqrt(3) - 1 in 32-bit fixed point) from the
+ * SC'11 paper. */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t prod0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c0;
+        uint64_t prod1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += ORC_PHILOX_W0;
+        k1 += ORC_PHILOX_W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double orc_uniform(uint32_t w)
+{
+    return ((double)(w >> 9) + 0.5) * ldexp(1.0, -23);
+}
+
+void orc_counter(uint32_t block, uint64_t path, uint32_t stream_id, uint32_t ctr[4])
+{
+    ctr[0] = block;
+    ctr[1] = (uint32_t)(path & 0xffffffffu);
+    ctr[2] = (uint32_t)((path >> 32) & 0xffffu) | (stream_id << 16);
+    ctr[3] = 0u;
+}
+
+void orc_normals4(uint64_t seed, uint32_t stream_id, uint64_t path, uint32_t block, double z[4])
+{
+    uint32_t ctr[4], key[2], w[4];
+    orc_counter(block, path, stream_id, ctr);
+    key[0] = (uint32_t)(seed & 0xffffffffu);
+    key[1] = (uint32_t)(seed >> 32);
+    orc_philox4x32_10(ctr, key, w);
+    for (int pair = 0; pair < 2; ++pair) {
+        double ua = orc_uniform(w[2 * pair]);
+        double ub = orc_uniform(w[2 * pair + 1]);
+        double radius = sqrt(-2.0 * log(ua));
+        double angle = 2.0 * ORC_PI * ub;
+        z[2 * pair] = radius * cos(angle);
+        z[2 * pair + 1] = radius * sin(angle);
+    }
+}
+
+void orc_normals(uint64_t seed, uint32_t stream_id, uint64_t path, int32_t n_steps, double* z)
+{
+    double blk[4];
+    for (int32_t n = 0; n < n_steps; ++n) {
+        if (n % 4 == 0) orc_normals4(seed, stream_id, path, (uint32_t)(n / 4), blk);
+        z[n] = blk[n % 4];
+    }
+}
+
+/* ------------------------------------------------------ bilinear surface */
+
+/* Largest c in [0, n-2] with nodes[c] <= x (0 when x < nodes[0]). */
+static int32_t orc_cell(const double* nodes, int32_t n, double x)
+{
+    int32_t lo = 0, hi = n - 2;
+    while (lo < hi) {
+        int32_t mid = (lo + hi + 1) / 2;
+        if (nodes[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+static double orc_clamp01(double a)
+{
+    return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+}
+
+void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p)
+{
+    const int32_t I = sf->n_spot, J = sf->n_time;
+    int32_t i = orc_cell(sf->spot, I, S);
+    double width = sf->spot[i + 1] - sf->spot[i];
+    double u_raw = (S - sf->spot[i]) / width;
+    double u = orc_clamp01(u_raw);
+    int inside = (u_raw >= 0.0 && u_raw <= 1.0);
+
+    int32_t j = 0;
+    double v = 0.0;
+    if (J > 1) {
+        j = orc_cell(sf->time, J, t);
+        v = orc_clamp01((t - sf->time[j]) / (sf->time[j + 1] - sf->time[j]));
+    }
+    /* sigma_ij lives at sig[i * J + j] */
+    double s00 = sf->sigma[i * J + j];
+    double s10 = sf->sigma[(i + 1) * J + j];
+    double s01 = (J > 1) ? sf->sigma[i * J + j + 1] : 0.0;
+    double s11 = (J > 1) ? sf->sigma[(i + 1) * J + j + 1] : 0.0;
+
+    p->i = i;
+    p->j = j;
+    p->u = u;
+    p->v = v;
+    p->w[0] = (1.0 - u) * (1.0 - v);   /* node (i,   j)   */
+    p->w[1] = u * (1.0 - v);           /* node (i+1, j)   */
+    p->w[2] = (1.0 - u) * v;           /* node (i,   j+1) */
+    p->w[3] = u * v;                   /* node (i+1, j+1) */
+    p->sigma = p->w[0] * s00 + p->w[1] * s10 + p->w[2] * s01 + p->w[3] * s11;
+    if (inside)
+        p->dsigma_dS = ((1.0 - v) * (s10 - s00) + v * (s11 - s01)) / width;
+    else
+        p->dsigma_dS = 0.0;
+}
+
+/* --------------------------------------------------------------- one path */
+
+typedef struct {
+    double* x;   /* [N + 1] log-spot trajectory */
+    double* z;   /* [N] normals */
+} orc_workspace;
+
+typedef struct {
+    double V;       /* discounted payoff */
+    double xbar0;   /* d V / d x_0 */
+    double SN;      /* terminal spot */
+    double vtot;    /* sum over buckets of this path's sigma adjoints */
+    int kink;       /* |S_N - K| within the kink band */
+} orc_path_result;
+
+/* Simulates one path, and when vega != NULL runs its reverse sweep and adds
+ * every sigma adjoint to vega[i * J + j] (and |.| to kink_vega for paths
+ * flagged near the payoff kink). */
+static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t path,
+                         orc_workspace* ws, int want_greeks, double kink_tol,
+                         double* vega, double* kink_vega, orc_path_result* res)
+{
+    const int32_t N = op->n_steps, J = sf->n_time;
+    const double dt = op->T / (double)N;
+    const double sqdt = sqrt(dt);
+    double* x = ws->x;
+    double* z = ws->z;
+    orc_point pt;
+
+    orc_normals(op->seed, op->stream_id, path, N, z);
+
+    /* forward: Euler on the log-spot (Sec. IV-A) */
+    x[0] = log(op->S0);
+    for (int32_t n = 0; n < N; ++n) {
+        double t = (double)n * dt;
+        orc_sigma_eval(sf, exp(x[n]), t, &pt);
+        x[n + 1] = x[n] + (op->r - 0.5 * pt.sigma * pt.sigma) * dt + pt.sigma * sqdt * z[n];
+    }
+
+    /* payoff (Sec. IV-B) */
+    const double disc = exp(-op->r * op->T);
+    const double SN = exp(x[N]);
+    const double itm = (double)op->phi * (SN - op->K);
+    res->V = disc * (itm > 0.0 ? itm : 0.0);
+    res->SN = SN;
+    res->kink = (kink_tol > 0.0) && (fabs(SN - op->K) <= kink_tol * SN);
+    res->xbar0 = 0.0;
+    res->vtot = 0.0;
+    if (!want_greeks) return;
+
+    /* reverse sweep over the stored trajectory (back-propagation, Sec. IV-C) */
+    double xbar = itm > 0.0 ? disc * (double)op->phi * SN : 0.0;
+    double vtot = 0.0;
+    for (int32_t n = N - 1; n >= 0; --n) {
+        double t = (double)n * dt;
+        double S = exp(x[n]);
+        orc_sigma_eval(sf, S, t, &pt);
+        double h = sqdt * z[n] - pt.sigma * dt;     /* d x_{n+1} / d sigma_n */
+        double sbar = xbar * h;                     /* adjoint of sigma_n */
+        int32_t nodes[4] = { pt.i * J + pt.j, (pt.i + 1) * J + pt.j,
+                             pt.i * J + pt.j + 1, (pt.i + 1) * J + pt.j + 1 };
+        int n_corners = (J > 1) ? 4 : 2;
+        for (int c = 0; c < n_corners; ++c) {
+            double contrib = sbar * pt.w[c];
+            vega[nodes[c]] += contrib;
+            if (res->kink) kink_vega[nodes[c]] += fabs(contrib);
+            vtot += contrib;
+        }
+        /* d x_{n+1} / d x_n = 1 + h * d sigma / d x, and d sigma/d x = S d sigma/d S */
+        xbar = xbar * (1.0 + h * S * pt.dsigma_dS);
+    }
+    res->xbar0 = xbar;
+    res->vtot = vtot;
+}
+
+/* ----------------------------------------------------------- path ranges */
+
+typedef struct {
+    const orc_surface* sf;
+    const orc_option* op;
+    int64_t begin, end;
+    int want_greeks;
+    double kink_tol;
+    double* out;     /* ORC_NSCAL + 2 I J */
+    int status;
+} orc_job;
+
+static void* orc_job_run(void* arg)
+{
+    orc_job* jb = (orc_job*)arg;
+    const int64_t IJ = (int64_t)jb->sf->n_spot * jb->sf->n_time;
+    double* out = jb->out;
+    double* vega = out + ORC_NSCAL;
+    double* kink_vega = vega + IJ;
+    orc_workspace ws;
+    ws.x = (double*)malloc(sizeof(double) * (size_t)(jb->op->n_steps + 1));
+    ws.z = (double*)malloc(sizeof(double) * (size_t)jb->op->n_steps);
+    if (!ws.x || !ws.z) {
+        free(ws.x); free(ws.z);
+        jb->status = ORC_ENOMEM;
+        return NULL;
+    }
+    for (int64_t p = jb->begin; p < jb->end; ++p) {
+        orc_path_result res;
+        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->want_greeks, jb->kink_tol,
+                     vega, kink_vega, &res);
+        out[ORC_SUM_V] += res.V;
+        out[ORC_SUM_V2] += res.V * res.V;
+        out[ORC_SUM_XBAR0] += res.xbar0;
+        out[ORC_SUM_XBAR0_2] += res.xbar0 * res.xbar0;
+        out[ORC_SUM_VTOT] += res.vtot;
+        out[ORC_SUM_VTOT_2] += res.vtot * res.vtot;
+        out[ORC_SUM_SN] += res.SN;
+        if (res.kink) {
+            out[ORC_KINK_COUNT] += 1.0;
+            out[ORC_KINK_XBAR0] += fabs(res.xbar0);
+        }
+    }
+    free(ws.x);
+    free(ws.z);
+    jb->status = ORC_OK;
+    return NULL;
+}
+
+static int orc_check(const orc_surface* sf, const orc_option* op)
+{
+    if (!sf || !op || !sf->spot || !sf->time || !sf->sigma) return ORC_EINVAL;
+    if (sf->n_spot < 2 || sf->n_time < 1 || op->n_steps < 1 || !(op->T > 0.0) || !(op->S0 > 0.0))
+        return ORC_EINVAL;
+    if (op->phi != 1 && op->phi != -1) return ORC_EINVAL;
+    return ORC_OK;
+}
+
+int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
+            int want_greeks, double kink_tol, int32_t n_threads, double* out)
+{
+    int st = orc_check(sf, op);
+    if (st != ORC_OK) return st;
+    if (path_begin < 0 || path_end < path_begin || !out) return ORC_EINVAL;
+    const int64_t IJ = (int64_t)sf->n_spot * sf->n_time;
+    const int64_t width = ORC_NSCAL + 2 * IJ;
+    memset(out, 0, sizeof(double) * (size_t)width);
+    int64_t P = path_end - path_begin;
+    if (P == 0) return ORC_OK;
+    if (n_threads < 1) n_threads = 1;
+    if ((int64_t)n_threads > P) n_threads = (int32_t)P;
+
+    orc_job* jobs = (orc_job*)calloc((size_t)n_threads, sizeof(orc_job));
+    double* parts = (double*)calloc((size_t)(n_threads * width), sizeof(double));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !parts || !th) {
+        free(jobs); free(parts); free(th);
+        return ORC_ENOMEM;
+    }
+    for (int32_t k = 0; k < n_threads; ++k) {
+        jobs[k].sf = sf;
+        jobs[k].op = op;
+        jobs[k].begin = path_begin + P * k / n_threads;
+        jobs[k].end = path_begin + P * (k + 1) / n_threads;
+        jobs[k].want_greeks = want_greeks;
+        jobs[k].kink_tol = kink_tol;
+        jobs[k].out = parts + (int64_t)k * width;
+        jobs[k].status = ORC_EINTERNAL;
+    }
+    int started = 0;
+    for (int32_t k = 1; k < n_threads; ++k) {
+        if (pthread_create(&th[k], NULL, orc_job_run, &jobs[k]) != 0) break;
+        started = k;
+    }
+    orc_job_run(&jobs[0]);
+    for (int32_t k = 1; k <= started; ++k) pthread_join(th[k], NULL);
+    for (int32_t k = started + 1; k < n_threads; ++k) orc_job_run(&jobs[k]);
+
+    st = ORC_OK;
+    for (int32_t k = 0; k < n_threads; ++k) {     /* fixed order: range 0 first */
+        if (jobs[k].status != ORC_OK) st = jobs[k].status;
+        for (int64_t e = 0; e < width; ++e) out[e] += jobs[k].out[e];
+    }
+    free(jobs); free(parts); free(th);
+    return st;
+}
+
+int orc_finalize(const double* sums, int64_t n_paths, double S0, int64_t IJ, double* res)
+{
+    if (n_paths < 1 || !sums || !res) return ORC_EINVAL;
+    const double P = (double)n_paths;
+    const double mean = sums[ORC_SUM_V] / P;
+    double var = 0.0;
+    if (n_paths > 1) var = (sums[ORC_SUM_V2] / P - mean * mean) * P / (P - 1.0);
+    res[0] = mean;                                   /* price */
+    res[1] = sums[ORC_SUM_XBAR0] / (P * S0);         /* delta = E[xbar_0] / S0 */
+    res[2] = var > 0.0 ? sqrt(var / P) : 0.0;        /* standard error of the price */
+    for (int64_t e = 0; e < IJ; ++e) res[3 + e] = sums[ORC_NSCAL + e] / P;
+    return ORC_OK;
+}
+
+int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
+              double* out_xN, double* out_V, double* out_xbar0)
+{
+    int st = orc_check(sf, op);
+    if (st != ORC_OK) return st;
+    const int64_t IJ = (int64_t)sf->n_spot * sf->n_time;
+    orc_workspace ws;
+    ws.x = (double*)malloc(sizeof(double) * (size_t)(op->n_steps + 1));
+    ws.z = (double*)malloc(sizeof(double) * (size_t)op->n_steps);
+    double* vega = (double*)calloc((size_t)(2 * IJ), sizeof(double));
+    if (!ws.x || !ws.z || !vega) {
+        free(ws.x); free(ws.z); free(vega);
+        return ORC_ENOMEM;
+    }
+    for (int64_t q = 0; q < m; ++q) {
+        orc_path_result res;
+        orc_one_path(sf, op, (uint64_t)(path_begin + q), &ws, 1, 0.0, vega, vega + IJ, &res);
+        if (out_xN) out_xN[q] = ws.x[op->n_steps];
+        if (out_V) out_V[q] = res.V;
+        if (out_xbar0) out_xbar0[q] = res.xbar0;
+    }
+    free(ws.x); free(ws.z); free(vega);
+    return ORC_OK;
+}
+
+/* --------------------------------------------------------- bump and reprice */
+
+static int orc_price_only(const orc_surface* sf, const orc_option* op, int64_t n_paths,
+                          int32_t n_threads, double* sum_V)
+{
+    const int64_t IJ = (int64_t)sf->n_spot * sf->n_time;
+    double* out = (double*)malloc(sizeof(double) * (size_t)(ORC_NSCAL + 2 * IJ));
+    if (!out) return ORC_ENOMEM;
+    int st = orc_run(sf, op, 0, n_paths, 0, 0.0, n_threads, out);
+    *sum_V = out[ORC_SUM_V];
+    free(out);
+    return st;
+}
+
+int orc_bump(const orc_surface* sf, const orc_option* op, int64_t n_paths, double eps_sigma,
+             double eps_S0, int32_t n_threads, double* out_vega, double* out_delta)
+{
+    int st = orc_check(sf, op);
+    if (st != ORC_OK) return st;
+    if (n_paths < 1 || !(eps_sigma > 0.0) || !(eps_S0 > 0.0)) return ORC_EINVAL;
+    const int64_t IJ = (int64_t)sf->n_spot * sf->n_time;
+    const double P = (double)n_paths;
+    double* bumped = (double*)malloc(sizeof(double) * (size_t)IJ);
+    if (!bumped) return ORC_ENOMEM;
+    memcpy(bumped, sf->sigma, sizeof(double) * (size_t)IJ);
+    orc_surface bs = *sf;
+    bs.sigma = bumped;
+
+    /* one central difference per grid value, same seed for both sides (CRN), Sec. III */
+    for (int64_t e = 0; e < IJ && st == ORC_OK; ++e) {
+        double up = 0.0, dn = 0.0;
+        bumped[e] = sf->sigma[e] + 0.5 * eps_sigma;
+        st = orc_price_only(&bs, op, n_paths, n_threads, &up);
+        bumped[e] = sf->sigma[e] - 0.5 * eps_sigma;
+        if (st == ORC_OK) st = orc_price_only(&bs, op, n_paths, n_threads, &dn);
+        bumped[e] = sf->sigma[e];
+        out_vega[e] = (up - dn) / (P * eps_sigma);
+    }
+    if (st == ORC_OK) {
+        orc_option o2 = *op;
+        double up = 0.0, dn = 0.0;
+        o2.S0 = op->S0 + 0.5 * eps_S0;
+        st = orc_price_only(sf, &o2, n_paths, n_threads, &up);
+        o2.S0 = op->S0 - 0.5 * eps_S0;
+        if (st == ORC_OK) st = orc_price_only(sf, &o2, n_paths, n_threads, &dn);
+        *out_delta = (up - dn) / (P * eps_S0);
+    }
+    free(bumped);
+    return st;
+}

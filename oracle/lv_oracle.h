@@ -1,0 +1,74 @@
+/*
+ * lv_oracle.h -- interface of the FP64 CPU oracle (test infrastructure
+ * only; see lv_oracle.c). Independent of the CUDA library's header.
+ */
+#ifndef LV_ORACLE_H
+#define LV_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EINTERNAL = 4 };
+
+/* Layout of the sums array filled by orc_run: ORC_NSCAL scalars, then
+ * vega[I*J] (sum of sigma adjoints per node, spot-major), then
+ * kink_vega[I*J] (sum of |contribution| of paths in the payoff-kink band). */
+enum {
+    ORC_SUM_V = 0,        /* sum of discounted payoffs */
+    ORC_SUM_V2 = 1,       /* sum of squared payoffs */
+    ORC_SUM_XBAR0 = 2,    /* sum of d V / d x_0 */
+    ORC_SUM_XBAR0_2 = 3,  /* sum of squares of the above */
+    ORC_SUM_VTOT = 4,     /* sum over paths of (sum over nodes of the path's vega) */
+    ORC_SUM_VTOT_2 = 5,   /* sum of squares of the above */
+    ORC_SUM_SN = 6,       /* sum of terminal spots */
+    ORC_KINK_COUNT = 7,   /* paths with |S_N - K| <= kink_tol * S_N */
+    ORC_KINK_XBAR0 = 8,   /* sum of |d V / d x_0| over those paths */
+    ORC_NSCAL = 9
+};
+
+typedef struct {
+    int32_t n_spot;       /* I >= 2 */
+    int32_t n_time;       /* J >= 1 */
+    const double* spot;   /* [I], strictly increasing */
+    const double* time;   /* [J], strictly increasing */
+    const double* sigma;  /* [I*J], sigma_ij at i*J + j */
+} orc_surface;
+
+typedef struct {
+    double S0, r, K, T;
+    int32_t n_steps;
+    int32_t phi;          /* +1 call, -1 put */
+    uint64_t seed;
+    uint32_t stream_id;
+} orc_option;
+
+typedef struct {
+    int32_t i, j;         /* cell */
+    double u, v;          /* clamped weights in spot and time */
+    double w[4];          /* node weights (i,j), (i+1,j), (i,j+1), (i+1,j+1) */
+    double sigma;
+    double dsigma_dS;
+} orc_point;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_uniform(uint32_t w);
+void orc_counter(uint32_t block, uint64_t path, uint32_t stream_id, uint32_t ctr[4]);
+void orc_normals4(uint64_t seed, uint32_t stream_id, uint64_t path, uint32_t block, double z[4]);
+void orc_normals(uint64_t seed, uint32_t stream_id, uint64_t path, int32_t n_steps, double* z);
+void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p);
+
+int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
+            int want_greeks, double kink_tol, int32_t n_threads, double* out);
+int orc_finalize(const double* sums, int64_t n_paths, double S0, int64_t IJ, double* res);
+int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
+              double* out_xN, double* out_V, double* out_xbar0);
+int orc_bump(const orc_surface* sf, const orc_option* op, int64_t n_paths, double eps_sigma,
+             double eps_S0, int32_t n_threads, double* out_vega, double* out_delta);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

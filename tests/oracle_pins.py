@@ -1,0 +1,304 @@
+"""Pins that tie the FP64 oracle to facts outside itself.
+
+Each pin takes an oracle library handle, so the same battery runs against
+the real oracle (tests/test_oracle_pins.py) and against copies with a
+planted mistake (tests/test_oracle_mutants.py), where at least one pin must
+fail. None of them retypes the oracle's own formulas: they compare with
+cuRAND's Philox, with distribution laws, with Black-Scholes closed forms,
+with identities that hold path by path, with central differences of the
+oracle's own forward estimator, and with torch.autograd on an independent
+restatement of the forward (tests/torch_lv.py).
+"""
+import math
+
+import numpy as np
+from scipy import stats
+from scipy.special import ndtr
+
+import oracle
+import workloads as W
+
+from . import _curand_host
+from . import torch_lv
+
+
+# ---------------------------------------------------------------- helpers
+
+def bs_call_put(S0, K, T, r, sigma, phi):
+    """Black-Scholes price, delta and vega (textbook closed forms)."""
+    sd = sigma * math.sqrt(T)
+    d1 = (math.log(S0 / K) + (r + 0.5 * sigma * sigma) * T) / sd
+    d2 = d1 - sd
+    disc = math.exp(-r * T)
+    if phi > 0:
+        price = S0 * ndtr(d1) - K * disc * ndtr(d2)
+        delta = ndtr(d1)
+    else:
+        price = K * disc * ndtr(-d2) - S0 * ndtr(-d1)
+        delta = ndtr(d1) - 1.0
+    vega = S0 * math.exp(-0.5 * d1 * d1) / math.sqrt(2 * math.pi) * math.sqrt(T)
+    return price, delta, vega
+
+
+def se_of(sum1, sum2, n):
+    mean = sum1 / n
+    var = max(sum2 / n - mean * mean, 0.0) * n / max(n - 1, 1)
+    return math.sqrt(var / n)
+
+
+# ------------------------------------------------------------------- RNG
+
+def pin_philox_curand(lib):
+    """Philox4x32-10 block function == cuRAND's host generator, over
+    counters with nonzero c0, c1 and c2 and several keys."""
+    cu = _curand_host.load()
+    if cu is None:
+        import pytest
+        pytest.skip("libcurand not available")
+    seeds = [0, 1, 0x123456789ABCDEF0, 0xFFFFFFFFFFFFFFFF]
+    offsets = [0, 4 * (5 * 65536 + 123), 4 * (1 << 48), 4 * (((1 << 32) + 7) * 65536 + 65530)]
+    for seed in seeds:
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for off in offsets:
+            words = _curand_host.generate(cu, seed, off, 4 * 12).reshape(-1, 4)
+            for t in range(words.shape[0]):
+                ctr = _curand_host.counter_of(off // 4 + t)
+                got = oracle.philox4x32_10(ctr, key, lib=lib)
+                assert np.array_equal(got, words[t]), (seed, off, t, got, words[t])
+
+
+def pin_normals_from_curand_words(lib):
+    """The oracle's normals for (seed, stream, path, step) are Box-Muller of
+    the uniforms of the Philox words at counter (step/4, path low, path high
+    | stream << 16, 0); words taken from cuRAND, transform by Python's math."""
+    cu = _curand_host.load()
+    if cu is None:
+        import pytest
+        pytest.skip("libcurand not available")
+    seed = 0x00000000DEADBEEF
+    # cuRAND tuple p sits at counter (p >> 16 over c0:c1, p & 0xffff, 0); with stream 0 and
+    # path < 2^14 the oracle's counter (blk, path, 0, 0) is tuple ((path << 32 | blk) << 16)
+    for path in (0, 3, 9000):
+        z = oracle.normals(seed, path, 12, lib=lib)
+        for blk in range(3):
+            p = ((path << 32) | blk) << 16
+            w = _curand_host.generate(cu, seed, 4 * p, 4)
+            u = [((int(x) >> 9) + 0.5) * 2.0 ** -23 for x in w]
+            expect = []
+            for a, b in ((u[0], u[1]), (u[2], u[3])):
+                rad = math.sqrt(-2.0 * math.log(a))
+                expect += [rad * math.cos(2 * math.pi * b), rad * math.sin(2 * math.pi * b)]
+            np.testing.assert_allclose(z[4 * blk:4 * blk + 4], expect, rtol=1e-13, atol=1e-13)
+
+
+def pin_uniform_exact(lib):
+    """Every uniform lies in (0, 1) and is exactly representable in binary32
+    (both precisions see the same value); the extremes are 2^-24, 1 - 2^-24."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    ws = list(rng.integers(0, 2 ** 32, size=2000, dtype=np.uint64)) + [0, 0xFFFFFFFF, 1 << 31]
+    for w in ws:
+        u = oracle.uniform(int(w), lib=lib)
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u
+    assert oracle.uniform(0, lib=lib) == 2.0 ** -24
+    assert oracle.uniform(0xFFFFFFFF, lib=lib) == 1.0 - 2.0 ** -24
+
+
+def pin_normal_law(lib):
+    """2^18 normals: moments within 4 SE of N(0, 1), KS test, radius^2 of
+    each Box-Muller pair ~ Exp(mean 2), no lag-1 correlation."""
+    n_paths, n_steps = 4096, 64
+    z = np.concatenate([oracle.normals(7, p, n_steps, lib=lib) for p in range(n_paths)])
+    n = z.size
+    assert abs(z.mean()) < 4 / math.sqrt(n)
+    assert abs(z.var() - 1) < 4 * math.sqrt(2 / n)
+    assert abs(stats.skew(z)) < 4 * math.sqrt(6 / n)
+    assert abs(stats.kurtosis(z)) < 4 * math.sqrt(24 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    pairs = z.reshape(-1, 2)
+    r2 = (pairs ** 2).sum(1)
+    assert stats.kstest(r2, "expon", args=(0, 2)).pvalue > 1e-4
+    assert abs(np.corrcoef(z[:-1], z[1:])[0, 1]) < 4 / math.sqrt(n)
+
+
+# ------------------------------------------------------------ flat surface
+
+def pin_black_scholes(lib):
+    """Flat sigma: log-Euler is exact in law, so price, delta and the sum of
+    all vega buckets match Black-Scholes within 3.5 standard errors."""
+    sig = 0.2
+    cases = [(1.0, 0.0, 1, 100.0), (3.0, 0.0, 1, 100.0), (5.0, 0.0, 1, 100.0),
+             (1.0, 0.03, -1, 110.0), (2.0, 0.03, 1, 90.0)]
+    surf = W.flat_surface(sig, n_spot=6, n_time=4, s_lo=30.0, s_hi=400.0, t_hi=5.0)
+    for T, r, phi, K in cases:
+        opt = W.Option(S0=100.0, r=r, K=K, T=T, n_steps=26, n_paths=1 << 15, seed=3, phi=phi)
+        s = oracle.run_sums(surf, opt, lib=lib)
+        P = opt.n_paths
+        price, delta, vega = bs_call_put(100.0, K, T, r, sig, phi)
+        got_p = s[oracle.SUM_V] / P
+        got_d = s[oracle.SUM_XBAR0] / (P * 100.0)
+        got_v = s[oracle.SUM_VTOT] / P
+        assert abs(got_p - price) < 3.5 * se_of(s[oracle.SUM_V], s[oracle.SUM_V2], P), (T, got_p, price)
+        se_d = se_of(s[oracle.SUM_XBAR0], s[oracle.SUM_XBAR0_2], P) / 100.0
+        assert abs(got_d - delta) < 3.5 * se_d, (T, got_d, delta)
+        se_v = se_of(s[oracle.SUM_VTOT], s[oracle.SUM_VTOT_2], P)
+        assert abs(got_v - vega) < 3.5 * se_v, (T, got_v, vega)
+        # the bucket array sums to the same total
+        vb = s[oracle.NSCAL:oracle.NSCAL + surf.n_spot * surf.n_time].sum() / P
+        assert abs(vb - got_v) <= 1e-10 * max(1.0, abs(got_v))
+
+
+def pin_flat_closed_form_paths(lib):
+    """Flat sigma, per path: x_N = ln S0 + (r - sigma^2/2) T + sigma sqrt(dt)
+    sum Z exactly, and the path's bucket total equals the flat pathwise vega
+    e^{-rT} 1{phi(S_N-K)>0} phi S_N (sqrt(dt) sum Z - sigma T) (partition of
+    unity of the bilinear weights)."""
+    sig, r, T, N, K = 0.25, 0.02, 2.0, 24, 100.0
+    surf = W.flat_surface(sig, n_spot=4, n_time=3, s_lo=50.0, s_hi=200.0, t_hi=2.0)
+    for phi in (1, -1):
+        opt = W.Option(S0=100.0, r=r, K=K, T=T, n_steps=N, n_paths=64, seed=9, phi=phi)
+        xN, V, xb = oracle.paths(surf, opt, 0, 64, lib=lib)
+        dt = T / N
+        for p in range(64):
+            zs = oracle.normals(9, p, N, lib=lib).sum()
+            x_exact = math.log(100.0) + (r - 0.5 * sig * sig) * T + sig * math.sqrt(dt) * zs
+            assert abs(xN[p] - x_exact) < 1e-12
+            SN = math.exp(x_exact)
+            itm = phi * (SN - K) > 0
+            s = oracle.run_sums(surf, opt, p, p + 1, lib=lib, n_threads=1)
+            vpath = math.exp(-r * T) * phi * SN * (math.sqrt(dt) * zs - sig * T) if itm else 0.0
+            assert abs(s[oracle.SUM_VTOT] - vpath) <= 1e-11 * max(1.0, abs(vpath)), (p, s[oracle.SUM_VTOT], vpath)
+            # flat grid: d x_N / d x_0 = 1, so xbar_0 = e^{-rT} phi S_N on in-the-money paths
+            assert abs(xb[p] - (math.exp(-r * T) * phi * SN if itm else 0.0)) < 1e-10
+
+
+# --------------------------------------------------------------- invariants
+
+def pin_martingale(lib):
+    """Any grid: E[e^{-rT} S_N] = S0 under log-Euler, so a call struck at 0
+    prices S0 with delta 1 and zero total vega, within 3.5 SE."""
+    surf, _ = W.config_small()
+    for r in (0.0, 0.04):
+        opt = W.Option(S0=100.0, r=r, K=0.0, T=1.0, n_steps=52, n_paths=1 << 15, seed=5)
+        s = oracle.run_sums(surf, opt, lib=lib)
+        P = opt.n_paths
+        assert abs(s[oracle.SUM_V] / P - 100.0) < 3.5 * se_of(s[oracle.SUM_V], s[oracle.SUM_V2], P)
+        se_d = se_of(s[oracle.SUM_XBAR0], s[oracle.SUM_XBAR0_2], P) / 100.0
+        assert abs(s[oracle.SUM_XBAR0] / (P * 100.0) - 1.0) < 3.5 * se_d
+        se_v = se_of(s[oracle.SUM_VTOT], s[oracle.SUM_VTOT_2], P)
+        assert abs(s[oracle.SUM_VTOT] / P) < 3.5 * se_v
+
+
+def pin_put_call_parity(lib):
+    """Path by path, call - put = e^{-rT}(S_N - K); with the same seeds the
+    price, delta and every bucket of (call - put) equal those of a call
+    struck at 0 minus K e^{-rT}, to rounding."""
+    surf, _ = W.config_small()
+    r, T, K = 0.03, 1.0, 104.0
+    base = dict(S0=100.0, r=r, T=T, n_steps=40, n_paths=4096, seed=21)
+    c = oracle.run_sums(surf, W.Option(K=K, phi=1, **base), lib=lib)
+    p = oracle.run_sums(surf, W.Option(K=K, phi=-1, **base), lib=lib)
+    f = oracle.run_sums(surf, W.Option(K=0.0, phi=1, **base), lib=lib)
+    P = base["n_paths"]
+    IJ = surf.n_spot * surf.n_time
+    assert abs((c[0] - p[0]) - (f[0] - P * K * math.exp(-r * T))) < 1e-9 * f[0]
+    assert abs((c[oracle.SUM_XBAR0] - p[oracle.SUM_XBAR0]) - f[oracle.SUM_XBAR0]) < 1e-9 * f[oracle.SUM_XBAR0]
+    vc, vp, vf = (a[oracle.NSCAL:oracle.NSCAL + IJ] for a in (c, p, f))
+    assert np.max(np.abs((vc - vp) - vf)) < 1e-9 * np.max(np.abs(vf))
+
+
+# ------------------------------------------------------------- the adjoint
+
+ADJOINT_CASES = [
+    # name, surface, S0, r, K, T, N, phi, P, seed
+    ("2x1 constant-in-time", W.random_surface(1, 2, 1, s_lo=80, s_hi=125), 100.0, 0.0, 100.0, 1.0, 6, 1, 24, 3),
+    ("3x2 leaves grid both sides", W.random_surface(2, 3, 2, s_lo=92, s_hi=108, t_hi=0.5), 100.0, 0.01, 99.0, 0.5, 8, 1, 32, 4),
+    ("uneven 5x4 put, K at node", None, 100.0, 0.02, None, 0.8, 10, -1, 32, 5),
+    ("4x3 T mid-cell", W.random_surface(4, 4, 3, s_lo=70, s_hi=140, t_hi=2.0), 100.0, 0.0, 95.0, 1.3, 9, 1, 32, 6),
+    ("small skew r>0", W.config_small()[0], 100.0, 0.05, 100.0, 1.0, 13, 1, 32, 7),
+]
+
+
+def _case(c):
+    name, surf, S0, r, K, T, N, phi, P, seed = c
+    if surf is None:
+        surf = W.random_surface(3, 5, 4, s_lo=75, s_hi=130, t_hi=1.0, uneven=True)
+        K = float(surf.spot[2])
+    return name, surf, W.Option(S0=S0, r=r, K=K, T=T, n_steps=N, n_paths=P, seed=seed, phi=phi)
+
+
+def pin_adjoint_vs_autograd(lib):
+    """The hand-written reverse sweep equals torch.autograd of an independent
+    FP64 restatement of the forward, on tiny grids covering a one-column
+    grid, paths leaving the grid on both sides, irregular nodes, a strike at
+    a node, a maturity inside a time cell, puts and a nonzero rate."""
+    for c in ADJOINT_CASES:
+        name, surf, opt = _case(c)
+        Z = np.stack([oracle.normals(opt.seed, p, opt.n_steps, lib=lib) for p in range(opt.n_paths)])
+        price, delta, vega, _ = torch_lv.autograd_greeks(
+            surf.spot, surf.time, surf.sigma, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.phi, Z)
+        res = oracle.finalize(oracle.run_sums(surf, opt, lib=lib), opt.n_paths, opt.S0,
+                              surf.n_spot * surf.n_time, lib=lib)
+        scale = max(1e-3, np.max(np.abs(vega)))
+        assert abs(res[0] - price) <= 1e-11 * max(1.0, abs(price)), name
+        assert abs(res[1] - delta) <= 1e-11 * max(1.0, abs(delta)), (name, res[1], delta)
+        np.testing.assert_allclose(res[3:].reshape(vega.shape), vega, rtol=0, atol=1e-11 * scale,
+                                   err_msg=name)
+
+
+def pin_adjoint_vs_bump(lib):
+    """Adjoint delta and buckets equal central bump-and-reprice (Sec. III)
+    with common random numbers and eps = 1e-6, to O(eps^2), on a small grid
+    where no path sits within the bump of a payoff or cell kink."""
+    surf = W.random_surface(8, 3, 2, s_lo=85, s_hi=118, t_hi=0.6)
+    opt = W.Option(S0=100.0, r=0.01, K=101.0, T=0.6, n_steps=4, n_paths=64, seed=12, phi=1)
+    xN, _, _ = oracle.paths(surf, opt, 0, opt.n_paths, lib=lib)
+    assert np.min(np.abs(np.exp(xN) - opt.K)) > 1e-3   # no path near the payoff kink
+    res = oracle.finalize(oracle.run_sums(surf, opt, lib=lib), opt.n_paths, opt.S0, 6, lib=lib)
+    vfd, dfd = oracle.bump(surf, opt, 1e-6, 1e-6 * opt.S0, lib=lib)
+    scale = np.max(np.abs(vfd))
+    np.testing.assert_allclose(res[3:].reshape(3, 2), vfd, rtol=0, atol=2e-6 * scale)
+    assert abs(res[1] - dfd) < 2e-6 * max(1.0, abs(dfd))
+
+
+def pin_bilinear(lib):
+    """Bilinear sigma: exact node values at nodes, flat outside the grid,
+    weights a partition of unity, d sigma/d S equal to a central difference
+    inside a cell and 0 outside, and the cell rule max{i : s_i <= S}."""
+    surf = W.random_surface(5, 4, 3, s_lo=80, s_hi=120, t_hi=1.0, uneven=True)
+    s, t, g = surf.spot, surf.time, surf.sigma
+    for i in range(4):
+        for j in range(3):
+            e = oracle.sigma_eval(surf, s[i], t[j], lib=lib)
+            assert abs(e["sigma"] - g[i, j]) < 1e-15
+            assert e["i"] == min(i, 2) and e["j"] == min(j, 1)
+    lo = oracle.sigma_eval(surf, 10.0, 0.5, lib=lib)
+    hi = oracle.sigma_eval(surf, 1000.0, 0.5, lib=lib)
+    assert lo["dsigma_dS"] == 0.0 and hi["dsigma_dS"] == 0.0
+    edge_lo = oracle.sigma_eval(surf, s[0], 0.5, lib=lib)
+    edge_hi = oracle.sigma_eval(surf, s[-1], 0.5, lib=lib)
+    assert abs(lo["sigma"] - edge_lo["sigma"]) < 1e-15 and abs(hi["sigma"] - edge_hi["sigma"]) < 1e-15
+    late = oracle.sigma_eval(surf, 100.0, 7.0, lib=lib)
+    last = oracle.sigma_eval(surf, 100.0, t[-1], lib=lib)
+    assert abs(late["sigma"] - last["sigma"]) < 1e-15
+    rng = np.random.Generator(np.random.PCG64(4))
+    for _ in range(50):
+        S = rng.uniform(s[0], s[-1])
+        tt = rng.uniform(0.0, t[-1])
+        e = oracle.sigma_eval(surf, S, tt, lib=lib)
+        assert abs(sum(e["w"]) - 1.0) < 1e-14
+        assert s[e["i"]] <= S < s[e["i"] + 1] or (e["i"] == 2 and S <= s[3])
+        h = 1e-6
+        if min(abs(S - x) for x in s) > 10 * h:
+            fd = (oracle.sigma_eval(surf, S + h, tt, lib=lib)["sigma"]
+                  - oracle.sigma_eval(surf, S - h, tt, lib=lib)["sigma"]) / (2 * h)
+            assert abs(fd - e["dsigma_dS"]) < 1e-7
+        # value from scipy's regular-grid linear interpolator
+        from scipy.interpolate import RegularGridInterpolator
+        ref = RegularGridInterpolator((s, t), g, method="linear")([[S, tt]])[0]
+        assert abs(ref - e["sigma"]) < 1e-13
+
+
+ALL_PINS = [pin_philox_curand, pin_normals_from_curand_words, pin_uniform_exact, pin_normal_law,
+            pin_black_scholes, pin_flat_closed_form_paths, pin_martingale, pin_put_call_parity,
+            pin_adjoint_vs_autograd, pin_adjoint_vs_bump, pin_bilinear]

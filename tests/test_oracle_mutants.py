@@ -1,0 +1,60 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case copies lv_oracle.c, plants one plausible mistake (a dropped term,
+a wrong sign, a wrong index, a swapped operand), compiles the copy on the
+CPU and runs the pin battery against it: at least one pin has to fail.
+This checks that the pins are strong enough to vouch for the oracle.
+"""
+import os
+
+import pytest
+
+import oracle
+
+from . import oracle_pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "lv_oracle.c")
+
+MUTANTS = {
+    "drift sign": ("(op->r - 0.5 * pt.sigma * pt.sigma) * dt",
+                   "(op->r + 0.5 * pt.sigma * pt.sigma) * dt"),
+    "dx/dsigma sign": ("double h = sqdt * z[n] - pt.sigma * dt;",
+                       "double h = sqdt * z[n] + pt.sigma * dt;"),
+    "dsigma/dx drops S": ("xbar * (1.0 + h * S * pt.dsigma_dS)",
+                          "xbar * (1.0 + h * pt.dsigma_dS)"),
+    "node weights transposed": ("p->w[1] = u * (1.0 - v);", "p->w[1] = (1.0 - u) * v;"),
+    "philox wrong product": ("uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;"),
+    "philox key schedule": ("k1 += ORC_PHILOX_W1;", "k1 += ORC_PHILOX_W0;"),
+    "box-muller cos/sin swapped": ("z[2 * pair] = radius * cos(angle);",
+                                   "z[2 * pair] = radius * sin(angle);"),
+    "uniform offset dropped": ("((double)(w >> 9) + 0.5)", "((double)(w >> 9) + 0.0)"),
+    "discount missing in adjoint": ("disc * (double)op->phi * SN : 0.0", "(double)op->phi * SN : 0.0"),
+    "time-neighbour index": ("double s01 = (J > 1) ? sf->sigma[i * J + j + 1] : 0.0;",
+                             "double s01 = (J > 1) ? sf->sigma[i * J + j] : 0.0;"),
+    "cell rule strict": ("if (nodes[mid] <= x) lo = mid;", "if (nodes[mid] < x) lo = mid;"),
+    "slope kept outside grid": ("if (inside)\n", "if (1)\n"),
+    "sigma at right point": ("        double t = (double)n * dt;\n        orc_sigma_eval(sf, exp(x[n]), t, &pt);",
+                             "        double t = (double)(n + 1) * dt;\n        orc_sigma_eval(sf, exp(x[n]), t, &pt);"),
+    "payoff sign": ("const double itm = (double)op->phi * (SN - op->K);",
+                    "const double itm = (SN - op->K);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    text = open(SRC).read()
+    assert text.count(old) == 1, f"mutation site for {name!r} not unique"
+    src = tmp_path / "lv_oracle_mutant.c"
+    src.write_text(text.replace(old, new))
+    so = str(tmp_path / "liblv_oracle_mutant.so")
+    oracle.build(src=str(src), out=so)
+    lib = oracle.load_library(so)
+    caught = []
+    for pin in oracle_pins.ALL_PINS:
+        try:
+            pin(lib)
+        except AssertionError:
+            caught.append(pin.__name__)
+            break
+    assert caught, f"no pin caught the planted mistake {name!r}"

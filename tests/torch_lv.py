@@ -1,0 +1,54 @@
+"""An independent FP64 restatement of the forward estimator in plain torch
+ops, differentiated by torch.autograd. Test helper only: it pins the
+oracle's hand-written reverse sweep (back-propagation, Sec. IV-C of arXiv
+2002.02481) against a general-purpose AD engine.
+
+It shares no code with the oracle; the only thing it takes from the oracle
+is the array of normals (pinned on its own against cuRAND).
+"""
+import math
+
+import torch
+
+
+def forward_price(spot, time, sigma, S0, r, K, T, n_steps, phi, Z):
+    """Mean discounted payoff of log-Euler paths driven by Z [P, N] under
+    the bilinear local-vol grid (spot [I], time [J], sigma [I, J]).
+
+    The cell convention is the largest node index at or below the point,
+    clamped so that the cell has a right neighbour; weights are clamped to
+    [0, 1] (flat outside the grid)."""
+    I, J = spot.shape[0], time.shape[0]
+    P = Z.shape[0]
+    dt = T / n_steps
+    x = torch.log(S0) * torch.ones(P, dtype=torch.float64)
+    for n in range(n_steps):
+        t = n * dt
+        S = torch.exp(x)
+        i = torch.clamp(torch.searchsorted(spot, S.detach(), right=True) - 1, 0, I - 2)
+        u = torch.clamp((S - spot[i]) / (spot[i + 1] - spot[i]), 0.0, 1.0)
+        if J > 1:
+            tt = torch.tensor([t], dtype=torch.float64)
+            j = int(torch.clamp(torch.searchsorted(time, tt, right=True) - 1, 0, J - 2).item())
+            v = min(max((t - float(time[j])) / float(time[j + 1] - time[j]), 0.0), 1.0)
+            lo = sigma[i, j] * (1 - u) + sigma[i + 1, j] * u
+            hi = sigma[i, j + 1] * (1 - u) + sigma[i + 1, j + 1] * u
+            sig = lo * (1 - v) + hi * v
+        else:
+            sig = sigma[i, 0] * (1 - u) + sigma[i + 1, 0] * u
+        x = x + (r - 0.5 * sig * sig) * dt + sig * math.sqrt(dt) * Z[:, n]
+    SN = torch.exp(x)
+    V = math.exp(-r * T) * torch.relu(phi * (SN - K))
+    return V.mean(), SN
+
+
+def autograd_greeks(spot, time, sigma, S0, r, K, T, n_steps, phi, Z):
+    """(price, delta, vega [I, J], S_N [P]) by torch.autograd, all FP64."""
+    sp = torch.tensor(spot, dtype=torch.float64)
+    tm = torch.tensor(time, dtype=torch.float64)
+    sg = torch.tensor(sigma, dtype=torch.float64, requires_grad=True)
+    s0 = torch.tensor(float(S0), dtype=torch.float64, requires_grad=True)
+    z = torch.tensor(Z, dtype=torch.float64)
+    price, SN = forward_price(sp, tm, sg, s0, r, K, T, n_steps, phi, z)
+    d_s0, d_sig = torch.autograd.grad(price, [s0, sg])
+    return float(price.detach()), float(d_s0), d_sig.numpy(), SN.detach().numpy()
