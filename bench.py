@@ -1,0 +1,301 @@
+"""Benchmark: adjoint path-steps/s (price + delta + every vega bucket) of the
+local-volatility Monte Carlo on one GB300, on the paper's workload shape
+(30 x 60 grid = 1,800 buckets, 156 Euler steps, call K=100 T=3, 2^20 paths).
+
+One step = one lv_price_greeks_device call: forward, compaction, reverse
+sweep with checkpoint recompute, bucket accumulation and the fixed-order
+finalize, inputs resident on the device. Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on this host's cores on a
+bounded sample of the same workload (the reference arm of the comparison).
+Under torchrun (N > 1) every rank runs its own contiguous range of paths
+(weak scaling; no collective on the data path) and rank 0 reports the
+aggregate with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "adjoint path-steps/s (price+delta+all vegas)"
+WORKLOAD = "30x60 local-vol grid, 156 steps, 2^20 paths, European call K=100 T=3, price+delta+1800 vegas"
+
+# Algorithmic thread-operations of one path-step of the method: one forward
+# step (Philox share, uniforms, Box-Muller share, exp, cell, bilinear sigma,
+# Euler) plus one reverse step (sigma adjoint, x adjoint, bucket scatter);
+# the checkpoint recompute is overhead and is not counted.
+ALG_OPS_PER_PATH_STEP = 57.0
+# Issue rate of an SM: 4 schedulers x 32 lanes per clock.
+LANES_PER_SM_CLOCK = 128
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rk, lr
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_model() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def time_oracle(surf, opt, n_paths: int, n_threads: int) -> float:
+    """Seconds the FP64 oracle takes for price + delta + vegas over n_paths."""
+    import oracle
+    o = W.Option(**{**opt.__dict__, "n_paths": n_paths})
+    t0 = time.perf_counter()
+    oracle.run_sums(surf, o, 0, n_paths, greeks=True, n_threads=n_threads)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rk, _ = dist_env()
+    if rk != 0:
+        return 0
+    import oracle
+    oracle.load_library()
+    surf, opt = W.config_paper_shape()
+    threads = oracle.default_threads()
+    sample = 1 << 14
+    for _ in range(args.warmup):
+        time_oracle(surf, opt, sample, threads)
+    secs = [time_oracle(surf, opt, sample, threads) for _ in range(args.steps)]
+    t = sum(secs) / len(secs)
+    value = sample * opt.n_steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "30x60", "n_steps": opt.n_steps,
+                   "n_paths_timed_per_step": sample, "cpu": cpu_model()},
+        "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+                         "sample": f"first {sample} of the 2^20 paths per step, full 156 steps, "
+                                   "price+delta+1800 vegas"},
+        "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except (OSError, ValueError):
+        return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2002_02481_gb300 import lv
+
+    ws, rk, lr = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(lr)
+    dev = torch.device("cuda", lr)
+    lib = lv.load()
+    surf, opt = W.config_paper_shape()
+    P = opt.n_paths                       # per rank (weak scaling)
+    first_path = rk * P
+    S = lv.Surface.from_workload(surf, lib)
+    stream = torch.cuda.current_stream(dev)
+    S.set_stream(stream.cuda_stream)
+    n_out = 3 + surf.n_spot * surf.n_time
+    d_out = torch.zeros(n_out, dtype=torch.float64, device=dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)      # torch creates the underlying CUDA events on first record
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+    # a buffer larger than L2 (129 MB), rewritten between timed steps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        if ws == 1:
+            S.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed, d_out.data_ptr())
+        else:
+            S.price_greeks_sums_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, first_path,
+                                       first_path + P, opt.seed, 0, d_out.data_ptr())
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+
+    step_ms, kern_ms = [], []
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(lr) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            s0.record(stream)
+            step()
+            s1.record(stream)
+            s1.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            kern_ms.append(ev0.elapsed_time(ev1))
+        torch.cuda.synchronize(dev)
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    ms_per_step = total_ms / args.steps
+    value = ws * P * opt.n_steps / (ms_per_step * 1e-3)
+
+    # end to end through the public host API: sigma from pinned host memory in,
+    # price/delta/vega out to host memory, every step
+    e2e = None
+    if rk == 0:
+        sig_host = torch.from_numpy(np.ascontiguousarray(surf.sigma)).pin_memory()
+        sig_np = sig_host.numpy()
+        S.set_kernel_events(0, 0)
+        for _ in range(2):
+            S.set_sigma(sig_np)
+            S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            S.set_sigma(sig_np)
+            S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": P * opt.n_steps / e2e_s, "unit": "path-steps/s",
+               "h2d_bytes_per_step": int(sig_np.nbytes), "d2h_bytes_per_step": int(8 * n_out),
+               "ms_per_step": e2e_s * 1e3}
+
+    if rk == 0:
+        peaks, src = load_peaks()
+        clocks = clk.summary()
+        kern = statistics.mean(kern_ms)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+        peak_gops = n_sm * LANES_PER_SM_CLOCK * mhz * 1e6 / 1e9
+        achieved = ALG_OPS_PER_PATH_STEP * P * opt.n_steps / (kern * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
+                    "frac": achieved / peak_gops, "traffic": None,
+                    "kernel": "mc_kernel<8,true>", "kernel_ms": kern,
+                    "peak_source": f"{n_sm} SMs x {LANES_PER_SM_CLOCK} lanes/clk x median SM clock "
+                                   f"{mhz:.0f} MHz under load ({src} clocks)"}
+        import oracle
+        threads = oracle.default_threads()
+        sample = 1 << 13
+        cpu_s = time_oracle(surf, opt, sample, threads)
+        cpu = {"value": sample * opt.n_steps / cpu_s, "unit": "path-steps/s", "cores": threads,
+               "kind": "oracle", "sample": f"first {sample} of the 2^20 paths, 156 steps, "
+                                           f"price+delta+1800 vegas ({cpu_model()})"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "30x60", "n_steps": opt.n_steps, "n_paths_per_gpu": P,
+                       "l2": "256 MB buffer rewritten between timed steps (outside the timed region)",
+                       "parallelism": f"path-range shards x{ws}"},
+            "clocks": clocks, "gpu_launches": 3 * args.steps, "roofline": roofline,
+            "cpu_baseline": cpu, "e2e": e2e,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,176 @@
+/*
+ * lv.h -- C ABI of the GB300 (sm_103a) local-volatility Monte Carlo library.
+ *
+ * The library prices a European option under Dupire's local-volatility
+ * model, dX/X = sigma(X, t) dW (arXiv 2002.02481, Sec. IV-A), with sigma
+ * given on a spot x time grid and interpolated bilinearly (Sec. IV-D), by
+ * Monte Carlo over explicit Euler paths of the log-spot, and returns the
+ * price together with its pathwise adjoint (back-propagation, Sec. III and
+ * IV-C): the delta d price / d S0 and one vega bucket d price / d sigma_ij
+ * per grid node. Central bump-and-reprice (Sec. III) is provided as the
+ * baseline the adjoint is measured against.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an lv_status and never aborts; on failure the
+ *    outputs are left untouched and lv_last_error() describes the cause.
+ *  - Host arrays passed in are copied before the call returns; the caller
+ *    keeps ownership of everything it passes.
+ *  - A handle must not be used from two host threads at the same time.
+ *    Work runs on the handle's CUDA stream (lv_set_stream; default: the
+ *    legacy default stream). Entry points with host outputs synchronise that
+ *    stream before returning; the *_device variants only enqueue work.
+ *  - Arithmetic: paths in binary32; per-block accumulation of payoffs and
+ *    vega buckets in binary64 (or Kahan-compensated binary32, see
+ *    lv_set_accumulation); cross-block reduction in binary64, fixed order.
+ *  - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with
+ *    key (seed & 0xffffffff, seed >> 32) and counter
+ *    (step / 4, path & 0xffffffff, ((path >> 32) & 0xffff) | stream_id << 16, 0).
+ *    Word w gives the uniform u = ((w >> 9) + 0.5) * 2^-23 in (0, 1); words
+ *    (0, 1) and (2, 3) give two normals each by Box-Muller,
+ *    Z_a = sqrt(-2 ln u_a) cos(2 pi u_b), Z_b = sqrt(-2 ln u_a) sin(2 pi u_b);
+ *    step n uses normal n mod 4 of block n / 4. Results therefore depend only
+ *    on (seed, stream_id, path index), not on the launch configuration, up
+ *    to the rounding order of the reductions.
+ *  - Model: x = ln S, x_{n+1} = x_n + (r - sigma_n^2 / 2) dt + sigma_n sqrt(dt) Z_n
+ *    with dt = T / n_steps and sigma_n = sigma(S_n, t_n), t_n = n dt (left
+ *    point). Payoff e^{-rT} max(phi (S_N - K), 0), phi = +1 call, -1 put.
+ *    Interpolation is bilinear in S and t: cell i is the largest i <= I-2
+ *    with s_i <= S (0 below the grid), weight u = (S - s_i) / (s_{i+1} - s_i)
+ *    clamped to [0, 1]; the same in time. sigma is flat outside the grid,
+ *    and there d sigma / d S = 0. With n_time == 1 sigma does not depend on t.
+ *    The payoff indicator is 1{phi (S_N - K) > 0}: a tie contributes 0.
+ *  - Vega is d price / d sigma_ij per unit of sigma, stored spot-major at
+ *    index i * n_time + j, the same layout as the sigma input.
+ */
+#ifndef LV_H
+#define LV_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lv_surface_s* lv_surface_t;
+typedef struct lv_book_s* lv_book_t;
+
+typedef enum {
+    LV_OK = 0,
+    LV_EINVAL = 1,      /* an argument is out of its documented domain */
+    LV_ENOMEM = 2,      /* a host or device allocation failed */
+    LV_ECUDA = 3,       /* a CUDA runtime call failed (message in lv_last_error) */
+    LV_EINTERNAL = 4    /* a consistency check inside the library failed */
+} lv_status;
+
+/* Level-2 (per-block, across path tiles) accumulation of the payoffs and of
+ * every vega bucket. */
+enum { LV_ACC_FP64 = 0, LV_ACC_KAHAN = 1 };
+
+/* Layout of the [3 + n_spot * n_time] result of lv_price_greeks_device. */
+enum { LV_OUT_PRICE = 0, LV_OUT_DELTA = 1, LV_OUT_STDERR = 2, LV_OUT_VEGA = 3 };
+
+/* Layout of the [3 + n_spot * n_time] raw sums of lv_price_greeks_sums_device:
+ * sum of payoffs, sum of squared payoffs, sum of d V / d x_0 (x_0 = ln S0),
+ * then the sum over paths of every sigma adjoint (spot-major). Sums from
+ * disjoint path ranges add up to the sums of their union. */
+enum { LV_SUM_V = 0, LV_SUM_V2 = 1, LV_SUM_XBAR0 = 2, LV_SUM_VEGA = 3 };
+
+/* Largest supported sizes (shared memory holds the grid, the bucket
+ * accumulators and the per-step time table). */
+#define LV_MAX_STEPS 8192
+#define LV_MAX_NODES 16384
+#define LV_MAX_PATH_INDEX (((int64_t)1) << 48)
+
+/* lv_surface_create -- stage a local-vol grid on the current CUDA device.
+ *   Grid {(s_i, tau_j)} of Sec. IV-A with values sigma_ij.
+ *   spot_nodes [n_spot]  strictly increasing, > 0, n_spot >= 2
+ *   time_nodes [n_time]  strictly increasing, >= 0, n_time >= 1
+ *   sigma [n_spot*n_time] sigma_ij at index i * n_time + j, finite, > 0
+ *   n_spot * n_time <= LV_MAX_NODES
+ *   out                  receives the handle (owned by the caller; release
+ *                        with lv_surface_destroy)
+ * The arrays are copied (to binary32 device copies) before return. */
+lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot,
+                            const double* time_nodes, int32_t n_time,
+                            const double* sigma, lv_surface_t* out);
+
+/* Release a handle and its device memory (NULL is ignored). */
+void lv_surface_destroy(lv_surface_t h);
+
+/* Replace the grid values (same layout and domain as in lv_surface_create);
+ * the host-to-device copy is enqueued on the handle's stream. */
+lv_status lv_surface_set_sigma(lv_surface_t h, const double* sigma);
+
+/* +1 call (default), -1 put. */
+lv_status lv_set_option_type(lv_surface_t h, int32_t phi);
+
+/* CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * that later calls enqueue on; NULL selects the legacy default stream. */
+lv_status lv_set_stream(lv_surface_t h, void* cuda_stream);
+
+/* LV_ACC_FP64 (default) or LV_ACC_KAHAN. */
+lv_status lv_set_accumulation(lv_surface_t h, int32_t mode);
+
+/* Launch shape: threads per block (64..512, multiple of 32), checkpoint
+ * interval k of the reverse sweep (4, 8, 16 or 32 steps) and resident
+ * blocks per SM; 0 keeps the tuned or default value. Results do not depend
+ * on it beyond reduction-order rounding. */
+lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks_per_sm);
+
+/* Record two caller-owned CUDA events (cudaEvent_t, created with timing
+ * enabled) on the handle's stream immediately before and after the Monte
+ * Carlo kernel of every later call, so that a caller can time that kernel
+ * alone; NULL, NULL switches this off. */
+lv_status lv_set_kernel_events(lv_surface_t h, void* start_event, void* end_event);
+
+/* Read back the launch shape the next call will use for (n_steps, greeks). */
+lv_status lv_get_launch(lv_surface_t h, int32_t n_steps, int32_t greeks,
+                        int32_t* block, int32_t* k, int32_t* blocks_per_sm);
+
+/* lv_price -- Monte Carlo price of the option over paths [0, n_paths)
+ * (Sec. IV-C: the mean of the discounted payoff).
+ *   S0 > 0, r finite, K >= 0, T > 0, 1 <= n_steps <= LV_MAX_STEPS,
+ *   1 <= n_paths <= LV_MAX_PATH_INDEX.
+ *   out_price   host, 1 double
+ *   out_stderr  host, 1 double or NULL: standard error of the price */
+lv_status lv_price(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                   int64_t n_paths, uint64_t seed, double* out_price, double* out_stderr);
+
+/* lv_price_greeks -- price, delta and every vega bucket by the pathwise
+ * adjoint (back-propagation through the Euler scheme, Sec. III / IV-C),
+ * from one forward pass and one checkpointed reverse sweep per path.
+ *   out_price  host, 1 double
+ *   out_delta  host, 1 double
+ *   out_vega   host, [n_spot * n_time] doubles, spot-major */
+lv_status lv_price_greeks(lv_surface_t h, double S0, double r, double K, double T,
+                          int32_t n_steps, int64_t n_paths, uint64_t seed,
+                          double* out_price, double* out_delta, double* out_vega);
+
+/* Device-output variant: writes [3 + n_spot * n_time] doubles (layout
+ * LV_OUT_*) to d_out (device memory owned by the caller) on the handle's
+ * stream, without synchronising. */
+lv_status lv_price_greeks_device(lv_surface_t h, double S0, double r, double K, double T,
+                                 int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out);
+
+/* Raw sums over paths [path_begin, path_end) with a given stream_id
+ * (< 65536): [3 + n_spot * n_time] doubles, layout LV_SUM_*, written to
+ * device memory d_sums owned by the caller, without synchronising. This is
+ * the unit of path-range sharding: sums of disjoint ranges add up. */
+lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, double K, double T,
+                                      int32_t n_steps, int64_t path_begin, int64_t path_end,
+                                      uint64_t seed, uint32_t stream_id, double* d_sums);
+
+/* Per-path diagnostics for paths [path_begin, path_begin + m): terminal
+ * log-spot x_N, discounted payoff V and d V / d x_0, each [m] binary32 in
+ * host memory owned by the caller (any of them may be NULL). */
+lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T,
+                         int32_t n_steps, uint64_t seed, int64_t path_begin, int64_t m,
+                         float* out_xN, float* out_V, float* out_xbar0);
+
+/* Thread-local description of the last failure on this host thread. */
+const char* lv_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LV_H */

@@ -96,9 +96,14 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.orc_run.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                             ctypes.c_double, ctypes.c_int32, f64p]
     lib.orc_run.restype = ctypes.c_int
+    lib.orc_run_ex.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                               ctypes.c_double, P(ctypes.c_int64), P(ctypes.c_int8), ctypes.c_int64,
+                               ctypes.c_int32, f64p]
+    lib.orc_run_ex.restype = ctypes.c_int
     lib.orc_finalize.argtypes = [f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, f64p]
     lib.orc_finalize.restype = ctypes.c_int
-    lib.orc_paths.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, f64p, f64p, f64p]
+    lib.orc_paths.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
+                              f64p, f64p, f64p]
     lib.orc_paths.restype = ctypes.c_int
     lib.orc_bump.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int32, f64p, f64p]
@@ -170,17 +175,25 @@ def sigma_eval(surface, S: float, t: float, lib=None) -> dict:
 
 def run_sums(surface, opt, path_begin: int = 0, path_end: Optional[int] = None,
              greeks: bool = True, kink_tol: float = 0.0, n_threads: Optional[int] = None,
-             lib=None) -> np.ndarray:
+             lib=None, itm_overrides: Optional[dict] = None) -> np.ndarray:
     """Raw sums over paths [path_begin, path_end): NSCAL scalars, vega[IJ],
-    kink_vega[IJ] (see lv_oracle.h for the layout)."""
+    kink_vega[IJ] (see lv_oracle.h for the layout). ``itm_overrides`` maps
+    path index -> payoff-indicator decision (bool) to impose on paths whose
+    terminal spot lies within rounding of the strike."""
     lib = lib or load_library()
     a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
               opt.n_steps, opt.seed, opt.phi, opt.stream_id)
     if path_end is None:
         path_end = opt.n_paths
     out = np.zeros(NSCAL + 2 * a.IJ, dtype=np.float64)
-    st = lib.orc_run(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(path_end),
-                     int(bool(greeks)), float(kink_tol), int(n_threads or default_threads()), _ptr(out))
+    keys = sorted((itm_overrides or {}).keys())
+    ov_p = np.array(keys, dtype=np.int64)
+    ov_i = np.array([1 if itm_overrides[k] else 0 for k in keys], dtype=np.int8)
+    st = lib.orc_run_ex(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(path_end),
+                        int(bool(greeks)), float(kink_tol),
+                        ov_p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                        ov_i.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(len(keys)),
+                        int(n_threads or default_threads()), _ptr(out))
     _check(st, "run")
     return out
 
@@ -203,14 +216,14 @@ def price_greeks(surface, opt, n_threads: Optional[int] = None, lib=None) -> dic
                 vega=res[3:].reshape(surface.n_spot, surface.n_time), sums=s)
 
 
-def paths(surface, opt, path_begin: int, m: int, lib=None):
+def paths(surface, opt, path_begin: int, m: int, n_threads: Optional[int] = None, lib=None):
     """Per-path x_N, discounted payoff and d V / d x_0 for m paths."""
     lib = lib or load_library()
     a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
               opt.n_steps, opt.seed, opt.phi, opt.stream_id)
     xN, V, xb = (np.zeros(m) for _ in range(3))
     _check(lib.orc_paths(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(m),
-                         _ptr(xN), _ptr(V), _ptr(xb)), "paths")
+                         int(n_threads or default_threads()), _ptr(xN), _ptr(V), _ptr(xb)), "paths")
     return xN, V, xb
 
 

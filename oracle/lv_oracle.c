@@ -194,12 +194,38 @@ typedef struct {
     int kink;       /* |S_N - K| within the kink band */
 } orc_path_result;
 
+/* Payoff-indicator decisions imposed from outside for a sorted list of
+ * paths: the indicator 1{phi (S_N - K) > 0} is an integer decided in
+ * floating point, and a path whose S_N lies within rounding of K may be
+ * decided differently by a binary32 implementation. Parity tests pass that
+ * implementation's decision for exactly those paths (after checking that
+ * they sit at the kink), so both sides take the same decision. */
+typedef struct {
+    const int64_t* path;   /* sorted ascending */
+    const int8_t* itm;     /* 1 in the money, 0 out */
+    int64_t n;
+} orc_overrides;
+
+static int orc_forced_itm(const orc_overrides* ov, uint64_t path)
+{
+    if (!ov || ov->n <= 0) return -1;
+    int64_t lo = 0, hi = ov->n - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if ((uint64_t)ov->path[mid] == path) return ov->itm[mid] ? 1 : 0;
+        if ((uint64_t)ov->path[mid] < path) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
 /* Simulates one path, and when vega != NULL runs its reverse sweep and adds
  * every sigma adjoint to vega[i * J + j] (and |.| to kink_vega for paths
  * flagged near the payoff kink). */
 static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t path,
                          orc_workspace* ws, int want_greeks, double kink_tol,
-                         double* vega, double* kink_vega, orc_path_result* res)
+                         const orc_overrides* ov, double* vega, double* kink_vega,
+                         orc_path_result* res)
 {
     const int32_t N = op->n_steps, J = sf->n_time;
     const double dt = op->T / (double)N;
@@ -230,7 +256,9 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     if (!want_greeks) return;
 
     /* reverse sweep over the stored trajectory (back-propagation, Sec. IV-C) */
-    double xbar = itm > 0.0 ? disc * (double)op->phi * SN : 0.0;
+    const int forced = orc_forced_itm(ov, path);
+    const int in_money = forced >= 0 ? forced : (itm > 0.0);
+    double xbar = in_money ? disc * (double)op->phi * SN : 0.0;
     double vtot = 0.0;
     for (int32_t n = N - 1; n >= 0; --n) {
         double t = (double)n * dt;
@@ -262,6 +290,7 @@ typedef struct {
     int64_t begin, end;
     int want_greeks;
     double kink_tol;
+    const orc_overrides* ov;
     double* out;     /* ORC_NSCAL + 2 I J */
     int status;
 } orc_job;
@@ -283,7 +312,7 @@ static void* orc_job_run(void* arg)
     }
     for (int64_t p = jb->begin; p < jb->end; ++p) {
         orc_path_result res;
-        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->want_greeks, jb->kink_tol,
+        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->want_greeks, jb->kink_tol, jb->ov,
                      vega, kink_vega, &res);
         out[ORC_SUM_V] += res.V;
         out[ORC_SUM_V2] += res.V * res.V;
@@ -315,6 +344,17 @@ static int orc_check(const orc_surface* sf, const orc_option* op)
 int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
             int want_greeks, double kink_tol, int32_t n_threads, double* out)
 {
+    return orc_run_ex(sf, op, path_begin, path_end, want_greeks, kink_tol, NULL, NULL, 0,
+                      n_threads, out);
+}
+
+int orc_run_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
+               int want_greeks, double kink_tol, const int64_t* ov_path, const int8_t* ov_itm,
+               int64_t n_ov, int32_t n_threads, double* out)
+{
+    orc_overrides ov = { ov_path, ov_itm, n_ov };
+    for (int64_t e = 1; e < n_ov; ++e)
+        if (ov_path[e] <= ov_path[e - 1]) return ORC_EINVAL;
     int st = orc_check(sf, op);
     if (st != ORC_OK) return st;
     if (path_begin < 0 || path_end < path_begin || !out) return ORC_EINVAL;
@@ -340,6 +380,7 @@ int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int
         jobs[k].end = path_begin + P * (k + 1) / n_threads;
         jobs[k].want_greeks = want_greeks;
         jobs[k].kink_tol = kink_tol;
+        jobs[k].ov = &ov;
         jobs[k].out = parts + (int64_t)k * width;
         jobs[k].status = ORC_EINTERNAL;
     }
@@ -375,29 +416,79 @@ int orc_finalize(const double* sums, int64_t n_paths, double S0, int64_t IJ, dou
     return ORC_OK;
 }
 
-int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
-              double* out_xN, double* out_V, double* out_xbar0)
+typedef struct {
+    const orc_surface* sf;
+    const orc_option* op;
+    int64_t first, begin, end;    /* paths [begin, end) written at index p - first */
+    double *xN, *V, *xbar0;
+    int status;
+} orc_path_job;
+
+static void* orc_path_job_run(void* arg)
 {
-    int st = orc_check(sf, op);
-    if (st != ORC_OK) return st;
-    const int64_t IJ = (int64_t)sf->n_spot * sf->n_time;
+    orc_path_job* jb = (orc_path_job*)arg;
+    const int64_t IJ = (int64_t)jb->sf->n_spot * jb->sf->n_time;
     orc_workspace ws;
-    ws.x = (double*)malloc(sizeof(double) * (size_t)(op->n_steps + 1));
-    ws.z = (double*)malloc(sizeof(double) * (size_t)op->n_steps);
+    ws.x = (double*)malloc(sizeof(double) * (size_t)(jb->op->n_steps + 1));
+    ws.z = (double*)malloc(sizeof(double) * (size_t)jb->op->n_steps);
     double* vega = (double*)calloc((size_t)(2 * IJ), sizeof(double));
     if (!ws.x || !ws.z || !vega) {
         free(ws.x); free(ws.z); free(vega);
-        return ORC_ENOMEM;
+        jb->status = ORC_ENOMEM;
+        return NULL;
     }
-    for (int64_t q = 0; q < m; ++q) {
+    for (int64_t p = jb->begin; p < jb->end; ++p) {
         orc_path_result res;
-        orc_one_path(sf, op, (uint64_t)(path_begin + q), &ws, 1, 0.0, vega, vega + IJ, &res);
-        if (out_xN) out_xN[q] = ws.x[op->n_steps];
-        if (out_V) out_V[q] = res.V;
-        if (out_xbar0) out_xbar0[q] = res.xbar0;
+        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, 1, 0.0, NULL, vega, vega + IJ, &res);
+        const int64_t q = p - jb->first;
+        if (jb->xN) jb->xN[q] = ws.x[jb->op->n_steps];
+        if (jb->V) jb->V[q] = res.V;
+        if (jb->xbar0) jb->xbar0[q] = res.xbar0;
     }
     free(ws.x); free(ws.z); free(vega);
-    return ORC_OK;
+    jb->status = ORC_OK;
+    return NULL;
+}
+
+int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
+              int32_t n_threads, double* out_xN, double* out_V, double* out_xbar0)
+{
+    int st = orc_check(sf, op);
+    if (st != ORC_OK) return st;
+    if (path_begin < 0 || m < 0) return ORC_EINVAL;
+    if (m == 0) return ORC_OK;
+    if (n_threads < 1) n_threads = 1;
+    if ((int64_t)n_threads > m) n_threads = (int32_t)m;
+    orc_path_job* jobs = (orc_path_job*)calloc((size_t)n_threads, sizeof(orc_path_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(jobs); free(th);
+        return ORC_ENOMEM;
+    }
+    for (int32_t k = 0; k < n_threads; ++k) {
+        jobs[k].sf = sf;
+        jobs[k].op = op;
+        jobs[k].first = path_begin;
+        jobs[k].begin = path_begin + m * k / n_threads;
+        jobs[k].end = path_begin + m * (k + 1) / n_threads;
+        jobs[k].xN = out_xN;
+        jobs[k].V = out_V;
+        jobs[k].xbar0 = out_xbar0;
+        jobs[k].status = ORC_EINTERNAL;
+    }
+    int started = 0;
+    for (int32_t k = 1; k < n_threads; ++k) {
+        if (pthread_create(&th[k], NULL, orc_path_job_run, &jobs[k]) != 0) break;
+        started = k;
+    }
+    orc_path_job_run(&jobs[0]);
+    for (int32_t k = 1; k <= started; ++k) pthread_join(th[k], NULL);
+    for (int32_t k = started + 1; k < n_threads; ++k) orc_path_job_run(&jobs[k]);
+    st = ORC_OK;
+    for (int32_t k = 0; k < n_threads; ++k)
+        if (jobs[k].status != ORC_OK) st = jobs[k].status;
+    free(jobs); free(th);
+    return st;
 }
 
 /* --------------------------------------------------------- bump and reprice */

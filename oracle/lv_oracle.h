@@ -62,9 +62,12 @@ void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p);
 
 int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
             int want_greeks, double kink_tol, int32_t n_threads, double* out);
+int orc_run_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
+               int want_greeks, double kink_tol, const int64_t* ov_path, const int8_t* ov_itm,
+               int64_t n_ov, int32_t n_threads, double* out);
 int orc_finalize(const double* sums, int64_t n_paths, double S0, int64_t IJ, double* res);
 int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
-              double* out_xN, double* out_V, double* out_xbar0);
+              int32_t n_threads, double* out_xN, double* out_V, double* out_xbar0);
 int orc_bump(const orc_surface* sf, const orc_option* op, int64_t n_paths, double eps_sigma,
              double eps_S0, int32_t n_threads, double* out_vega, double* out_delta);
 

@@ -1,0 +1,564 @@
+// lv_api.cu -- host runtime behind the C ABI of include/lv.h: handle
+// lifetime, argument validation, launch planning, scratch management and
+// the host-output wrappers.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lv.h"
+#include "lv_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+lv_status fail(lv_status s, const std::string& msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+#define LV_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(LV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+// Makes the handle's device current for the duration of a call and
+// restores the caller's device afterwards.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_finite(double a) { return std::isfinite(a); }
+
+}  // namespace
+
+struct lv_surface_s {
+    int device = 0;
+    int num_sms = 0;
+    int I = 0, J = 0, Je = 0;
+    std::vector<double> spot, time;
+    float* d_sig = nullptr;
+    float* d_node = nullptr;
+    float2* d_ab = nullptr;
+    double* d_tau = nullptr;
+    float* h_sig_stage = nullptr;    // pinned staging for sigma uploads
+    int log_uniform = 0;
+    float cell_scale = 0.0f, cell_shift = 0.0f, s_lo = 0.0f, s_hi = 0.0f;
+    int phi = 1;
+    cudaStream_t stream = nullptr;
+    int acc_mode = LV_ACC_FP64;
+    int cfg_block = 0, cfg_k = 0, cfg_bps = 0;
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double* d_res = nullptr;         // [3 + I*J] result of the host-output calls
+    double* h_res = nullptr;         // pinned copy of it
+    cudaEvent_t ev_start = nullptr;  // optional events around the Monte Carlo kernel
+    cudaEvent_t ev_end = nullptr;
+};
+
+namespace {
+
+lv_status check_sigma(const double* sigma, int64_t n)
+{
+    if (!sigma) return fail(LV_EINVAL, "sigma is NULL");
+    for (int64_t e = 0; e < n; ++e)
+        if (!is_finite(sigma[e]) || !(sigma[e] > 0.0))
+            return fail(LV_EINVAL, "sigma[" + std::to_string(e) + "] must be finite and > 0");
+    return LV_OK;
+}
+
+// sigma (spot-major, binary64) -> time-major binary32 rows, with row 0
+// repeated when the grid has a single time node.
+void pack_sigma(const lv_surface_s* h, const double* sigma, float* dst)
+{
+    for (int j = 0; j < h->Je; ++j) {
+        const int jj = j < h->J ? j : h->J - 1;
+        for (int i = 0; i < h->I; ++i) dst[(size_t)j * h->I + i] = (float)sigma[(size_t)i * h->J + jj];
+    }
+}
+
+void free_surface(lv_surface_s* h)
+{
+    if (!h) return;
+    cudaFree(h->d_sig);
+    cudaFree(h->d_node);
+    cudaFree(h->d_ab);
+    cudaFree(h->d_tau);
+    cudaFree(h->d_scratch);
+    cudaFree(h->d_res);
+    cudaFreeHost(h->h_sig_stage);
+    cudaFreeHost(h->h_res);
+    delete h;
+}
+
+lv_status check_option(double S0, double r, double K, double T, int32_t n_steps)
+{
+    if (!is_finite(S0) || !(S0 > 0.0)) return fail(LV_EINVAL, "S0 must be finite and > 0");
+    if (!is_finite(r)) return fail(LV_EINVAL, "r must be finite");
+    if (!is_finite(K) || K < 0.0) return fail(LV_EINVAL, "K must be finite and >= 0");
+    if (!is_finite(T) || !(T > 0.0)) return fail(LV_EINVAL, "T must be finite and > 0");
+    if (n_steps < 1 || n_steps > LV_MAX_STEPS)
+        return fail(LV_EINVAL, "n_steps must be in [1, LV_MAX_STEPS]");
+    return LV_OK;
+}
+
+struct Plan {
+    int block = 256, k = 8, bps = 1, grid = 1;
+    size_t smem = 0;
+    int n_tiles = 0, n_ck = 0, row_words = 0, n_chunks = 0;
+    size_t off_counter = 0, off_part = 0, off_chunks = 0, off_ckpt = 0, total = 0;
+};
+
+size_t round_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
+
+lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps)
+{
+    *block = h->cfg_block ? h->cfg_block : 256;
+    *k = greeks ? (h->cfg_k ? h->cfg_k : 8) : 4;
+    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks);
+    if (smem > 200 * 1024)
+        return fail(LV_EINVAL, "grid and time table do not fit in shared memory (" +
+                               std::to_string(smem) + " bytes)");
+    int occ = 0;
+    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, smem, &occ));
+    if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
+    *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
+    return LV_OK;
+}
+
+lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, Plan* p)
+{
+    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps);
+    if (st != LV_OK) return st;
+    p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks);
+    const int64_t tiles = (n_paths + p->block - 1) / p->block;
+    if (tiles > (int64_t)0x7fffffff) return fail(LV_EINVAL, "too many paths for one call");
+    p->n_tiles = (int)tiles;
+    const int64_t slots = (int64_t)p->bps * h->num_sms;
+    p->grid = (int)(tiles < slots ? tiles : slots);
+    if (p->grid < 1) p->grid = 1;
+    p->n_ck = greeks ? (n_steps + p->k - 1) / p->k : 0;
+    p->row_words = greeks ? 3 + h->Je * h->I : 3;   // price-only rows hold the scalars
+    p->n_chunks = lv::finalize_chunks(p->grid);
+    size_t o = 0;
+    p->off_counter = o; o += 256;
+    p->off_part = o;    o = round_up(o + sizeof(double) * (size_t)p->grid * p->row_words, 256);
+    p->off_chunks = o;  o = round_up(o + sizeof(double) * (size_t)p->n_chunks * p->row_words, 256);
+    p->off_ckpt = o;    o = round_up(o + sizeof(float) * (size_t)p->n_ck * p->grid * p->block, 256);
+    p->total = o;
+    return LV_OK;
+}
+
+lv_status ensure_scratch(lv_surface_s* h, size_t bytes)
+{
+    if (bytes <= h->scratch_bytes) return LV_OK;
+    if (h->d_scratch) {
+        LV_CUDA(cudaStreamSynchronize(h->stream));
+        LV_CUDA(cudaFree(h->d_scratch));
+        h->d_scratch = nullptr;
+        h->scratch_bytes = 0;
+    }
+    const size_t want = round_up(bytes + bytes / 4, 1 << 20);
+    if (cudaMalloc(&h->d_scratch, want) != cudaSuccess) {
+        cudaGetLastError();
+        h->d_scratch = nullptr;
+        return fail(LV_ENOMEM, "cannot allocate " + std::to_string(want) + " bytes of scratch");
+    }
+    h->scratch_bytes = want;
+    // the tile counter starts at zero; every finalize resets it
+    LV_CUDA(cudaMemsetAsync(h->d_scratch, 0, 256, h->stream));
+    return LV_OK;
+}
+
+struct McCall {
+    double S0, r, K, T;
+    int32_t n_steps;
+    int64_t path_begin, n_paths;
+    uint64_t seed;
+    uint32_t stream_id;
+    bool greeks;
+    bool want_sums;
+    double* d_out;           // [3 + I*J] device
+    float* dbg_xN = nullptr;
+    float* dbg_V = nullptr;
+    float* dbg_xbar0 = nullptr;
+};
+
+lv::McParams base_params(const lv_surface_s* h, const McCall& c)
+{
+    lv::McParams P{};
+    P.sig = h->d_sig;
+    P.node = h->d_node;
+    P.ab = h->d_ab;
+    P.tau = h->d_tau;
+    P.I = h->I;
+    P.J = h->J;
+    P.Je = h->Je;
+    P.log_uniform = h->log_uniform;
+    P.cell_scale = h->cell_scale;
+    P.cell_shift = h->cell_shift;
+    P.s_lo = h->s_lo;
+    P.s_hi = h->s_hi;
+    const double dt = c.T / (double)c.n_steps;
+    P.x0 = (float)std::log(c.S0);
+    P.rdt = (float)(c.r * dt);
+    P.hdt = (float)(0.5 * dt);
+    P.dt = (float)dt;
+    P.sqdt = (float)std::sqrt(dt);
+    P.K = (float)c.K;
+    P.disc = (float)std::exp(-c.r * c.T);
+    P.phi = (float)h->phi;
+    P.dt_d = dt;
+    P.N = c.n_steps;
+    P.k0 = (uint32_t)(c.seed & 0xffffffffu);
+    P.k1 = (uint32_t)(c.seed >> 32);
+    P.stream_id = c.stream_id;
+    P.path_begin = c.path_begin;
+    P.n_paths = c.n_paths;
+    P.acc_mode = h->acc_mode;
+    return P;
+}
+
+lv_status run_mc(lv_surface_s* h, const McCall& c)
+{
+    lv_status st = check_option(c.S0, c.r, c.K, c.T, c.n_steps);
+    if (st != LV_OK) return st;
+    if (c.n_paths < 1) return fail(LV_EINVAL, "the path range is empty");
+    if (c.path_begin < 0 || c.path_begin + c.n_paths > LV_MAX_PATH_INDEX)
+        return fail(LV_EINVAL, "path indices must lie in [0, 2^48)");
+    if (c.stream_id >= 65536u) return fail(LV_EINVAL, "stream_id must be < 65536");
+    Plan p;
+    st = make_plan(h, c.n_steps, c.n_paths, c.greeks, &p);
+    if (st != LV_OK) return st;
+    st = ensure_scratch(h, p.total);
+    if (st != LV_OK) return st;
+    char* base = static_cast<char*>(h->d_scratch);
+    lv::McParams P = base_params(h, c);
+    P.n_tiles = p.n_tiles;
+    P.tile_counter = reinterpret_cast<unsigned int*>(base + p.off_counter);
+    P.partials = reinterpret_cast<double*>(base + p.off_part);
+    P.row_words = p.row_words;
+    P.ckpt = reinterpret_cast<float*>(base + p.off_ckpt);
+    P.n_ck = p.n_ck;
+    P.dbg_xN = c.dbg_xN;
+    P.dbg_V = c.dbg_V;
+    P.dbg_xbar0 = c.dbg_xbar0;
+    if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
+    LV_CUDA(lv::launch_mc(P, p.grid, p.block, p.k, c.greeks, p.smem, h->stream));
+    if (h->ev_end) LV_CUDA(cudaEventRecord(h->ev_end, h->stream));
+    lv::FinalizeParams F{};
+    F.partials = P.partials;
+    F.G = p.grid;
+    F.row_words = p.row_words;
+    F.I = h->I;
+    F.J = h->J;
+    F.acc_mode = c.greeks ? h->acc_mode : 0;
+    F.n_paths = c.n_paths;
+    F.S0 = c.S0;
+    F.want_sums = c.want_sums ? 1 : 0;
+    F.chunks = reinterpret_cast<double*>(base + p.off_chunks);
+    F.out = c.d_out;
+    F.tile_counter = P.tile_counter;
+    LV_CUDA(lv::launch_finalize(F, h->stream));
+    return LV_OK;
+}
+
+lv_status fetch_result(lv_surface_s* h)
+{
+    const size_t n = 3 + (size_t)h->I * h->J;
+    LV_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    LV_CUDA(cudaStreamSynchronize(h->stream));
+    return LV_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lv_last_error(void) { return g_last_error.c_str(); }
+
+lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const double* time_nodes,
+                            int32_t n_time, const double* sigma, lv_surface_t* out)
+{
+    if (!out) return fail(LV_EINVAL, "out is NULL");
+    if (!spot_nodes || !time_nodes) return fail(LV_EINVAL, "node arrays must not be NULL");
+    if (n_spot < 2) return fail(LV_EINVAL, "n_spot must be >= 2");
+    if (n_time < 1) return fail(LV_EINVAL, "n_time must be >= 1");
+    if ((int64_t)n_spot * n_time > LV_MAX_NODES)
+        return fail(LV_EINVAL, "n_spot * n_time exceeds LV_MAX_NODES");
+    for (int i = 0; i < n_spot; ++i) {
+        if (!is_finite(spot_nodes[i]) || !(spot_nodes[i] > 0.0))
+            return fail(LV_EINVAL, "spot nodes must be finite and > 0");
+        if (i > 0 && !(spot_nodes[i] > spot_nodes[i - 1]))
+            return fail(LV_EINVAL, "spot nodes must be strictly increasing");
+    }
+    for (int j = 0; j < n_time; ++j) {
+        if (!is_finite(time_nodes[j]) || time_nodes[j] < 0.0)
+            return fail(LV_EINVAL, "time nodes must be finite and >= 0");
+        if (j > 0 && !(time_nodes[j] > time_nodes[j - 1]))
+            return fail(LV_EINVAL, "time nodes must be strictly increasing");
+    }
+    lv_status st = check_sigma(sigma, (int64_t)n_spot * n_time);
+    if (st != LV_OK) return st;
+
+    lv_surface_s* h = new (std::nothrow) lv_surface_s();
+    if (!h) return fail(LV_ENOMEM, "out of host memory");
+    h->I = n_spot;
+    h->J = n_time;
+    h->Je = n_time > 1 ? n_time : 2;
+    h->spot.assign(spot_nodes, spot_nodes + n_spot);
+    h->time.assign(time_nodes, time_nodes + n_time);
+
+    // cell lookup straight from ln S when the nodes are equally spaced in ln S
+    const double l0 = std::log(spot_nodes[0]);
+    const double dl = (std::log(spot_nodes[n_spot - 1]) - l0) / (n_spot - 1);
+    double dev = 0.0;
+    for (int i = 0; i < n_spot; ++i)
+        dev = std::fmax(dev, std::fabs(std::log(spot_nodes[i]) - (l0 + i * dl)));
+    h->log_uniform = dev <= 1e-6 * dl ? 1 : 0;
+    h->cell_scale = (float)(1.0 / dl);
+    h->cell_shift = (float)(-l0 / dl);
+    h->s_lo = (float)spot_nodes[0];
+    h->s_hi = (float)spot_nodes[n_spot - 1];
+
+    auto bail = [&](lv_status s, const std::string& m) {
+        free_surface(h);
+        return fail(s, m);
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(LV_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return bail(LV_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+
+    const size_t nsig = (size_t)h->Je * h->I;
+    const size_t nres = 3 + (size_t)n_spot * n_time;
+    if (cudaMalloc(&h->d_sig, sizeof(float) * nsig) != cudaSuccess ||
+        cudaMalloc(&h->d_node, sizeof(float) * n_spot) != cudaSuccess ||
+        cudaMalloc(&h->d_ab, sizeof(float2) * n_spot) != cudaSuccess ||
+        cudaMalloc(&h->d_tau, sizeof(double) * n_time) != cudaSuccess ||
+        cudaMalloc(&h->d_res, sizeof(double) * nres) != cudaSuccess ||
+        cudaMallocHost(&h->h_sig_stage, sizeof(float) * nsig) != cudaSuccess ||
+        cudaMallocHost(&h->h_res, sizeof(double) * nres) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(LV_ENOMEM, "device or pinned allocation failed");
+    }
+    std::vector<float> node(n_spot);
+    std::vector<float2> ab(n_spot);
+    for (int i = 0; i < n_spot; ++i) {
+        node[i] = (float)spot_nodes[i];
+        if (i + 1 < n_spot) {
+            const double w = spot_nodes[i + 1] - spot_nodes[i];
+            ab[i] = make_float2((float)(1.0 / w), (float)(-spot_nodes[i] / w));
+        } else {
+            ab[i] = make_float2(0.0f, 0.0f);
+        }
+    }
+    pack_sigma(h, sigma, h->h_sig_stage);
+    if (cudaMemcpy(h->d_sig, h->h_sig_stage, sizeof(float) * nsig, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_node, node.data(), sizeof(float) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_ab, ab.data(), sizeof(float2) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_tau, time_nodes, sizeof(double) * n_time, cudaMemcpyHostToDevice) != cudaSuccess) {
+        e = cudaGetLastError();
+        return bail(LV_ECUDA, std::string("upload of the grid failed: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    return LV_OK;
+}
+
+void lv_surface_destroy(lv_surface_t h)
+{
+    if (!h) return;
+    DeviceGuard g(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    free_surface(h);
+}
+
+lv_status lv_surface_set_sigma(lv_surface_t h, const double* sigma)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    lv_status st = check_sigma(sigma, (int64_t)h->I * h->J);
+    if (st != LV_OK) return st;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    // the staging buffer may still feed an earlier asynchronous copy
+    LV_CUDA(cudaStreamSynchronize(h->stream));
+    pack_sigma(h, sigma, h->h_sig_stage);
+    LV_CUDA(cudaMemcpyAsync(h->d_sig, h->h_sig_stage, sizeof(float) * (size_t)h->Je * h->I,
+                            cudaMemcpyHostToDevice, h->stream));
+    return LV_OK;
+}
+
+lv_status lv_set_option_type(lv_surface_t h, int32_t phi)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (phi != 1 && phi != -1) return fail(LV_EINVAL, "phi must be +1 (call) or -1 (put)");
+    h->phi = phi;
+    return LV_OK;
+}
+
+lv_status lv_set_stream(lv_surface_t h, void* cuda_stream)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    return LV_OK;
+}
+
+lv_status lv_set_accumulation(lv_surface_t h, int32_t mode)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (mode != LV_ACC_FP64 && mode != LV_ACC_KAHAN)
+        return fail(LV_EINVAL, "mode must be LV_ACC_FP64 or LV_ACC_KAHAN");
+    h->acc_mode = mode;
+    return LV_OK;
+}
+
+lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks_per_sm)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (block != 0 && (block < 64 || block > 512 || block % 32 != 0))
+        return fail(LV_EINVAL, "block must be 0 or a multiple of 32 in [64, 512]");
+    if (k != 0 && k != 4 && k != 8 && k != 16 && k != 32)
+        return fail(LV_EINVAL, "k must be 0, 4, 8, 16 or 32");
+    if (blocks_per_sm < 0) return fail(LV_EINVAL, "blocks_per_sm must be >= 0");
+    h->cfg_block = block;
+    h->cfg_k = k;
+    h->cfg_bps = blocks_per_sm;
+    return LV_OK;
+}
+
+lv_status lv_set_kernel_events(lv_surface_t h, void* start_event, void* end_event)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if ((start_event == nullptr) != (end_event == nullptr))
+        return fail(LV_EINVAL, "pass both events or neither");
+    h->ev_start = static_cast<cudaEvent_t>(start_event);
+    h->ev_end = static_cast<cudaEvent_t>(end_event);
+    return LV_OK;
+}
+
+lv_status lv_get_launch(lv_surface_t h, int32_t n_steps, int32_t greeks, int32_t* block, int32_t* k,
+                        int32_t* blocks_per_sm)
+{
+    if (!h || !block || !k || !blocks_per_sm) return fail(LV_EINVAL, "NULL argument");
+    if (n_steps < 1 || n_steps > LV_MAX_STEPS) return fail(LV_EINVAL, "n_steps out of range");
+    DeviceGuard g(h->device);
+    int b = 0, kk = 0, bps = 0;
+    lv_status st = choose_launch(h, n_steps, greeks != 0, &b, &kk, &bps);
+    if (st != LV_OK) return st;
+    *block = b;
+    *k = kk;
+    *blocks_per_sm = bps;
+    return LV_OK;
+}
+
+lv_status lv_price(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                   int64_t n_paths, uint64_t seed, double* out_price, double* out_stderr)
+{
+    if (!h || !out_price) return fail(LV_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, false, false, h->d_res};
+    lv_status st = run_mc(h, c);
+    if (st != LV_OK) return st;
+    st = fetch_result(h);
+    if (st != LV_OK) return st;
+    *out_price = h->h_res[LV_OUT_PRICE];
+    if (out_stderr) *out_stderr = h->h_res[LV_OUT_STDERR];
+    return LV_OK;
+}
+
+lv_status lv_price_greeks_device(lv_surface_t h, double S0, double r, double K, double T,
+                                 int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out)
+{
+    if (!h || !d_out) return fail(LV_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, d_out};
+    return run_mc(h, c);
+}
+
+lv_status lv_price_greeks(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                          int64_t n_paths, uint64_t seed, double* out_price, double* out_delta,
+                          double* out_vega)
+{
+    if (!h || !out_price || !out_delta || !out_vega) return fail(LV_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, h->d_res};
+    lv_status st = run_mc(h, c);
+    if (st != LV_OK) return st;
+    st = fetch_result(h);
+    if (st != LV_OK) return st;
+    *out_price = h->h_res[LV_OUT_PRICE];
+    *out_delta = h->h_res[LV_OUT_DELTA];
+    std::memcpy(out_vega, h->h_res + LV_OUT_VEGA, sizeof(double) * (size_t)h->I * h->J);
+    return LV_OK;
+}
+
+lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, double K, double T,
+                                      int32_t n_steps, int64_t path_begin, int64_t path_end,
+                                      uint64_t seed, uint32_t stream_id, double* d_sums)
+{
+    if (!h || !d_sums) return fail(LV_EINVAL, "NULL argument");
+    if (path_end <= path_begin) return fail(LV_EINVAL, "path_end must exceed path_begin");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, path_begin, path_end - path_begin, seed, stream_id, true, true, d_sums};
+    return run_mc(h, c);
+}
+
+lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                         uint64_t seed, int64_t path_begin, int64_t m, float* out_xN, float* out_V,
+                         float* out_xbar0)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (m < 1 || m > (int64_t)1 << 26) return fail(LV_EINVAL, "m must be in [1, 2^26]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    float* d = nullptr;
+    if (cudaMalloc(&d, sizeof(float) * 3 * (size_t)m) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LV_ENOMEM, "cannot allocate the per-path buffers");
+    }
+    McCall c{S0, r, K, T, n_steps, path_begin, m, seed, 0u, true, false, h->d_res};
+    c.dbg_xN = d;
+    c.dbg_V = d + m;
+    c.dbg_xbar0 = d + 2 * m;
+    lv_status st = run_mc(h, c);
+    if (st == LV_OK) {
+        std::vector<float> hb(3 * (size_t)m);
+        cudaError_t e = cudaMemcpyAsync(hb.data(), d, sizeof(float) * 3 * (size_t)m,
+                                        cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            st = fail(LV_ECUDA, std::string("per-path copy: ") + cudaGetErrorString(e));
+        } else {
+            if (out_xN) std::memcpy(out_xN, hb.data(), sizeof(float) * m);
+            if (out_V) std::memcpy(out_V, hb.data() + m, sizeof(float) * m);
+            if (out_xbar0) std::memcpy(out_xbar0, hb.data() + 2 * m, sizeof(float) * m);
+        }
+    }
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    return st;
+}
+
+}  // extern "C"

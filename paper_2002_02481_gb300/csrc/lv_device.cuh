@@ -1,0 +1,155 @@
+// lv_device.cuh -- device building blocks: counter-based normals, the
+// bilinear local-vol lookup and one log-Euler step (arXiv 2002.02481,
+// Sec. IV-A, IV-B, IV-D).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lv_internal.h"
+
+namespace lv {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit products and xors with a Weyl-sequence key schedule.
+__device__ __forceinline__ void philox4x32_10(uint32_t& c0, uint32_t& c1, uint32_t& c2,
+                                              uint32_t& c3, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// u = ((w >> 9) + 1/2) 2^-23 = (2m + 1) 2^-24, m < 2^23: the mantissa trick
+// gives 1 + m 2^-23 in [1, 2), and subtracting 1 - 2^-24 is exact.
+__device__ __forceinline__ float uniform_open01(uint32_t w)
+{
+    return __uint_as_float((w >> 9) | 0x3f800000u) - __uint_as_float(0x3f7fffffu);
+}
+
+__device__ __forceinline__ float sqrt_approx(float a)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+__device__ __forceinline__ float ex2_approx(float a)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+__device__ __forceinline__ float lg2_approx(float a)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
+// Four standard normals for Philox block `blk` of a path. Box-Muller on
+// word pairs (0,1) and (2,3): Z_a = rho cos(2 pi u_b), Z_b = rho sin(2 pi u_b),
+// rho = sqrt(-2 ln u_a). The angle is evaluated as 2 pi (u_b - 1/2) (exact
+// shift, keeps the hardware sine/cosine inside [-pi, pi)), which flips the
+// sign of both: cos(a + pi) = -cos a, sin(a + pi) = -sin a.
+__device__ __forceinline__ void normals4(uint32_t blk, uint32_t c1, uint32_t c2, uint32_t k0,
+                                         uint32_t k1, float z[4])
+{
+    uint32_t w0 = blk, w1 = c1, w2 = c2, w3 = 0u;
+    philox4x32_10(w0, w1, w2, w3, k0, k1);
+    const float m2ln2 = -1.3862943611198906f;   // -2 ln 2
+    const float two_pi = 6.2831853071795865f;
+    {
+        const float rho = sqrt_approx(m2ln2 * lg2_approx(uniform_open01(w0)));
+        float s, c;
+        __sincosf(two_pi * (uniform_open01(w1) - 0.5f), &s, &c);
+        z[0] = -rho * c;
+        z[1] = -rho * s;
+    }
+    {
+        const float rho = sqrt_approx(m2ln2 * lg2_approx(uniform_open01(w2)));
+        float s, c;
+        __sincosf(two_pi * (uniform_open01(w3) - 0.5f), &s, &c);
+        z[2] = -rho * c;
+        z[3] = -rho * s;
+    }
+}
+
+// Shared-memory view of the grid for one block.
+struct SmemGrid {
+    const int2* tab;       // [N] per step: (j * I, bits of v)
+    const float* sig;      // [Je * I] time-major
+    const float* node;     // [I]
+    const float2* ab;      // [I - 1]
+};
+
+// Spot cell: the largest i <= I-2 with s_i <= S. On log-uniform grids the
+// index comes from ln S directly (off by one only when S is within binary32
+// rounding of a node, where the clamped weight gives the same value); on
+// other grids a binary search over the nodes.
+__device__ __forceinline__ int spot_cell(const McParams& P, const SmemGrid& g, float x, float S)
+{
+    if (P.log_uniform) {
+        const int i = __float2int_rd(fmaf(x, P.cell_scale, P.cell_shift));
+        return min(max(i, 0), P.I - 2);
+    }
+    int lo = 0, hi = P.I - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g.node[mid] <= S) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct StepEval {
+    float S;       // e^{x_n}
+    float sigma;   // sigma(S_n, t_n)
+    float u;       // clamped spot weight
+    int i;         // spot cell
+    float slope;   // d sigma / d S (0 outside the grid)
+};
+
+// Bilinear sigma at (S_n, t_n), Sec. IV-D; slope only when WANT_SLOPE.
+template <bool WANT_SLOPE>
+__device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid& g, float x,
+                                               int row, float v)
+{
+    StepEval e;
+    e.S = ex2_approx(x * 1.4426950408889634f);
+    e.i = spot_cell(P, g, x, e.S);
+    const float2 ab = g.ab[e.i];
+    e.u = __saturatef(fmaf(e.S, ab.x, ab.y));
+    const float* r0 = g.sig + row + e.i;
+    const float s00 = r0[0], s10 = r0[1], s01 = r0[P.I], s11 = r0[P.I + 1];
+    const float d0 = s10 - s00, d1 = s11 - s01;
+    const float top = fmaf(e.u, d0, s00);
+    const float bot = fmaf(e.u, d1, s01);
+    e.sigma = fmaf(v, bot - top, top);
+    if (WANT_SLOPE) {
+        const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
+        e.slope = inside ? fmaf(v, d1 - d0, d0) * ab.x : 0.0f;
+    } else {
+        e.slope = 0.0f;
+    }
+    return e;
+}
+
+// x_{n+1} = x_n + (r - sigma^2/2) dt + sigma sqrt(dt) Z  (Sec. IV-A, log-Euler)
+__device__ __forceinline__ float euler_step(const McParams& P, float x, float sigma, float z)
+{
+    return x + fmaf(sigma, P.sqdt * z, fmaf(-P.hdt * sigma, sigma, P.rdt));
+}
+
+}  // namespace lv

@@ -1,0 +1,215 @@
+"""Thin ctypes binding of the C ABI in include/lv.h (argument marshalling
+only: every step of the Monte Carlo path and its adjoint runs in the CUDA
+library). The functions keep the C names.
+
+The library is loaded from the package's _lib/ directory; when it is missing
+this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblv_gb300.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "lv.h")
+
+LV_OK, LV_EINVAL, LV_ENOMEM, LV_ECUDA, LV_EINTERNAL = range(5)
+LV_ACC_FP64, LV_ACC_KAHAN = 0, 1
+LV_OUT_PRICE, LV_OUT_DELTA, LV_OUT_STDERR, LV_OUT_VEGA = 0, 1, 2, 3
+LV_SUM_V, LV_SUM_V2, LV_SUM_XBAR0, LV_SUM_VEGA = 0, 1, 2, 3
+
+_lock = threading.Lock()
+_lib: Optional[ctypes.CDLL] = None
+
+
+class LVError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str):
+        super().__init__(f"{what} failed (status {status}): {msg}")
+        self.status = status
+
+
+def exported_names() -> list[str]:
+    """Every function name declared in include/lv.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:lv_status|void|const char\*)\s+(lv_\w+)\s*\(", text, re.M)))
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load the compiled library (no build, no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"CUDA library not built: {p} is missing "
+                              "(run __graft_entry__.build() or python -m paper_2002_02481_gb300.build)")
+        lib = _declare(ctypes.CDLL(p))
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
+    c = ctypes
+    vp, d, i32, i64, u64, u32 = c.c_void_p, c.c_double, c.c_int32, c.c_int64, c.c_uint64, c.c_uint32
+    dp, fp = c.POINTER(c.c_double), c.POINTER(c.c_float)
+    sig = {
+        "lv_surface_create": [dp, i32, dp, i32, dp, c.POINTER(vp)],
+        "lv_surface_destroy": [vp],
+        "lv_surface_set_sigma": [vp, dp],
+        "lv_set_option_type": [vp, i32],
+        "lv_set_stream": [vp, vp],
+        "lv_set_accumulation": [vp, i32],
+        "lv_set_launch": [vp, i32, i32, i32],
+        "lv_set_kernel_events": [vp, vp, vp],
+        "lv_get_launch": [vp, i32, i32, c.POINTER(i32), c.POINTER(i32), c.POINTER(i32)],
+        "lv_price": [vp, d, d, d, d, i32, i64, u64, dp, dp],
+        "lv_price_greeks": [vp, d, d, d, d, i32, i64, u64, dp, dp, dp],
+        "lv_price_greeks_device": [vp, d, d, d, d, i32, i64, u64, vp],
+        "lv_price_greeks_sums_device": [vp, d, d, d, d, i32, i64, i64, u64, u32, vp],
+        "lv_debug_paths": [vp, d, d, d, d, i32, u64, i64, i64, fp, fp, fp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = None if name == "lv_surface_destroy" else c.c_int
+    lib.lv_last_error.argtypes = []
+    lib.lv_last_error.restype = c.c_char_p
+    for name, args in _optional_sigs(c).items():
+        if hasattr(lib, name):
+            getattr(lib, name).argtypes = args
+            getattr(lib, name).restype = c.c_int
+    return lib
+
+
+def _optional_sigs(c):
+    vp, d, i32, i64, u64 = c.c_void_p, c.c_double, c.c_int32, c.c_int64, c.c_uint64
+    dp = c.POINTER(c.c_double)
+    return {
+        "lv_bump_greeks": [vp, d, d, d, d, i32, i64, u64, d, dp, dp, dp],
+    }
+
+
+def _check(lib, st: int, what: str) -> None:
+    if st != LV_OK:
+        raise LVError(st, what, lib.lv_last_error().decode(errors="replace"))
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fp(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Surface:
+    """A local-vol grid staged on the current CUDA device (lv_surface_t)."""
+
+    def __init__(self, spot, time, sigma, lib: Optional[ctypes.CDLL] = None):
+        self.lib = lib or load()
+        self.spot = np.ascontiguousarray(spot, dtype=np.float64)
+        self.time = np.ascontiguousarray(time, dtype=np.float64)
+        s = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
+        self.n_spot, self.n_time = self.spot.shape[0], self.time.shape[0]
+        self.h = ctypes.c_void_p()
+        _check(self.lib, self.lib.lv_surface_create(_dp(self.spot), self.n_spot, _dp(self.time), self.n_time,
+                                                    _dp(s), ctypes.byref(self.h)), "lv_surface_create")
+
+    @classmethod
+    def from_workload(cls, surf, lib=None) -> "Surface":
+        return cls(surf.spot, surf.time, surf.sigma, lib)
+
+    @property
+    def IJ(self) -> int:
+        return self.n_spot * self.n_time
+
+    def close(self) -> None:
+        if self.h:
+            self.lib.lv_surface_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # settings
+    def set_sigma(self, sigma) -> None:
+        s = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
+        _check(self.lib, self.lib.lv_surface_set_sigma(self.h, _dp(s)), "lv_surface_set_sigma")
+
+    def set_option_type(self, phi: int) -> None:
+        _check(self.lib, self.lib.lv_set_option_type(self.h, int(phi)), "lv_set_option_type")
+
+    def set_stream(self, stream_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_set_stream(self.h, ctypes.c_void_p(stream_ptr or None)), "lv_set_stream")
+
+    def set_accumulation(self, mode: int) -> None:
+        _check(self.lib, self.lib.lv_set_accumulation(self.h, int(mode)), "lv_set_accumulation")
+
+    def set_launch(self, block: int = 0, k: int = 0, blocks_per_sm: int = 0) -> None:
+        _check(self.lib, self.lib.lv_set_launch(self.h, int(block), int(k), int(blocks_per_sm)), "lv_set_launch")
+
+    def set_kernel_events(self, start_ptr: int, end_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_set_kernel_events(self.h, ctypes.c_void_p(start_ptr or None),
+                                                       ctypes.c_void_p(end_ptr or None)), "lv_set_kernel_events")
+
+    def get_launch(self, n_steps: int, greeks: bool = True):
+        b, k, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib, self.lib.lv_get_launch(self.h, int(n_steps), int(greeks), ctypes.byref(b),
+                                                ctypes.byref(k), ctypes.byref(s)), "lv_get_launch")
+        return b.value, k.value, s.value
+
+    # pricing
+    def price(self, S0, r, K, T, n_steps, n_paths, seed):
+        p, e = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib, self.lib.lv_price(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
+                                           ctypes.byref(p), ctypes.byref(e)), "lv_price")
+        return p.value, e.value
+
+    def price_greeks(self, S0, r, K, T, n_steps, n_paths, seed):
+        p, d = ctypes.c_double(), ctypes.c_double()
+        vega = np.zeros(self.IJ, dtype=np.float64)
+        _check(self.lib, self.lib.lv_price_greeks(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
+                                                  ctypes.byref(p), ctypes.byref(d), _dp(vega)), "lv_price_greeks")
+        return p.value, d.value, vega.reshape(self.n_spot, self.n_time)
+
+    def price_greeks_device(self, S0, r, K, T, n_steps, n_paths, seed, d_out_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_price_greeks_device(self.h, S0, r, K, T, int(n_steps), int(n_paths),
+                                                         int(seed), ctypes.c_void_p(d_out_ptr)),
+               "lv_price_greeks_device")
+
+    def price_greeks_sums_device(self, S0, r, K, T, n_steps, path_begin, path_end, seed, stream_id,
+                                 d_sums_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_price_greeks_sums_device(
+            self.h, S0, r, K, T, int(n_steps), int(path_begin), int(path_end), int(seed), int(stream_id),
+            ctypes.c_void_p(d_sums_ptr)), "lv_price_greeks_sums_device")
+
+    def debug_paths(self, S0, r, K, T, n_steps, seed, path_begin, m):
+        xN, V, xb = (np.zeros(m, dtype=np.float32) for _ in range(3))
+        _check(self.lib, self.lib.lv_debug_paths(self.h, S0, r, K, T, int(n_steps), int(seed), int(path_begin),
+                                                 int(m), _fp(xN), _fp(V), _fp(xb)), "lv_debug_paths")
+        return xN, V, xb
+
+    def bump_greeks(self, S0, r, K, T, n_steps, n_paths, seed, eps):
+        p, d = ctypes.c_double(), ctypes.c_double()
+        vega = np.zeros(self.IJ, dtype=np.float64)
+        _check(self.lib, self.lib.lv_bump_greeks(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
+                                                 float(eps), ctypes.byref(p), ctypes.byref(d), _dp(vega)),
+               "lv_bump_greeks")
+        return p.value, d.value, vega.reshape(self.n_spot, self.n_time)

@@ -1,0 +1,172 @@
+"""CUDA path against the FP64 oracle, element by element on the same seeded
+inputs, through the C ABI (needs a GB300)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from paper_2002_02481_gb300 import build, lv
+
+from . import gpu_common as G
+
+pytestmark = pytest.mark.gpu
+
+REPORT = os.environ.get("LV_PARITY_REPORT")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return lv.load()
+
+
+def _report(name, d):
+    if REPORT:
+        with open(REPORT, "a") as f:
+            f.write(json.dumps({"case": name, **d}) + "\n")
+
+
+EDGE = [
+    # name, surface, option
+    ("2x1 grid, one time node", W.random_surface(1, 2, 1, s_lo=80, s_hi=125),
+     W.Option(S0=100.0, r=0.0, K=100.0, T=1.0, n_steps=13, n_paths=3000, seed=3)),
+    ("3x2 grid, paths leave both sides", W.random_surface(2, 3, 2, s_lo=97, s_hi=103, t_hi=0.5),
+     W.Option(S0=100.0, r=0.01, K=99.0, T=0.5, n_steps=8, n_paths=5000, seed=4)),
+    ("uneven 7x5 grid (binary search), put", W.random_surface(3, 7, 5, s_lo=75, s_hi=130, t_hi=1.0, uneven=True),
+     W.Option(S0=100.0, r=0.02, K=101.0, T=0.8, n_steps=10, n_paths=4097, seed=5, phi=-1)),
+    ("strike at a node, maturity inside a time cell", W.random_surface(4, 6, 4, s_lo=70, s_hi=140, t_hi=2.0),
+     W.Option(S0=100.0, r=0.0, K=float(W.random_surface(4, 6, 4, s_lo=70, s_hi=140, t_hi=2.0).spot[2]),
+              T=1.3, n_steps=9, n_paths=2500, seed=6)),
+    ("one path", W.small_skew_surface(), W.Option(S0=100.0, r=0.0, K=90.0, T=1.0, n_steps=52, n_paths=1, seed=2)),
+    ("ragged tail 33 paths, 1 step", W.small_skew_surface(),
+     W.Option(S0=100.0, r=0.03, K=100.0, T=0.1, n_steps=1, n_paths=33, seed=8)),
+    ("deep OTM call (few live paths)", W.small_skew_surface(),
+     W.Option(S0=100.0, r=0.0, K=160.0, T=1.0, n_steps=52, n_paths=20000, seed=9)),
+    ("K = 0 (every path live)", W.small_skew_surface(),
+     W.Option(S0=100.0, r=0.04, K=0.0, T=1.0, n_steps=20, n_paths=8192, seed=10)),
+]
+
+
+@pytest.mark.parametrize("case", EDGE, ids=[c[0] for c in EDGE])
+def test_edge_cases(case, lib):
+    name, surf, opt = case
+    _report(name, G.full_parity(surf, opt, lib, label=name))
+
+
+def test_small_skew_16384_paths(lib):
+    surf, opt = W.config_small()
+    _report("20x10 grid, 52 steps, 2^14 paths", G.full_parity(surf, opt, lib, label="small"))
+
+
+def test_paper_shape_full_size(lib):
+    """30x60 grid, 156 steps, 2^20 paths: every path checked, aggregates at
+    full size in the default launch shape."""
+    surf, opt = W.config_paper_shape()
+    _report("30x60 grid, 156 steps, 2^20 paths", G.full_parity(surf, opt, lib, label="paper shape"))
+
+
+@pytest.mark.parametrize("acc", [0, 1], ids=["fp64", "kahan"])
+def test_precision_subset(acc, lib):
+    """2^24-path precision workload: its first 2^18 paths against the oracle
+    with both level-2 accumulations."""
+    for which in ("small", "paper"):
+        surf, opt = W.config_precision(which)
+        opt.n_paths = 1 << 18
+        _report(f"precision {which} 2^18 acc={acc}", G.full_parity(surf, opt, lib, accumulation=acc,
+                                                                    label=f"precision {which}"))
+
+
+def test_large_grid_sample(lib):
+    """100x100 grid, 1,260 steps, checkpoints every 32 steps: the first 2^14
+    paths against the oracle."""
+    surf, opt = W.config_large()
+    opt.n_paths = 1 << 14
+    _report("100x100 grid, 1260 steps, 2^14 paths, k=32",
+            G.full_parity(surf, opt, lib, launch=(256, 32, 0), label="large"))
+
+
+@pytest.mark.parametrize("launch", [(128, 4, 0), (256, 8, 0), (512, 16, 0), (256, 32, 1), (64, 8, 2)])
+def test_launch_shape_invariance(launch, lib):
+    """Per-path arithmetic does not depend on the launch shape; results agree
+    to reduction-order rounding."""
+    surf, opt = W.config_small()
+    opt.n_paths = 20000
+    base = G.make_surface(surf, opt, lib)
+    p0, d0, v0 = base.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    alt = G.make_surface(surf, opt, lib, launch=launch)
+    p1, d1, v1 = alt.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert abs(p1 - p0) <= 1e-12 * abs(p0)
+    assert abs(d1 - d0) <= 1e-9 * abs(d0)
+    assert np.max(np.abs(v1 - v0)) <= 1e-6 * np.max(np.abs(v0))
+
+
+def test_path_range_sharding(lib):
+    """Sums over [0, P/3), [P/3, P) add up to the sums over [0, P): the
+    path-range split a multi-GPU run would use."""
+    import torch
+    surf, opt = W.config_paper_shape()
+    P = 1 << 16
+    gs = G.make_surface(surf, opt, lib)
+    n = 3 + surf.n_spot * surf.n_time
+    whole = torch.zeros(n, dtype=torch.float64, device="cuda")
+    a = torch.zeros(n, dtype=torch.float64, device="cuda")
+    b = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gs.set_stream(torch.cuda.current_stream().cuda_stream)
+    args = (opt.S0, opt.r, opt.K, opt.T, opt.n_steps)
+    gs.price_greeks_sums_device(*args, 0, P, opt.seed, 0, whole.data_ptr())
+    gs.price_greeks_sums_device(*args, 0, P // 3, opt.seed, 0, a.data_ptr())
+    gs.price_greeks_sums_device(*args, P // 3, P, opt.seed, 0, b.data_ptr())
+    torch.cuda.synchronize()
+    w, s = whole.cpu().numpy(), (a + b).cpu().numpy()
+    assert abs(w[0] - s[0]) <= 1e-12 * abs(w[0])
+    assert abs(w[2] - s[2]) <= 1e-10 * abs(w[2])
+    assert np.max(np.abs(w[3:] - s[3:])) <= 1e-6 * np.max(np.abs(w[3:]))
+    # and the raw sums agree with the oracle's
+    ref = oracle.run_sums(surf, opt, 0, P)
+    assert abs(w[0] - ref[oracle.SUM_V]) <= 1e-5 * abs(ref[oracle.SUM_V])
+
+
+def test_device_output_matches_host_output(lib):
+    import torch
+    surf, opt = W.config_small()
+    gs = G.make_surface(surf, opt, lib)
+    gs.set_stream(torch.cuda.current_stream().cuda_stream)
+    out = torch.zeros(3 + surf.n_spot * surf.n_time, dtype=torch.float64, device="cuda")
+    gs.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, out.data_ptr())
+    torch.cuda.synchronize()
+    p, d, v = gs.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    o = out.cpu().numpy()
+    assert abs(o[0] - p) <= 1e-12 * abs(p)
+    assert abs(o[1] - d) <= 1e-9 * abs(d)
+    np.testing.assert_allclose(o[3:].reshape(v.shape), v, rtol=0, atol=1e-6 * np.max(np.abs(v)))
+    # the price-only entry point agrees with the price of the adjoint call
+    pp, se = gs.price(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert abs(pp - p) <= 1e-12 * abs(p) and se > 0
+
+
+def test_gpu_argument_errors(lib):
+    surf, opt = W.config_small()
+    gs = G.make_surface(surf, opt, lib)
+    bad = [
+        dict(S0=-1.0), dict(T=0.0), dict(K=-5.0), dict(n_steps=0), dict(n_steps=lv_max_steps() + 1),
+        dict(n_paths=0), dict(r=float("inf")),
+    ]
+    for b in bad:
+        a = dict(S0=100.0, r=0.0, K=100.0, T=1.0, n_steps=10, n_paths=100, seed=1)
+        a.update(b)
+        with pytest.raises(lv.LVError) as e:
+            gs.price_greeks(**a)
+        assert e.value.status == lv.LV_EINVAL, b
+    with pytest.raises(lv.LVError):
+        gs.set_launch(100, 8, 0)
+    with pytest.raises(lv.LVError):
+        gs.set_launch(256, 12, 0)
+
+
+def lv_max_steps():
+    return 8192
