@@ -229,6 +229,23 @@ def run_ours(args):
     ms_per_step = total_ms / args.steps
     value = ws * P * opt.n_steps / (ms_per_step * 1e-3)
 
+    # forward only (price without Greeks) and the bump-and-reprice baseline, same workload
+    fwd_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        S.price(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
+        fwd_ms.append(ev0.elapsed_time(ev1))
+    bump = None
+    if rk == 0 and not args.no_bump:
+        pa, da, va = S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
+        flush.fill_(1)
+        pb, db, vb = S.bump_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed, 1e-4)
+        bump_ms = ev0.elapsed_time(ev1)
+        bump = {"ms": bump_ms, "scenarios": 3 + 2 * surf.n_spot * surf.n_time, "eps": 1e-4,
+                "speedup_vs_adjoint_kernel": bump_ms / statistics.mean(kern_ms),
+                "max_vega_diff_vs_adjoint_of_max": float(np.max(np.abs(vb - va)) / np.max(np.abs(va))),
+                "delta_diff_vs_adjoint_rel": abs(db - da) / abs(da)}
+
     # end to end through the public host API: sigma from pinned host memory in,
     # price/delta/vega out to host memory, every step
     e2e = None
@@ -259,7 +276,9 @@ def run_ours(args):
         achieved = ALG_OPS_PER_PATH_STEP * P * opt.n_steps / (kern * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
                     "frac": achieved / peak_gops, "traffic": None,
-                    "kernel": "mc_kernel<8,true>", "kernel_ms": kern,
+                    "kernel": "adjoint_kernel<k=%d,binary64 level 2> (block %d, %d blocks/SM)" % (
+                        S.get_launch(opt.n_steps, True)[1], S.get_launch(opt.n_steps, True)[0],
+                        S.get_launch(opt.n_steps, True)[2]), "kernel_ms": kern,
                     "peak_source": f"{n_sm} SMs x {LANES_PER_SM_CLOCK} lanes/clk x median SM clock "
                                    f"{mhz:.0f} MHz under load ({src} clocks)"}
         import oracle
@@ -278,6 +297,9 @@ def run_ours(args):
                        "parallelism": f"path-range shards x{ws}"},
             "clocks": clocks, "gpu_launches": 3 * args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e,
+            "forward_only": {"kernel_ms": statistics.mean(fwd_ms),
+                             "value": P * opt.n_steps / (statistics.mean(fwd_ms) * 1e-3), "unit": "path-steps/s"},
+            "bump_reprice": bump,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -291,6 +313,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-bump", action="store_true", help="skip the bump-and-reprice timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -111,7 +111,7 @@ lv_status lv_set_stream(lv_surface_t h, void* cuda_stream);
 /* LV_ACC_FP64 (default) or LV_ACC_KAHAN. */
 lv_status lv_set_accumulation(lv_surface_t h, int32_t mode);
 
-/* Launch shape: threads per block (64..512, multiple of 32), checkpoint
+/* Launch shape: threads per block (64..256, multiple of 32), checkpoint
  * interval k of the reverse sweep (4, 8, 16 or 32 steps) and resident
  * blocks per SM; 0 keeps the tuned or default value. Results do not depend
  * on it beyond reduction-order rounding. */
@@ -130,7 +130,7 @@ lv_status lv_get_launch(lv_surface_t h, int32_t n_steps, int32_t greeks,
 /* lv_price -- Monte Carlo price of the option over paths [0, n_paths)
  * (Sec. IV-C: the mean of the discounted payoff).
  *   S0 > 0, r finite, K >= 0, T > 0, 1 <= n_steps <= LV_MAX_STEPS,
- *   1 <= n_paths <= LV_MAX_PATH_INDEX.
+ *   1 <= n_paths < 2^31 per call (path indices below LV_MAX_PATH_INDEX).
  *   out_price   host, 1 double
  *   out_stderr  host, 1 double or NULL: standard error of the price */
 lv_status lv_price(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
@@ -160,12 +160,32 @@ lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, doubl
                                       int32_t n_steps, int64_t path_begin, int64_t path_end,
                                       uint64_t seed, uint32_t stream_id, double* d_sums);
 
-/* Per-path diagnostics for paths [path_begin, path_begin + m): terminal
- * log-spot x_N, discounted payoff V and d V / d x_0, each [m] binary32 in
- * host memory owned by the caller (any of them may be NULL). */
+/* lv_bump_greeks -- central bump-and-reprice (Sec. III), the baseline the
+ * adjoint is measured against: every grid value sigma_ij +/- eps/2 and
+ * S0 +/- eps_S/2 with eps_S = 1e-4 * S0, each pair of scenarios on the same
+ * random numbers (common random numbers), the price difference divided by
+ * the bump. One batched launch over the 3 + 2 * n_spot * n_time scenarios.
+ * Outputs as in lv_price_greeks (the price is that of the unbumped model).
+ *   eps > 0, finite. */
+lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T,
+                         int32_t n_steps, int64_t n_paths, uint64_t seed, double eps,
+                         double* out_price, double* out_delta, double* out_vega);
+
+/* Per-path diagnostics for paths [path_begin, path_begin + m), m <= 2^26:
+ * terminal log-spot x_N, discounted payoff V and d V / d x_0, each [m]
+ * binary32 in host memory owned by the caller (any may be NULL). The values
+ * of a path do not depend on the launch shape. Also logs every forward step
+ * whose spot S lies within node_band * s of one of its cell's nodes s:
+ * out_ev [ev_cap][3] int32 receives (path - path_begin, step, 2 i + inside)
+ * with i the spot cell taken and inside = 1 when S lay in [s_0, s_{I-1}]
+ * (which switches d sigma / d S on); *out_n_ev the number of such steps
+ * (entries beyond ev_cap are counted but not stored; order unspecified).
+ * These are the integer decisions a binary64 reimplementation may take
+ * differently when S sits within rounding of a node. */
 lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T,
                          int32_t n_steps, uint64_t seed, int64_t path_begin, int64_t m,
-                         float* out_xN, float* out_V, float* out_xbar0);
+                         float* out_xN, float* out_V, float* out_xbar0,
+                         double node_band, int64_t ev_cap, int32_t* out_ev, int64_t* out_n_ev);
 
 /* Thread-local description of the last failure on this host thread. */
 const char* lv_last_error(void);

@@ -44,6 +44,37 @@ class _Option(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32)]
 
 
+class _Decisions(ctypes.Structure):
+    _fields_ = [("itm_path", ctypes.POINTER(ctypes.c_int64)), ("itm_val", ctypes.POINTER(ctypes.c_int8)),
+                ("n_itm", ctypes.c_int64),
+                ("cell_path", ctypes.POINTER(ctypes.c_int64)), ("cell_step", ctypes.POINTER(ctypes.c_int32)),
+                ("cell_code", ctypes.POINTER(ctypes.c_int32)), ("n_cell", ctypes.c_int64)]
+
+
+class Decisions:
+    """Decisions taken from another implementation (see lv_oracle.c):
+    ``itm`` maps path -> payoff indicator; ``cells`` is (paths, steps,
+    codes) with code = 2 * spot_cell + inside_grid."""
+
+    def __init__(self, itm: Optional[dict] = None, cells=None):
+        keys = sorted((itm or {}).keys())
+        self.itm_path = np.array(keys, dtype=np.int64)
+        self.itm_val = np.array([1 if itm[k] else 0 for k in keys], dtype=np.int8)
+        if cells is None:
+            cells = (np.zeros(0, np.int64), np.zeros(0, np.int32), np.zeros(0, np.int32))
+        cp, cs, cc = (np.asarray(a) for a in cells)
+        order = np.lexsort((cs, cp))
+        self.cell_path = np.ascontiguousarray(cp[order], dtype=np.int64)
+        self.cell_step = np.ascontiguousarray(cs[order], dtype=np.int32)
+        self.cell_code = np.ascontiguousarray(cc[order], dtype=np.int32)
+        P = ctypes.POINTER
+        self.c = _Decisions(self.itm_path.ctypes.data_as(P(ctypes.c_int64)),
+                            self.itm_val.ctypes.data_as(P(ctypes.c_int8)), len(keys),
+                            self.cell_path.ctypes.data_as(P(ctypes.c_int64)),
+                            self.cell_step.ctypes.data_as(P(ctypes.c_int32)),
+                            self.cell_code.ctypes.data_as(P(ctypes.c_int32)), len(self.cell_path))
+
+
 class _Point(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("u", ctypes.c_double),
                 ("v", ctypes.c_double), ("w", ctypes.c_double * 4),
@@ -97,14 +128,16 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                             ctypes.c_double, ctypes.c_int32, f64p]
     lib.orc_run.restype = ctypes.c_int
     lib.orc_run_ex.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
-                               ctypes.c_double, P(ctypes.c_int64), P(ctypes.c_int8), ctypes.c_int64,
-                               ctypes.c_int32, f64p]
+                               ctypes.c_double, P(_Decisions), ctypes.c_int32, f64p]
     lib.orc_run_ex.restype = ctypes.c_int
     lib.orc_finalize.argtypes = [f64p, ctypes.c_int64, ctypes.c_double, ctypes.c_int64, f64p]
     lib.orc_finalize.restype = ctypes.c_int
     lib.orc_paths.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, ctypes.c_int32,
                               f64p, f64p, f64p]
     lib.orc_paths.restype = ctypes.c_int
+    lib.orc_paths_ex.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, P(_Decisions),
+                                 ctypes.c_int32, f64p, f64p, f64p]
+    lib.orc_paths_ex.restype = ctypes.c_int
     lib.orc_bump.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int32, f64p, f64p]
     lib.orc_bump.restype = ctypes.c_int
@@ -175,24 +208,19 @@ def sigma_eval(surface, S: float, t: float, lib=None) -> dict:
 
 def run_sums(surface, opt, path_begin: int = 0, path_end: Optional[int] = None,
              greeks: bool = True, kink_tol: float = 0.0, n_threads: Optional[int] = None,
-             lib=None, itm_overrides: Optional[dict] = None) -> np.ndarray:
+             lib=None, decisions: Optional[Decisions] = None) -> np.ndarray:
     """Raw sums over paths [path_begin, path_end): NSCAL scalars, vega[IJ],
-    kink_vega[IJ] (see lv_oracle.h for the layout). ``itm_overrides`` maps
-    path index -> payoff-indicator decision (bool) to impose on paths whose
-    terminal spot lies within rounding of the strike."""
+    kink_vega[IJ] (see lv_oracle.h for the layout). ``decisions`` imposes
+    payoff-indicator and spot-cell decisions on listed paths / steps."""
     lib = lib or load_library()
     a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
               opt.n_steps, opt.seed, opt.phi, opt.stream_id)
     if path_end is None:
         path_end = opt.n_paths
     out = np.zeros(NSCAL + 2 * a.IJ, dtype=np.float64)
-    keys = sorted((itm_overrides or {}).keys())
-    ov_p = np.array(keys, dtype=np.int64)
-    ov_i = np.array([1 if itm_overrides[k] else 0 for k in keys], dtype=np.int8)
     st = lib.orc_run_ex(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(path_end),
                         int(bool(greeks)), float(kink_tol),
-                        ov_p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                        ov_i.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(len(keys)),
+                        ctypes.byref(decisions.c) if decisions is not None else None,
                         int(n_threads or default_threads()), _ptr(out))
     _check(st, "run")
     return out
@@ -216,14 +244,16 @@ def price_greeks(surface, opt, n_threads: Optional[int] = None, lib=None) -> dic
                 vega=res[3:].reshape(surface.n_spot, surface.n_time), sums=s)
 
 
-def paths(surface, opt, path_begin: int, m: int, n_threads: Optional[int] = None, lib=None):
+def paths(surface, opt, path_begin: int, m: int, n_threads: Optional[int] = None, lib=None,
+          decisions: Optional[Decisions] = None):
     """Per-path x_N, discounted payoff and d V / d x_0 for m paths."""
     lib = lib or load_library()
     a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
               opt.n_steps, opt.seed, opt.phi, opt.stream_id)
     xN, V, xb = (np.zeros(m) for _ in range(3))
-    _check(lib.orc_paths(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(m),
-                         int(n_threads or default_threads()), _ptr(xN), _ptr(V), _ptr(xb)), "paths")
+    _check(lib.orc_paths_ex(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(m),
+                            ctypes.byref(decisions.c) if decisions is not None else None,
+                            int(n_threads or default_threads()), _ptr(xN), _ptr(V), _ptr(xb)), "paths")
     return xN, V, xb
 
 

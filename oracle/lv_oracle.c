@@ -143,14 +143,15 @@ static double orc_clamp01(double a)
     return a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
 }
 
-void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p)
+/* Bilinear sigma and d sigma / d S at (S, t) in spot cell i; `inside` says
+ * whether S lies in [s_0, s_{I-1}] (outside, sigma is flat in S and its
+ * S-derivative is 0). */
+static void orc_sigma_in_cell(const orc_surface* sf, double S, double t, int32_t i, int inside,
+                              orc_point* p)
 {
-    const int32_t I = sf->n_spot, J = sf->n_time;
-    int32_t i = orc_cell(sf->spot, I, S);
+    const int32_t J = sf->n_time;
     double width = sf->spot[i + 1] - sf->spot[i];
-    double u_raw = (S - sf->spot[i]) / width;
-    double u = orc_clamp01(u_raw);
-    int inside = (u_raw >= 0.0 && u_raw <= 1.0);
+    double u = orc_clamp01((S - sf->spot[i]) / width);
 
     int32_t j = 0;
     double v = 0.0;
@@ -179,6 +180,14 @@ void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p)
         p->dsigma_dS = 0.0;
 }
 
+void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p)
+{
+    const int32_t I = sf->n_spot;
+    int32_t i = orc_cell(sf->spot, I, S);
+    int inside = (S >= sf->spot[0] && S <= sf->spot[I - 1]);
+    orc_sigma_in_cell(sf, S, t, i, inside, p);
+}
+
 /* --------------------------------------------------------------- one path */
 
 typedef struct {
@@ -194,29 +203,55 @@ typedef struct {
     int kink;       /* |S_N - K| within the kink band */
 } orc_path_result;
 
-/* Payoff-indicator decisions imposed from outside for a sorted list of
- * paths: the indicator 1{phi (S_N - K) > 0} is an integer decided in
- * floating point, and a path whose S_N lies within rounding of K may be
- * decided differently by a binary32 implementation. Parity tests pass that
- * implementation's decision for exactly those paths (after checking that
- * they sit at the kink), so both sides take the same decision. */
-typedef struct {
-    const int64_t* path;   /* sorted ascending */
-    const int8_t* itm;     /* 1 in the money, 0 out */
-    int64_t n;
-} orc_overrides;
-
-static int orc_forced_itm(const orc_overrides* ov, uint64_t path)
+/* Decisions imposed from outside. Two integers of the method are decided
+ * in floating point: the payoff indicator 1{phi (S_N - K) > 0} and the spot
+ * cell of a step (with whether S lies inside the grid, which switches
+ * d sigma / d S on). A binary32 implementation may decide them differently
+ * for a path whose value lies within rounding of the strike or of a node.
+ * Parity tests pass that implementation's decisions for exactly those
+ * paths and steps (after checking that they sit at the kink), so both sides
+ * take the same decisions. Lists are sorted ascending by path (and step). */
+static int orc_forced_itm(const orc_decisions* d, uint64_t path)
 {
-    if (!ov || ov->n <= 0) return -1;
-    int64_t lo = 0, hi = ov->n - 1;
+    if (!d || d->n_itm <= 0) return -1;
+    int64_t lo = 0, hi = d->n_itm - 1;
     while (lo <= hi) {
         int64_t mid = lo + (hi - lo) / 2;
-        if ((uint64_t)ov->path[mid] == path) return ov->itm[mid] ? 1 : 0;
-        if ((uint64_t)ov->path[mid] < path) lo = mid + 1;
+        if ((uint64_t)d->itm_path[mid] == path) return d->itm_val[mid] ? 1 : 0;
+        if ((uint64_t)d->itm_path[mid] < path) lo = mid + 1;
         else hi = mid - 1;
     }
     return -1;
+}
+
+/* [*first, *last) = the entries of `path` in the cell list. */
+static void orc_cell_range(const orc_decisions* d, uint64_t path, int64_t* first, int64_t* last)
+{
+    *first = *last = 0;
+    if (!d || d->n_cell <= 0) return;
+    int64_t lo = 0, hi = d->n_cell;
+    while (lo < hi) {                      /* first entry with path >= `path` */
+        int64_t mid = lo + (hi - lo) / 2;
+        if ((uint64_t)d->cell_path[mid] < path) lo = mid + 1;
+        else hi = mid;
+    }
+    *first = lo;
+    while (lo < d->n_cell && (uint64_t)d->cell_path[lo] == path) ++lo;
+    *last = lo;
+}
+
+/* Forced cell code (2 i + inside) of step n, or -1. */
+static int32_t orc_forced_cell(const orc_decisions* d, int64_t first, int64_t last, int32_t n)
+{
+    for (int64_t e = first; e < last; ++e)
+        if (d->cell_step[e] == n) return d->cell_code[e];
+    return -1;
+}
+
+static void orc_sigma_decided(const orc_surface* sf, double S, double t, int32_t code, orc_point* p)
+{
+    if (code < 0) orc_sigma_eval(sf, S, t, p);
+    else orc_sigma_in_cell(sf, S, t, code >> 1, code & 1, p);
 }
 
 /* Simulates one path, and when vega != NULL runs its reverse sweep and adds
@@ -224,7 +259,7 @@ static int orc_forced_itm(const orc_overrides* ov, uint64_t path)
  * flagged near the payoff kink). */
 static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t path,
                          orc_workspace* ws, int want_greeks, double kink_tol,
-                         const orc_overrides* ov, double* vega, double* kink_vega,
+                         const orc_decisions* dec, double* vega, double* kink_vega,
                          orc_path_result* res)
 {
     const int32_t N = op->n_steps, J = sf->n_time;
@@ -235,12 +270,14 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     orc_point pt;
 
     orc_normals(op->seed, op->stream_id, path, N, z);
+    int64_t c_first, c_last;
+    orc_cell_range(dec, path, &c_first, &c_last);
 
     /* forward: Euler on the log-spot (Sec. IV-A) */
     x[0] = log(op->S0);
     for (int32_t n = 0; n < N; ++n) {
         double t = (double)n * dt;
-        orc_sigma_eval(sf, exp(x[n]), t, &pt);
+        orc_sigma_decided(sf, exp(x[n]), t, orc_forced_cell(dec, c_first, c_last, n), &pt);
         x[n + 1] = x[n] + (op->r - 0.5 * pt.sigma * pt.sigma) * dt + pt.sigma * sqdt * z[n];
     }
 
@@ -256,14 +293,14 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     if (!want_greeks) return;
 
     /* reverse sweep over the stored trajectory (back-propagation, Sec. IV-C) */
-    const int forced = orc_forced_itm(ov, path);
+    const int forced = orc_forced_itm(dec, path);
     const int in_money = forced >= 0 ? forced : (itm > 0.0);
     double xbar = in_money ? disc * (double)op->phi * SN : 0.0;
     double vtot = 0.0;
     for (int32_t n = N - 1; n >= 0; --n) {
         double t = (double)n * dt;
         double S = exp(x[n]);
-        orc_sigma_eval(sf, S, t, &pt);
+        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);
         double h = sqdt * z[n] - pt.sigma * dt;     /* d x_{n+1} / d sigma_n */
         double sbar = xbar * h;                     /* adjoint of sigma_n */
         int32_t nodes[4] = { pt.i * J + pt.j, (pt.i + 1) * J + pt.j,
@@ -290,7 +327,7 @@ typedef struct {
     int64_t begin, end;
     int want_greeks;
     double kink_tol;
-    const orc_overrides* ov;
+    const orc_decisions* dec;
     double* out;     /* ORC_NSCAL + 2 I J */
     int status;
 } orc_job;
@@ -312,7 +349,7 @@ static void* orc_job_run(void* arg)
     }
     for (int64_t p = jb->begin; p < jb->end; ++p) {
         orc_path_result res;
-        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->want_greeks, jb->kink_tol, jb->ov,
+        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->want_greeks, jb->kink_tol, jb->dec,
                      vega, kink_vega, &res);
         out[ORC_SUM_V] += res.V;
         out[ORC_SUM_V2] += res.V * res.V;
@@ -344,17 +381,26 @@ static int orc_check(const orc_surface* sf, const orc_option* op)
 int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
             int want_greeks, double kink_tol, int32_t n_threads, double* out)
 {
-    return orc_run_ex(sf, op, path_begin, path_end, want_greeks, kink_tol, NULL, NULL, 0,
-                      n_threads, out);
+    return orc_run_ex(sf, op, path_begin, path_end, want_greeks, kink_tol, NULL, n_threads, out);
+}
+
+static int orc_check_decisions(const orc_decisions* d)
+{
+    if (!d) return ORC_OK;
+    for (int64_t e = 1; e < d->n_itm; ++e)
+        if (d->itm_path[e] <= d->itm_path[e - 1]) return ORC_EINVAL;
+    for (int64_t e = 1; e < d->n_cell; ++e)
+        if (d->cell_path[e] < d->cell_path[e - 1] ||
+            (d->cell_path[e] == d->cell_path[e - 1] && d->cell_step[e] <= d->cell_step[e - 1]))
+            return ORC_EINVAL;
+    return ORC_OK;
 }
 
 int orc_run_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
-               int want_greeks, double kink_tol, const int64_t* ov_path, const int8_t* ov_itm,
-               int64_t n_ov, int32_t n_threads, double* out)
+               int want_greeks, double kink_tol, const orc_decisions* dec, int32_t n_threads,
+               double* out)
 {
-    orc_overrides ov = { ov_path, ov_itm, n_ov };
-    for (int64_t e = 1; e < n_ov; ++e)
-        if (ov_path[e] <= ov_path[e - 1]) return ORC_EINVAL;
+    if (orc_check_decisions(dec) != ORC_OK) return ORC_EINVAL;
     int st = orc_check(sf, op);
     if (st != ORC_OK) return st;
     if (path_begin < 0 || path_end < path_begin || !out) return ORC_EINVAL;
@@ -380,7 +426,7 @@ int orc_run_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, 
         jobs[k].end = path_begin + P * (k + 1) / n_threads;
         jobs[k].want_greeks = want_greeks;
         jobs[k].kink_tol = kink_tol;
-        jobs[k].ov = &ov;
+        jobs[k].dec = dec;
         jobs[k].out = parts + (int64_t)k * width;
         jobs[k].status = ORC_EINTERNAL;
     }
@@ -419,6 +465,7 @@ int orc_finalize(const double* sums, int64_t n_paths, double S0, int64_t IJ, dou
 typedef struct {
     const orc_surface* sf;
     const orc_option* op;
+    const orc_decisions* dec;
     int64_t first, begin, end;    /* paths [begin, end) written at index p - first */
     double *xN, *V, *xbar0;
     int status;
@@ -439,7 +486,7 @@ static void* orc_path_job_run(void* arg)
     }
     for (int64_t p = jb->begin; p < jb->end; ++p) {
         orc_path_result res;
-        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, 1, 0.0, NULL, vega, vega + IJ, &res);
+        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, 1, 0.0, jb->dec, vega, vega + IJ, &res);
         const int64_t q = p - jb->first;
         if (jb->xN) jb->xN[q] = ws.x[jb->op->n_steps];
         if (jb->V) jb->V[q] = res.V;
@@ -453,8 +500,16 @@ static void* orc_path_job_run(void* arg)
 int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
               int32_t n_threads, double* out_xN, double* out_V, double* out_xbar0)
 {
+    return orc_paths_ex(sf, op, path_begin, m, NULL, n_threads, out_xN, out_V, out_xbar0);
+}
+
+int orc_paths_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
+                 const orc_decisions* dec, int32_t n_threads, double* out_xN, double* out_V,
+                 double* out_xbar0)
+{
     int st = orc_check(sf, op);
     if (st != ORC_OK) return st;
+    if (orc_check_decisions(dec) != ORC_OK) return ORC_EINVAL;
     if (path_begin < 0 || m < 0) return ORC_EINVAL;
     if (m == 0) return ORC_OK;
     if (n_threads < 1) n_threads = 1;
@@ -468,6 +523,7 @@ int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, i
     for (int32_t k = 0; k < n_threads; ++k) {
         jobs[k].sf = sf;
         jobs[k].op = op;
+        jobs[k].dec = dec;
         jobs[k].first = path_begin;
         jobs[k].begin = path_begin + m * k / n_threads;
         jobs[k].end = path_begin + m * (k + 1) / n_threads;

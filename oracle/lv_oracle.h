@@ -53,6 +53,19 @@ typedef struct {
     double dsigma_dS;
 } orc_point;
 
+/* Decisions taken from outside for listed paths / steps (see lv_oracle.c):
+ * payoff indicator per path; spot-cell code 2 i + inside per (path, step).
+ * Both lists sorted ascending (by path, then step). */
+typedef struct {
+    const int64_t* itm_path;
+    const int8_t* itm_val;
+    int64_t n_itm;
+    const int64_t* cell_path;
+    const int32_t* cell_step;
+    const int32_t* cell_code;
+    int64_t n_cell;
+} orc_decisions;
+
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double orc_uniform(uint32_t w);
 void orc_counter(uint32_t block, uint64_t path, uint32_t stream_id, uint32_t ctr[4]);
@@ -63,11 +76,14 @@ void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p);
 int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
             int want_greeks, double kink_tol, int32_t n_threads, double* out);
 int orc_run_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
-               int want_greeks, double kink_tol, const int64_t* ov_path, const int8_t* ov_itm,
-               int64_t n_ov, int32_t n_threads, double* out);
+               int want_greeks, double kink_tol, const orc_decisions* dec, int32_t n_threads,
+               double* out);
 int orc_finalize(const double* sums, int64_t n_paths, double S0, int64_t IJ, double* res);
 int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
               int32_t n_threads, double* out_xN, double* out_V, double* out_xbar0);
+int orc_paths_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
+                 const orc_decisions* dec, int32_t n_threads, double* out_xN, double* out_V,
+                 double* out_xbar0);
 int orc_bump(const orc_surface* sf, const orc_option* op, int64_t n_paths, double eps_sigma,
              double eps_S0, int32_t n_threads, double* out_vega, double* out_delta);
 

@@ -45,16 +45,20 @@ def stale() -> bool:
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra: tuple = ()) -> str:
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, extra: tuple = (), out: str = LIB) -> str:
+    """Compile to ``out`` (default: the package's library); ``extra`` nvcc
+    flags and another ``out`` build a separate copy, with its own object
+    directory, without touching the package's library."""
+    if out == LIB and not force and not stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    objdir = BUILD if out == LIB else os.path.join(os.path.dirname(os.path.abspath(out)), "_obj")
+    os.makedirs(objdir, exist_ok=True)
+    os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -67,13 +71,13 @@ def build(force: bool = False, verbose: bool = False, extra: tuple = ()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, len(sources()))) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + ".tmp"
+    tmp = out + ".tmp"
     r = subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", *objs, "-o", tmp],
                        capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

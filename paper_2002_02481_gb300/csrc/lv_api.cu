@@ -123,7 +123,7 @@ struct Plan {
     int block = 256, k = 8, bps = 1, grid = 1;
     size_t smem = 0;
     int n_tiles = 0, n_ck = 0, row_words = 0, n_chunks = 0;
-    size_t off_counter = 0, off_part = 0, off_chunks = 0, off_ckpt = 0, total = 0;
+    size_t off_counter = 0, off_part = 0, off_chunks = 0, off_wrows = 0, off_l1 = 0, off_ckpt = 0, total = 0;
 };
 
 size_t round_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
@@ -131,13 +131,13 @@ size_t round_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps)
 {
     *block = h->cfg_block ? h->cfg_block : 256;
-    *k = greeks ? (h->cfg_k ? h->cfg_k : 8) : 4;
+    *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
     const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks);
     if (smem > 200 * 1024)
         return fail(LV_EINVAL, "grid and time table do not fit in shared memory (" +
                                std::to_string(smem) + " bytes)");
     int occ = 0;
-    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, smem, &occ));
+    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, h->acc_mode, smem, &occ));
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
     *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
     return LV_OK;
@@ -148,20 +148,26 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps);
     if (st != LV_OK) return st;
     p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks);
-    const int64_t tiles = (n_paths + p->block - 1) / p->block;
-    if (tiles > (int64_t)0x7fffffff) return fail(LV_EINVAL, "too many paths for one call");
+    const int warps = p->block / 32;
+    const int64_t tiles = (n_paths + 31) / 32;            // warps claim tiles of 32 paths
     p->n_tiles = (int)tiles;
+    const int64_t want_blocks = (tiles + warps - 1) / warps;
     const int64_t slots = (int64_t)p->bps * h->num_sms;
-    p->grid = (int)(tiles < slots ? tiles : slots);
+    p->grid = (int)(want_blocks < slots ? want_blocks : slots);
     if (p->grid < 1) p->grid = 1;
     p->n_ck = greeks ? (n_steps + p->k - 1) / p->k : 0;
-    p->row_words = greeks ? 3 + h->Je * h->I : 3;   // price-only rows hold the scalars
+    const size_t nIJ = (size_t)h->Je * h->I;
+    p->row_words = greeks ? 3 + (int)nIJ : 3;             // price-only rows hold the scalars
     p->n_chunks = lv::finalize_chunks(p->grid);
+    const size_t total_warps = (size_t)p->grid * warps;
     size_t o = 0;
     p->off_counter = o; o += 256;
     p->off_part = o;    o = round_up(o + sizeof(double) * (size_t)p->grid * p->row_words, 256);
     p->off_chunks = o;  o = round_up(o + sizeof(double) * (size_t)p->n_chunks * p->row_words, 256);
-    p->off_ckpt = o;    o = round_up(o + sizeof(float) * (size_t)p->n_ck * p->grid * p->block, 256);
+    p->off_wrows = o;   if (greeks) o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
+    p->off_l1 = o;      if (greeks) o = round_up(o + sizeof(float) * (size_t)p->grid * nIJ, 256);
+    p->off_ckpt = o;
+    o = round_up(o + sizeof(float) * (size_t)p->n_ck * total_warps * lv::ring_slots_per_warp(), 256);
     p->total = o;
     return LV_OK;
 }
@@ -199,6 +205,10 @@ struct McCall {
     float* dbg_xN = nullptr;
     float* dbg_V = nullptr;
     float* dbg_xbar0 = nullptr;
+    int* dbg_ev = nullptr;
+    unsigned long long* dbg_ev_count = nullptr;
+    int64_t dbg_ev_cap = 0;
+    double dbg_band = 0.0;
 };
 
 lv::McParams base_params(const lv_surface_s* h, const McCall& c)
@@ -244,6 +254,7 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     if (c.path_begin < 0 || c.path_begin + c.n_paths > LV_MAX_PATH_INDEX)
         return fail(LV_EINVAL, "path indices must lie in [0, 2^48)");
     if (c.stream_id >= 65536u) return fail(LV_EINVAL, "stream_id must be < 65536");
+    if (c.n_paths > 0x7fffffffLL) return fail(LV_EINVAL, "one call handles at most 2^31 - 1 paths");
     Plan p;
     st = make_plan(h, c.n_steps, c.n_paths, c.greeks, &p);
     if (st != LV_OK) return st;
@@ -255,11 +266,18 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     P.tile_counter = reinterpret_cast<unsigned int*>(base + p.off_counter);
     P.partials = reinterpret_cast<double*>(base + p.off_part);
     P.row_words = p.row_words;
+    P.warp_rows = reinterpret_cast<double*>(base + p.off_wrows);
+    P.l1 = reinterpret_cast<float*>(base + p.off_l1);
     P.ckpt = reinterpret_cast<float*>(base + p.off_ckpt);
     P.n_ck = p.n_ck;
+    P.flush_every = 8;
     P.dbg_xN = c.dbg_xN;
     P.dbg_V = c.dbg_V;
     P.dbg_xbar0 = c.dbg_xbar0;
+    P.dbg_ev = c.dbg_ev;
+    P.dbg_ev_count = c.dbg_ev_count;
+    P.dbg_ev_cap = c.dbg_ev_cap;
+    P.dbg_band = (float)c.dbg_band;
     if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
     LV_CUDA(lv::launch_mc(P, p.grid, p.block, p.k, c.greeks, p.smem, h->stream));
     if (h->ev_end) LV_CUDA(cudaEventRecord(h->ev_end, h->stream));
@@ -269,7 +287,6 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     F.row_words = p.row_words;
     F.I = h->I;
     F.J = h->J;
-    F.acc_mode = c.greeks ? h->acc_mode : 0;
     F.n_paths = c.n_paths;
     F.S0 = c.S0;
     F.want_sums = c.want_sums ? 1 : 0;
@@ -433,8 +450,8 @@ lv_status lv_set_accumulation(lv_surface_t h, int32_t mode)
 lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks_per_sm)
 {
     if (!h) return fail(LV_EINVAL, "handle is NULL");
-    if (block != 0 && (block < 64 || block > 512 || block % 32 != 0))
-        return fail(LV_EINVAL, "block must be 0 or a multiple of 32 in [64, 512]");
+    if (block != 0 && (block < 64 || block > 256 || block % 32 != 0))
+        return fail(LV_EINVAL, "block must be 0 or a multiple of 32 in [64, 256]");
     if (k != 0 && k != 4 && k != 8 && k != 16 && k != 32)
         return fail(LV_EINVAL, "k must be 0, 4, 8, 16 or 32");
     if (blocks_per_sm < 0) return fail(LV_EINVAL, "blocks_per_sm must be >= 0");
@@ -525,35 +542,117 @@ lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, doubl
     return run_mc(h, c);
 }
 
+lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                         int64_t n_paths, uint64_t seed, double eps, double* out_price,
+                         double* out_delta, double* out_vega)
+{
+    if (!h || !out_price || !out_delta || !out_vega) return fail(LV_EINVAL, "NULL argument");
+    lv_status st = check_option(S0, r, K, T, n_steps);
+    if (st != LV_OK) return st;
+    if (!is_finite(eps) || !(eps > 0.0)) return fail(LV_EINVAL, "eps must be finite and > 0");
+    if (n_paths < 1 || n_paths > LV_MAX_PATH_INDEX) return fail(LV_EINVAL, "n_paths out of range");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    const int IJ = h->I * h->J;
+    const int block = 256;
+    const int row_words = 2 + IJ;
+    const int n_scen = 3 + 2 * IJ;
+    const int M = lv::bump_slots_per_thread();
+    const int n_groups = (n_scen + M - 1) / M;
+    const size_t smem = lv::bump_smem_bytes(h->I, h->Je, n_steps, row_words);
+    if (smem > 200 * 1024) return fail(LV_EINVAL, "grid too large for the bump kernel's shared memory");
+    int bps = 0;
+    LV_CUDA(lv::bump_occupancy(block, smem, &bps));
+    if (bps < 1) return fail(LV_EINVAL, "bump launch shape does not fit on an SM");
+    const int64_t tiles = (n_paths + block - 1) / block;
+    const int64_t items = tiles * n_groups;
+    if (items > (int64_t)0x7fffffff) return fail(LV_EINVAL, "too many paths x scenarios for one call");
+    const int64_t slots = (int64_t)bps * h->num_sms;
+    const int grid = (int)(items < slots ? items : slots);
+    const int nch = lv::bump_chunks(grid);
+    size_t o = 256;
+    const size_t off_part = o;
+    o = round_up(o + sizeof(double) * (size_t)grid * row_words, 256);
+    const size_t off_chunks = o;
+    o = round_up(o + sizeof(double) * (size_t)nch * row_words, 256);
+    st = ensure_scratch(h, o);
+    if (st != LV_OK) return st;
+    char* base = static_cast<char*>(h->d_scratch);
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, false, false, h->d_res};
+    lv::BumpParams B{};
+    B.mc = base_params(h, c);
+    B.mc.n_tiles = (int)tiles;
+    B.mc.tile_counter = reinterpret_cast<unsigned int*>(base);
+    const double eps_S = 1e-4 * S0;
+    B.n_scen = n_scen;
+    B.n_groups = n_groups;
+    B.eps_half = (float)(0.5 * eps);
+    B.x0_up = (float)std::log(S0 + 0.5 * eps_S);
+    B.x0_dn = (float)std::log(S0 - 0.5 * eps_S);
+    B.partials = reinterpret_cast<double*>(base + off_part);
+    B.row_words = row_words;
+    if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
+    LV_CUDA(lv::launch_bump(B, grid, block, smem, h->stream));
+    if (h->ev_end) LV_CUDA(cudaEventRecord(h->ev_end, h->stream));
+    LV_CUDA(lv::launch_bump_finalize(B.partials, grid, row_words, reinterpret_cast<double*>(base + off_chunks),
+                                     IJ, n_paths, eps, eps_S, h->d_res, B.mc.tile_counter, h->stream));
+    st = fetch_result(h);
+    if (st != LV_OK) return st;
+    *out_price = h->h_res[LV_OUT_PRICE];
+    *out_delta = h->h_res[LV_OUT_DELTA];
+    std::memcpy(out_vega, h->h_res + LV_OUT_VEGA, sizeof(double) * (size_t)IJ);
+    return LV_OK;
+}
+
 lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
                          uint64_t seed, int64_t path_begin, int64_t m, float* out_xN, float* out_V,
-                         float* out_xbar0)
+                         float* out_xbar0, double node_band, int64_t ev_cap, int32_t* out_ev,
+                         int64_t* out_n_ev)
 {
     if (!h) return fail(LV_EINVAL, "handle is NULL");
     if (m < 1 || m > (int64_t)1 << 26) return fail(LV_EINVAL, "m must be in [1, 2^26]");
+    if (ev_cap < 0 || ev_cap > ((int64_t)1 << 28)) return fail(LV_EINVAL, "ev_cap must be in [0, 2^28]");
+    if (ev_cap > 0 && !out_ev) return fail(LV_EINVAL, "out_ev is NULL");
+    if (!is_finite(node_band) || node_band < 0.0) return fail(LV_EINVAL, "node_band must be >= 0");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
-    float* d = nullptr;
-    if (cudaMalloc(&d, sizeof(float) * 3 * (size_t)m) != cudaSuccess) {
+    const size_t f_bytes = sizeof(float) * 3 * (size_t)m;
+    const size_t e_bytes = sizeof(int) * 3 * (size_t)ev_cap;
+    char* d = nullptr;
+    if (cudaMalloc(&d, f_bytes + e_bytes + 16) != cudaSuccess) {
         cudaGetLastError();
         return fail(LV_ENOMEM, "cannot allocate the per-path buffers");
     }
+    float* df = reinterpret_cast<float*>(d);
+    unsigned long long* dcount = reinterpret_cast<unsigned long long*>(d + f_bytes + e_bytes);
     McCall c{S0, r, K, T, n_steps, path_begin, m, seed, 0u, true, false, h->d_res};
-    c.dbg_xN = d;
-    c.dbg_V = d + m;
-    c.dbg_xbar0 = d + 2 * m;
-    lv_status st = run_mc(h, c);
+    c.dbg_xN = df;
+    c.dbg_V = df + m;
+    c.dbg_xbar0 = df + 2 * m;
+    c.dbg_ev = reinterpret_cast<int*>(d + f_bytes);
+    c.dbg_ev_count = dcount;
+    c.dbg_ev_cap = ev_cap;
+    c.dbg_band = node_band;
+    lv_status st = LV_OK;
+    cudaError_t e = cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), h->stream);
+    if (e != cudaSuccess) st = fail(LV_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    if (st == LV_OK) st = run_mc(h, c);
     if (st == LV_OK) {
         std::vector<float> hb(3 * (size_t)m);
-        cudaError_t e = cudaMemcpyAsync(hb.data(), d, sizeof(float) * 3 * (size_t)m,
-                                        cudaMemcpyDeviceToHost, h->stream);
+        unsigned long long n_ev = 0;
+        e = cudaMemcpyAsync(hb.data(), df, f_bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&n_ev, dcount, sizeof(n_ev), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        const int64_t n_copy = (int64_t)n_ev < ev_cap ? (int64_t)n_ev : ev_cap;
+        if (e == cudaSuccess && n_copy > 0)
+            e = cudaMemcpy(out_ev, d + f_bytes, sizeof(int) * 3 * (size_t)n_copy, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             st = fail(LV_ECUDA, std::string("per-path copy: ") + cudaGetErrorString(e));
         } else {
             if (out_xN) std::memcpy(out_xN, hb.data(), sizeof(float) * m);
             if (out_V) std::memcpy(out_V, hb.data() + m, sizeof(float) * m);
             if (out_xbar0) std::memcpy(out_xbar0, hb.data() + 2 * m, sizeof(float) * m);
+            if (out_n_ev) *out_n_ev = (int64_t)n_ev;
         }
     }
     cudaStreamSynchronize(h->stream);

@@ -45,18 +45,26 @@ struct McParams {
     long long n_paths;
 
     // work decomposition and scratch
-    int n_tiles;           // ceil(n_paths / blockDim.x)
+    int n_tiles;           // ceil(n_paths / 32): tiles of 32 paths claimed by warps
     unsigned int* tile_counter;   // zero before the launch, reset by the finalize
-    double* partials;      // [gridDim.x][row_words] per-block level-2 accumulators
-    int row_words;         // 3 + Je * I
-    float* ckpt;           // [n_ck][gridDim.x * blockDim.x] checkpoints of x
+    double* partials;      // [gridDim.x][row_words] per-block binary64 rows
+    int row_words;         // 3 + Je * I (adjoint) or 3 (price only)
+    double* warp_rows;     // [gridDim.x * warps][Je * I] per-warp level-2 rows
+    float* l1;             // [gridDim.x][Je * I] per-block level-1 binary32 buckets
+    float* ckpt;           // [n_ck][gridDim.x * warps * ring_slots_per_warp()] checkpoints of x
     int n_ck;
-    int acc_mode;          // 0 FP64, 1 Kahan
+    int flush_every;       // reverse batches between level-1 -> level-2 drains
+    int acc_mode;          // 0 binary64, 1 Kahan binary32
 
-    // optional per-path outputs (debug entry point)
+    // per-path outputs and near-node decision log (debug entry point only;
+    // dbg_xN != null selects the logging instantiation)
     float* dbg_xN;
     float* dbg_V;
     float* dbg_xbar0;
+    int* dbg_ev;                        // [dbg_ev_cap][3]: path - path_begin, step, 2 i + inside
+    unsigned long long* dbg_ev_count;
+    long long dbg_ev_cap;
+    float dbg_band;                     // relative distance to a node that is logged
 };
 
 struct FinalizeParams {
@@ -64,7 +72,6 @@ struct FinalizeParams {
     int G;                 // rows
     int row_words;
     int I, J;
-    int acc_mode;
     long long n_paths;
     double S0;
     int want_sums;         // 1: raw sums, 0: price / delta / stderr / vega
@@ -75,12 +82,33 @@ struct FinalizeParams {
 
 int finalize_chunks(int G);
 
+// Batched central bump-and-reprice (lv_bump.cu).
+struct BumpParams {
+    McParams mc;           // grid, option, random numbers, path tiles, tile counter
+    int n_scen;            // 3 + 2 I J
+    int n_groups;          // ceil(n_scen / slots per thread)
+    float eps_half;        // eps / 2 on sigma
+    float x0_up, x0_dn;    // ln(S0 + eps_S / 2), ln(S0 - eps_S / 2)
+    double* partials;      // [gridDim.x][row_words] per-block binary64 rows
+    int row_words;         // 2 + I J
+};
+
+size_t bump_smem_bytes(int I, int Je, int N, int row_words);
+int bump_slots_per_thread();
+int bump_chunks(int G);
+cudaError_t bump_occupancy(int block, size_t smem, int* blocks_per_sm);
+cudaError_t launch_bump(const BumpParams& b, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_bump_finalize(const double* partials, int G, int row_words, double* chunks, int IJ,
+                                 long long n_paths, double eps, double eps_S, double* out,
+                                 unsigned int* tile_counter, cudaStream_t s);
+
 size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks);
 
 // Launchers; return cudaSuccess or the launch error.
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
-cudaError_t mc_occupancy(int block, int k, bool greeks, size_t smem, int* blocks_per_sm);
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, size_t smem, int* blocks_per_sm);
+int ring_slots_per_warp();
 
 }  // namespace lv

@@ -1,26 +1,39 @@
-// lv_kernels.cu -- the Monte Carlo price / pathwise-adjoint kernel and the
+// lv_kernels.cu -- the Monte Carlo price / pathwise-adjoint kernels and the
 // fixed-order finalize (arXiv 2002.02481, Sec. III, IV-A..IV-D).
 //
-// One persistent kernel per call. Each block claims tiles of blockDim.x
-// consecutive paths from a global counter. Per tile:
-//   1. forward: every thread simulates one path from x_0 = ln S0 with
-//      normals generated in registers, storing x every KCK steps (the
-//      checkpoints, in an L2-resident scratch slot owned by the thread);
-//   2. payoff and terminal adjoint xbar_N = e^{-rT} 1{phi(S_N-K)>0} phi S_N;
-//   3. compaction: paths with xbar_N = 0 have a zero adjoint everywhere, so
-//      only the others are queued (block-wide, in path order) and the
-//      reverse sweep runs on a dense set of threads;
-//   4. reverse sweep: per checkpoint segment, from last to first, recompute
-//      KCK steps (same Philox counters) keeping h_n = d x_{n+1} / d sigma_n,
-//      g_n = h_n S_n d sigma/d S, the cell and the weight in registers, then
-//      walk them backwards: sigma_bar_n = xbar_{n+1} h_n, xbar_n =
-//      xbar_{n+1} (1 + g_n), and scatter sigma_bar_n to the four corner
-//      buckets;
-//   5. bucket accumulation: per-thread run-length sums while the cell is
-//      unchanged (level 0), shared-memory binary32 atomics (level 1), and
-//      after every tile a per-block binary64 (or Kahan binary32) row in
-//      global memory (level 2). A separate fixed-order binary64 reduction
-//      over blocks (level 3) produces the outputs.
+// Adjoint kernel: persistent, warp-centric, no block-wide barrier in its
+// main loop. Every warp repeatedly either
+//   (F) claims a tile of 32 consecutive paths from a global counter and runs
+//       their forward passes: normals generated in registers, log-Euler
+//       steps under the bilinear grid staged in shared memory, x stored every
+//       KCK steps (the checkpoints) into one of kRing groups of 32 slots
+//       owned by the warp; payoff and terminal adjoint
+//       xbar_N = e^{-rT} 1{phi(S_N - K) > 0} phi S_N; the paths with a
+//       nonzero xbar_N (all others have a zero adjoint everywhere) are
+//       appended to a per-warp FIFO in shared memory; or
+//   (R) takes up to 32 queued paths and runs their reverse sweeps: per
+//       checkpoint segment, last to first, recompute KCK steps from the
+//       checkpoint with the same Philox counters keeping h_n = d x_{n+1} /
+//       d sigma_n, g_n = h_n S_n d sigma / d S, the cell and the weight in
+//       registers, then walk back: sigma_bar_n = xbar_{n+1} h_n,
+//       xbar_n = xbar_{n+1} (1 + g_n), sigma_bar_n spread over the four
+//       corner buckets with the bilinear weights.
+// A reverse batch runs when 32 paths are queued, when the oldest queued
+// path's checkpoint slots are about to be reused by the next forward tile,
+// and at the end; so the reverse sweeps run on full warps.
+//
+// Bucket accumulation: run-length sums in registers while the cell is
+// unchanged (level 0); binary32 reductions (red.global.add.f32, resolved in
+// L2 without a retry loop) into a per-block bucket array in global memory
+// (level 1); every few batches a warp drains that array (atomicExch) into a
+// row it owns, binary64 or Kahan-compensated binary32 (level 2); at the end
+// each block folds its warps' rows into one binary64 row, and a separate
+// fixed-order binary64 reduction over blocks gives the outputs (level 3).
+//
+// The DBG instantiation additionally writes per-path results and logs
+// every forward step whose spot lies within a relative band of its cell's
+// nodes, with the cell and inside-grid decision taken there, so that a
+// test can hand the same decisions to the binary64 oracle.
 #include <math.h>
 
 #include "lv_device.cuh"
@@ -29,28 +42,29 @@ namespace lv {
 
 namespace {
 
-constexpr int kMaxWarps = 16;   // blockDim.x <= 512
+constexpr int kRing = 4;       // checkpoint slot groups of 32 per warp
+constexpr int kQueue = 64;     // per-warp FIFO capacity (entries)
+constexpr int kMaxWarps = 8;   // blockDim.x <= 256
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 struct SmemLayout {
-    size_t tab, sig, node, ab, bk, qown, qxb, wcnt, red, tile, total;
+    size_t tab, sig, node, ab, qslot, qrel, qxb, red, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks)
 {
+    const int W = block / 32;
     SmemLayout L;
     size_t o = 0;
-    L.tab = o;  o += align16(sizeof(int2) * (size_t)N);
-    L.sig = o;  o += align16(sizeof(float) * (size_t)Je * I);
-    L.node = o; o += align16(sizeof(float) * (size_t)I);
-    L.ab = o;   o += align16(sizeof(float2) * (size_t)I);
-    L.bk = o;   if (greeks) o += align16(sizeof(float) * (size_t)Je * I);
-    L.qown = o; if (greeks) o += align16(sizeof(int) * (size_t)block);
-    L.qxb = o;  if (greeks) o += align16(sizeof(float) * (size_t)block);
-    L.wcnt = o; if (greeks) o += align16(sizeof(int) * kMaxWarps);
-    L.red = o;  o += align16(sizeof(double) * 3 * kMaxWarps);
-    L.tile = o; o += align16(sizeof(int) * 2);
+    L.tab = o;   o += align16(sizeof(int2) * (size_t)N);
+    L.sig = o;   o += align16(sizeof(float) * (size_t)Je * I);
+    L.node = o;  o += align16(sizeof(float) * (size_t)I);
+    L.ab = o;    o += align16(sizeof(float2) * (size_t)I);
+    L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
+    L.qrel = o;  if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
+    L.qxb = o;   if (greeks) o += align16(sizeof(float) * (size_t)W * kQueue);
+    L.red = o;   o += align16(sizeof(double) * 3 * kMaxWarps);
     L.total = o;
     return L;
 }
@@ -77,142 +91,186 @@ __device__ int2 time_cell(const McParams& P, int n)
     return make_int2(j * P.I, __float_as_int((float)v));
 }
 
-struct KahanF {
+// Level-2 accumulator of one value: binary64 or Kahan-compensated binary32.
+template <int ACC>
+struct Acc {
+    double d = 0.0;
     float s = 0.0f, c = 0.0f;
     __device__ __forceinline__ void add(float x)
     {
-        const float y = x - c;
-        const float t = s + y;
-        c = (t - s) - y;
-        s = t;
+        if (ACC == 1) {
+            const float y = x - c;
+            const float t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            d += (double)x;
+        }
     }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    __device__ __forceinline__ double value() const
+    {
+        return ACC == 1 ? (double)s - (double)c : d;
+    }
 };
 
-// Per-thread accumulation of the payoff, its square and xbar_0 across the
-// paths a thread handles (level 2 of the scalars).
-struct ScalarAcc {
-    double V = 0.0, V2 = 0.0, X = 0.0;
-    KahanF kV, kV2, kX;
-    __device__ __forceinline__ void add_V(float v, int mode)
-    {
-        if (mode == LV_ACC_KAHAN_DEV) { kV.add(v); kV2.add(v * v); }
-        else { V += (double)v; V2 += (double)v * (double)v; }
-    }
-    __device__ __forceinline__ void add_X(float x, int mode)
-    {
-        if (mode == LV_ACC_KAHAN_DEV) kX.add(x);
-        else X += (double)x;
-    }
-    __device__ __forceinline__ void get(int mode, double& a, double& b, double& c) const
-    {
-        if (mode == LV_ACC_KAHAN_DEV) { a = kV.value(); b = kV2.value(); c = kX.value(); }
-        else { a = V; b = V2; c = X; }
-    }
-    static constexpr int LV_ACC_KAHAN_DEV = 1;
-};
-
-template <int KCK, bool GREEKS>
-__global__ void __launch_bounds__(512) mc_kernel(const __grid_constant__ McParams P)
+__device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* smem, const SmemLayout& L)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int B = blockDim.x;
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, GREEKS);
+    const int B = blockDim.x, tid = threadIdx.x;
     int2* s_tab = reinterpret_cast<int2*>(smem + L.tab);
     float* s_sig = reinterpret_cast<float*>(smem + L.sig);
     float* s_node = reinterpret_cast<float*>(smem + L.node);
     float2* s_ab = reinterpret_cast<float2*>(smem + L.ab);
-    float* s_bk = reinterpret_cast<float*>(smem + L.bk);
-    int* s_qown = reinterpret_cast<int*>(smem + L.qown);
-    float* s_qxb = reinterpret_cast<float*>(smem + L.qxb);
-    int* s_wcnt = reinterpret_cast<int*>(smem + L.wcnt);
-    double* s_red = reinterpret_cast<double*>(smem + L.red);
-    int* s_tile = reinterpret_cast<int*>(smem + L.tile);
-
-    const int nIJ = P.Je * P.I;
-    for (int e = tid; e < nIJ; e += B) s_sig[e] = P.sig[e];
+    for (int e = tid; e < P.Je * P.I; e += B) s_sig[e] = P.sig[e];
     for (int e = tid; e < P.I; e += B) s_node[e] = P.node[e];
     for (int e = tid; e < P.I - 1; e += B) s_ab[e] = P.ab[e];
     for (int n = tid; n < P.N; n += B) s_tab[n] = time_cell(P, n);
-    double* row = P.partials + (size_t)blockIdx.x * P.row_words;
-    if (GREEKS) {
-        for (int e = tid; e < nIJ; e += B) s_bk[e] = 0.0f;
-        for (int e = tid; e < P.row_words; e += B) row[e] = 0.0;
-    }
-    if (tid == 0) s_tile[0] = (int)atomicAdd(P.tile_counter, 1u);
-    __syncthreads();
+}
 
-    SmemGrid g{ s_tab, s_sig, s_node, s_ab };
-    const int nseg = (P.N + KCK - 1) / KCK;
-    const size_t cks = (size_t)gridDim.x * B;           // checkpoint stride
-    float* const ck_base = P.ckpt + (size_t)blockIdx.x * B;
-    ScalarAcc acc;
-
-    int it = 0;
-    int tile = s_tile[0];
-    while (tile < P.n_tiles) {
-        const long long first = (long long)tile * B;     // relative to path_begin
-        const bool active = first + tid < P.n_paths;
-        float xbarN = 0.0f;
-        if (active) {
-            const unsigned long long p = (unsigned long long)(P.path_begin + first + tid);
-            const uint32_t c1 = (uint32_t)p;
-            const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
-            float x = P.x0;
-            float z[4];
-            for (int m = 0; m < nseg; ++m) {
-                if (GREEKS) ck_base[(size_t)m * cks + tid] = x;
+// Block sum of three per-thread binary64 values into row[0..2] (fixed order).
+__device__ __forceinline__ void block_scalars(double a, double b, double c, double* s_red, double* row)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-                for (int q = 0; q < KCK; ++q) {
-                    const int n = m * KCK + q;
-                    if (n < P.N) {
-                        if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
-                        const int2 tb = g.tab[n];
-                        const StepEval e = eval_sigma<false>(P, g, x, tb.x, __int_as_float(tb.y));
-                        x = euler_step(P, x, e.sigma, z[q & 3]);
-                    }
-                }
-            }
-            const float SN = expf(x);
-            const float itm = P.phi * (SN - P.K);
-            const float V = itm > 0.0f ? P.disc * itm : 0.0f;
-            xbarN = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
-            acc.add_V(V, P.acc_mode);
-            if (P.dbg_xN) {
-                const long long r = first + tid;
-                P.dbg_xN[r] = x;
-                P.dbg_V[r] = V;
-                P.dbg_xbar0[r] = 0.0f;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+    }
+    if (lane == 0) {
+        s_red[3 * warp + 0] = a;
+        s_red[3 * warp + 1] = b;
+        s_red[3 * warp + 2] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sa = 0.0, sb = 0.0, sc = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sa += s_red[3 * w + 0];
+            sb += s_red[3 * w + 1];
+            sc += s_red[3 * w + 2];
+        }
+        row[0] = sa;
+        row[1] = sb;
+        row[2] = sc;
+    }
+}
+
+__device__ __forceinline__ int claim_tile(unsigned int* counter)
+{
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = (int)atomicAdd(counter, 1u);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+// Near-node decision log of the DBG instantiation: (path, step, 2 i + inside).
+__device__ __forceinline__ void log_cell_decision(const McParams& P, const SmemGrid& g, const StepEval& e,
+                                                  long long rel, int n)
+{
+    const float lo = g.node[e.i], hi = g.node[e.i + 1];
+    if (fabsf(e.S - lo) <= P.dbg_band * lo || fabsf(e.S - hi) <= P.dbg_band * hi) {
+        const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
+        const unsigned long long k = atomicAdd(P.dbg_ev_count, 1ull);
+        if (k < (unsigned long long)P.dbg_ev_cap) {
+            P.dbg_ev[3 * k + 0] = (int)rel;
+            P.dbg_ev[3 * k + 1] = n;
+            P.dbg_ev[3 * k + 2] = 2 * e.i + (inside ? 1 : 0);
+        }
+    }
+}
+
+// Forward pass of one path from x0; checkpoints every KCK steps when STORE.
+template <int KCK, bool STORE, bool DBG>
+__device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
+                                              float* ck, size_t cks, long long rel)
+{
+    float x = P.x0;
+    float z[4];
+    const int nseg = (P.N + KCK - 1) / KCK;
+    for (int m = 0; m < nseg; ++m) {
+        if (STORE) ck[(size_t)m * cks] = x;
+#pragma unroll
+        for (int q = 0; q < KCK; ++q) {
+            const int n = m * KCK + q;
+            if (n < P.N) {
+                if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
+                const int2 tb = g.tab[n];
+                const StepEval e = eval_sigma<false>(P, g, x, tb.x, __int_as_float(tb.y));
+                if (DBG) log_cell_decision(P, g, e, rel, n);
+                x = euler_step(P, x, e.sigma, z[q & 3]);
             }
         }
-        if (GREEKS) {
-            // block-wide compaction of the paths with a nonzero adjoint, in path order
-            const bool live = xbarN != 0.0f;
-            const unsigned bal = __ballot_sync(0xffffffffu, live);
-            if (lane == 0) s_wcnt[warp] = __popc(bal);
-            __syncthreads();
-            int off = 0, total = 0;
-            const int nw = B >> 5;
-            for (int w = 0; w < nw; ++w) {
-                const int c = s_wcnt[w];
-                off += (w < warp) ? c : 0;
-                total += c;
-            }
-            if (live) {
-                const int idx = off + __popc(bal & ((1u << lane) - 1u));
-                s_qown[idx] = tid;
-                s_qxb[idx] = xbarN;
-            }
-            __syncthreads();
-            if (tid < total) {
-                const int owner = s_qown[tid];
-                float xbar = s_qxb[tid];
-                const unsigned long long p = (unsigned long long)(P.path_begin + first + owner);
+    }
+    return x;
+}
+
+template <int ACC>
+__device__ __forceinline__ void drain_buckets(float* l1, int nIJ, double* wrow)
+{
+    const int lane = threadIdx.x & 31;
+    for (int e = lane; e < nIJ; e += 32) {
+        if (l1[e] == 0.0f) continue;            // a skipped bucket is drained later
+        const float v = atomicExch(&l1[e], 0.0f);
+        if (ACC == 1) {
+            float2* k = reinterpret_cast<float2*>(wrow) + e;
+            float2 p = *k;
+            const float y = v - p.y;
+            const float t = p.x + y;
+            p.y = (t - p.x) - y;
+            p.x = t;
+            *k = p;
+        } else {
+            wrow[e] += (double)v;
+        }
+    }
+}
+
+template <int KCK, int ACC, bool DBG>
+__global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__ McParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B = blockDim.x, W = B >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true);
+    stage_grid(P, smem, L);
+    float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);    // this block's level-1 buckets
+    int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQueue;
+    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
+    float* q_xb = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
+    double* s_red = reinterpret_cast<double*>(smem + L.red);
+    const int nIJ = P.Je * P.I;
+    for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
+    const int wid = blockIdx.x * W + warp;                    // global warp id
+    double* wrow = P.warp_rows + (size_t)wid * nIJ;           // this warp's level-2 row
+    for (int e = lane; e < nIJ; e += 32) wrow[e] = 0.0;       // (also zero as a float2 pair)
+    __syncthreads();
+
+    const SmemGrid g{ reinterpret_cast<const int2*>(smem + L.tab), reinterpret_cast<const float*>(smem + L.sig),
+                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
+    const int nseg = (P.N + KCK - 1) / KCK;
+    const size_t cks = (size_t)gridDim.x * W * kRing * 32;   // checkpoint stride
+    float* const ckw = P.ckpt + (size_t)wid * kRing * 32;     // this warp's slots
+
+    Acc<ACC> aV, aV2, aX;
+    int q_head = 0, q_count = 0, batches = 0;
+    unsigned fwd_count = 0;
+    int tile = claim_tile(P.tile_counter);
+
+    while (true) {
+        const int g_next = (int)(fwd_count % kRing);
+        const bool more = tile < P.n_tiles;
+        const bool reuse = more && q_count > 0 && (q_slot[q_head] >> 5) == g_next;
+        if (q_count >= 32 || (!more && q_count > 0) || reuse) {
+            // ---------------- reverse batch over up to 32 queued paths
+            const int nb = min(32, q_count);
+            if (lane < nb) {
+                const int e = (q_head + lane) & (kQueue - 1);
+                const int slot = q_slot[e];
+                const long long rel = q_rel[e];
+                float xbar = q_xb[e];
+                const unsigned long long p = (unsigned long long)(P.path_begin + rel);
                 const uint32_t c1 = (uint32_t)p;
                 const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
-                const float* ck = ck_base + owner;
+                const float* ck = ckw + slot;
                 int cur = -1;
                 float A = 0.0f, AU = 0.0f, Bs = 0.0f, BU = 0.0f;
                 float z[4];
@@ -226,13 +284,13 @@ __global__ void __launch_bounds__(512) mc_kernel(const __grid_constant__ McParam
                         if (n < P.N) {
                             if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
                             const int2 tb = g.tab[n];
-                            const StepEval e = eval_sigma<true>(P, g, x, tb.x, __int_as_float(tb.y));
-                            const float h = fmaf(P.sqdt, z[q & 3], -e.sigma * P.dt);
+                            const StepEval ev = eval_sigma<true>(P, g, x, tb.x, __int_as_float(tb.y));
+                            const float h = fmaf(P.sqdt, z[q & 3], -ev.sigma * P.dt);
                             hq[q] = h;
-                            gq[q] = h * (e.S * e.slope);
-                            uq[q] = e.u;
-                            iq[q] = e.i;
-                            x = euler_step(P, x, e.sigma, z[q & 3]);
+                            gq[q] = h * (ev.S * ev.slope);
+                            uq[q] = ev.u;
+                            iq[q] = ev.i;
+                            x = euler_step(P, x, ev.sigma, z[q & 3]);
                         }
                     }
 #pragma unroll
@@ -246,10 +304,10 @@ __global__ void __launch_bounds__(512) mc_kernel(const __grid_constant__ McParam
                             xbar = fmaf(xbar, gq[q], xbar);
                             if (key != cur) {
                                 if (cur >= 0) {
-                                    atomicAdd(&s_bk[cur], A - AU);
-                                    atomicAdd(&s_bk[cur + 1], AU);
-                                    atomicAdd(&s_bk[cur + P.I], Bs - BU);
-                                    atomicAdd(&s_bk[cur + P.I + 1], BU);
+                                    atomicAdd(&l1[cur], A - AU);
+                                    atomicAdd(&l1[cur + 1], AU);
+                                    atomicAdd(&l1[cur + P.I], Bs - BU);
+                                    atomicAdd(&l1[cur + P.I + 1], BU);
                                 }
                                 cur = key;
                                 A = AU = Bs = BU = 0.0f;
@@ -264,67 +322,104 @@ __global__ void __launch_bounds__(512) mc_kernel(const __grid_constant__ McParam
                     }
                 }
                 if (cur >= 0) {
-                    atomicAdd(&s_bk[cur], A - AU);
-                    atomicAdd(&s_bk[cur + 1], AU);
-                    atomicAdd(&s_bk[cur + P.I], Bs - BU);
-                    atomicAdd(&s_bk[cur + P.I + 1], BU);
+                    atomicAdd(&l1[cur], A - AU);
+                    atomicAdd(&l1[cur + 1], AU);
+                    atomicAdd(&l1[cur + P.I], Bs - BU);
+                    atomicAdd(&l1[cur + P.I + 1], BU);
                 }
-                acc.add_X(xbar, P.acc_mode);
-                if (P.dbg_xN) P.dbg_xbar0[first + owner] = xbar;
+                aX.add(xbar);
+                if (DBG) P.dbg_xbar0[rel] = xbar;
+            }
+            q_head = (q_head + nb) & (kQueue - 1);
+            q_count -= nb;
+            __syncwarp();
+            if (++batches % P.flush_every == 0) drain_buckets<ACC>(l1, nIJ, wrow);
+            continue;
+        }
+        if (!more) break;
+
+        // ---------------- forward tile of 32 paths into slot group g_next
+        const long long rel = (long long)tile * 32 + lane;
+        const bool active = rel < P.n_paths;
+        const int slot = g_next * 32 + lane;
+        float xbarN = 0.0f;
+        if (active) {
+            const unsigned long long p = (unsigned long long)(P.path_begin + rel);
+            const uint32_t c1 = (uint32_t)p;
+            const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
+            const float x = forward_path<KCK, true, DBG>(P, g, c1, c2, ckw + slot, cks, rel);
+            const float SN = expf(x);
+            const float itm = P.phi * (SN - P.K);
+            const float V = itm > 0.0f ? P.disc * itm : 0.0f;
+            xbarN = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
+            aV.add(V);
+            aV2.add(V * V);
+            if (DBG) {
+                P.dbg_xN[rel] = x;
+                P.dbg_V[rel] = V;
+                P.dbg_xbar0[rel] = 0.0f;
             }
         }
-        if (tid == 0) s_tile[(it + 1) & 1] = (int)atomicAdd(P.tile_counter, 1u);
-        __syncthreads();
-        if (GREEKS) {
-            // level 2: this tile's buckets into the block's row, then clear them
-            if (P.acc_mode == 1) {
-                float2* krow = reinterpret_cast<float2*>(row + 3);
-                for (int e = tid; e < nIJ; e += B) {
-                    float2 k = krow[e];
-                    const float y = s_bk[e] - k.y;
-                    const float t = k.x + y;
-                    k.y = (t - k.x) - y;
-                    k.x = t;
-                    krow[e] = k;
-                    s_bk[e] = 0.0f;
-                }
-            } else {
-                for (int e = tid; e < nIJ; e += B) {
-                    row[3 + e] += (double)s_bk[e];
-                    s_bk[e] = 0.0f;
-                }
-            }
+        const bool live = xbarN != 0.0f;
+        const unsigned bal = __ballot_sync(0xffffffffu, live);
+        if (live) {
+            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
+            q_slot[e] = slot;
+            q_rel[e] = (int)rel;
+            q_xb[e] = xbarN;
         }
-        ++it;
-        tile = s_tile[it & 1];
+        q_count += __popc(bal);
+        ++fwd_count;
+        __syncwarp();
+        tile = claim_tile(P.tile_counter);
     }
 
-    // block reduction of the scalar sums (binary64, fixed order over warps)
-    double a, b, c;
-    acc.get(P.acc_mode, a, b, c);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) {
-        s_red[3 * warp + 0] = a;
-        s_red[3 * warp + 1] = b;
-        s_red[3 * warp + 2] = c;
-    }
+    // fold: remaining level-1 buckets and every warp row of this block into
+    // the block's binary64 row (after the barrier nothing adds any more)
     __syncthreads();
-    if (tid == 0) {
-        double sa = 0.0, sb = 0.0, sc = 0.0;
-        for (int w = 0; w < (B >> 5); ++w) {
-            sa += s_red[3 * w + 0];
-            sb += s_red[3 * w + 1];
-            sc += s_red[3 * w + 2];
+    double* row = P.partials + (size_t)blockIdx.x * P.row_words;
+    const double* rows0 = P.warp_rows + (size_t)blockIdx.x * W * nIJ;
+    for (int e = tid; e < nIJ; e += B) {
+        double s = (double)l1[e];
+        for (int w = 0; w < W; ++w) {
+            if (ACC == 1) {
+                const float2 k = reinterpret_cast<const float2*>(rows0 + (size_t)w * nIJ)[e];
+                s += (double)k.x - (double)k.y;
+            } else {
+                s += rows0[(size_t)w * nIJ + e];
+            }
         }
-        row[0] = sa;
-        row[1] = sb;
-        row[2] = sc;
+        row[3 + e] = s;
     }
+    block_scalars(aV.value(), aV2.value(), aX.value(), s_red, row);
+}
+
+template <int ACC>
+__global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ McParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, blockDim.x, false);
+    stage_grid(P, smem, L);
+    __syncthreads();
+    const SmemGrid g{ reinterpret_cast<const int2*>(smem + L.tab), reinterpret_cast<const float*>(smem + L.sig),
+                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
+    const int lane = threadIdx.x & 31;
+    Acc<ACC> aV, aV2;
+    for (int tile = claim_tile(P.tile_counter); tile < P.n_tiles; tile = claim_tile(P.tile_counter)) {
+        const long long rel = (long long)tile * 32 + lane;
+        if (rel < P.n_paths) {
+            const unsigned long long p = (unsigned long long)(P.path_begin + rel);
+            const uint32_t c1 = (uint32_t)p;
+            const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
+            const float x = forward_path<4, false, false>(P, g, c1, c2, nullptr, 0, rel);
+            const float itm = P.phi * (expf(x) - P.K);
+            const float V = itm > 0.0f ? P.disc * itm : 0.0f;
+            aV.add(V);
+            aV2.add(V * V);
+        }
+    }
+    double* s_red = reinterpret_cast<double*>(smem + L.red);
+    block_scalars(aV.value(), aV2.value(), 0.0, s_red, P.partials + (size_t)blockIdx.x * P.row_words);
 }
 
 // Level 3, stage 1: rows [chunk * RCH, (chunk + 1) * RCH) summed in order,
@@ -332,21 +427,14 @@ __global__ void __launch_bounds__(512) mc_kernel(const __grid_constant__ McParam
 constexpr int kRowsPerChunk = 32;
 
 __global__ void reduce_rows_kernel(const double* __restrict__ partials, int G, int row_words,
-                                   int acc_mode, double* __restrict__ chunks)
+                                   double* __restrict__ chunks)
 {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= row_words) return;
     const int r0 = blockIdx.y * kRowsPerChunk;
     const int r1 = min(G, r0 + kRowsPerChunk);
     double s = 0.0;
-    if (acc_mode == 1 && col >= 3) {
-        for (int r = r0; r < r1; ++r) {
-            const float2 k = reinterpret_cast<const float2*>(partials + (size_t)r * row_words)[col];
-            s += (double)k.x - (double)k.y;
-        }
-    } else {
-        for (int r = r0; r < r1; ++r) s += partials[(size_t)r * row_words + col];
-    }
+    for (int r = r0; r < r1; ++r) s += partials[(size_t)r * row_words + col];
     chunks[(size_t)blockIdx.y * row_words + col] = s;
 }
 
@@ -368,7 +456,7 @@ __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks,
             double sv2 = 0.0;
             for (int c = 0; c < n_chunks; ++c) sv2 += chunks[(size_t)c * row_words + 1];
             const double mean = s / P;
-            double var = n_paths > 1 ? (sv2 / P - mean * mean) * P / (P - 1.0) : 0.0;
+            const double var = n_paths > 1 ? (sv2 / P - mean * mean) * P / (P - 1.0) : 0.0;
             out[LV_OUT_PRICE_DEV] = mean;
             out[LV_OUT_STDERR_DEV] = var > 0.0 ? sqrt(var / P) : 0.0;
         } else if (col == 2) {
@@ -383,6 +471,46 @@ __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks,
     out[3 + i * J + j] = want_sums ? s : s / P;
 }
 
+template <typename K>
+cudaError_t set_smem_attr(K kernel)
+{
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+template <int KCK, int ACC, bool DBG>
+cudaError_t launch_adjoint(const McParams& p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = set_smem_attr(adjoint_kernel<KCK, ACC, DBG>);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    adjoint_kernel<KCK, ACC, DBG><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int ACC>
+cudaError_t launch_price(const McParams& p, int grid, int block, size_t smem, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = set_smem_attr(price_kernel<ACC>);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    price_kernel<ACC><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
+{
+    cudaError_t e = set_smem_attr(kernel);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kernel, block, smem);
+}
+
 }  // namespace
 
 size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks)
@@ -390,50 +518,39 @@ size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks)
     return smem_layout(I, Je, N, block, greeks).total;
 }
 
-template <int KCK, bool GREEKS>
-static cudaError_t launch_one(const McParams& p, int grid, int block, size_t smem, cudaStream_t s)
-{
-    static bool configured = false;   // per instantiation; the library is single-device per process
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(mc_kernel<KCK, GREEKS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    mc_kernel<KCK, GREEKS><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <int KCK, bool GREEKS>
-static cudaError_t occupancy_one(int block, size_t smem, int* bps)
-{
-    cudaError_t e = cudaFuncSetAttribute(mc_kernel<KCK, GREEKS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, mc_kernel<KCK, GREEKS>, block, smem);
-}
+int ring_slots_per_warp() { return kRing * 32; }
 
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s)
 {
-    if (!greeks) return launch_one<4, false>(p, grid, block, smem, s);
-    switch (k) {
-    case 4: return launch_one<4, true>(p, grid, block, smem, s);
-    case 8: return launch_one<8, true>(p, grid, block, smem, s);
-    case 16: return launch_one<16, true>(p, grid, block, smem, s);
-    case 32: return launch_one<32, true>(p, grid, block, smem, s);
+    const int acc = p.acc_mode;
+    if (!greeks) return acc ? launch_price<1>(p, grid, block, smem, s) : launch_price<0>(p, grid, block, smem, s);
+    if (p.dbg_xN) return launch_adjoint<4, 0, true>(p, grid, block, smem, s);
+    switch (k * 2 + acc) {
+    case 8: return launch_adjoint<4, 0, false>(p, grid, block, smem, s);
+    case 9: return launch_adjoint<4, 1, false>(p, grid, block, smem, s);
+    case 16: return launch_adjoint<8, 0, false>(p, grid, block, smem, s);
+    case 17: return launch_adjoint<8, 1, false>(p, grid, block, smem, s);
+    case 32: return launch_adjoint<16, 0, false>(p, grid, block, smem, s);
+    case 33: return launch_adjoint<16, 1, false>(p, grid, block, smem, s);
+    case 64: return launch_adjoint<32, 0, false>(p, grid, block, smem, s);
+    case 65: return launch_adjoint<32, 1, false>(p, grid, block, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t mc_occupancy(int block, int k, bool greeks, size_t smem, int* bps)
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, size_t smem, int* bps)
 {
-    if (!greeks) return occupancy_one<4, false>(block, smem, bps);
-    switch (k) {
-    case 4: return occupancy_one<4, true>(block, smem, bps);
-    case 8: return occupancy_one<8, true>(block, smem, bps);
-    case 16: return occupancy_one<16, true>(block, smem, bps);
-    case 32: return occupancy_one<32, true>(block, smem, bps);
+    if (!greeks) return acc ? occupancy(price_kernel<1>, block, smem, bps) : occupancy(price_kernel<0>, block, smem, bps);
+    switch (k * 2 + acc) {
+    case 8: return occupancy(adjoint_kernel<4, 0, false>, block, smem, bps);
+    case 9: return occupancy(adjoint_kernel<4, 1, false>, block, smem, bps);
+    case 16: return occupancy(adjoint_kernel<8, 0, false>, block, smem, bps);
+    case 17: return occupancy(adjoint_kernel<8, 1, false>, block, smem, bps);
+    case 32: return occupancy(adjoint_kernel<16, 0, false>, block, smem, bps);
+    case 33: return occupancy(adjoint_kernel<16, 1, false>, block, smem, bps);
+    case 64: return occupancy(adjoint_kernel<32, 0, false>, block, smem, bps);
+    case 65: return occupancy(adjoint_kernel<32, 1, false>, block, smem, bps);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -441,14 +558,13 @@ cudaError_t mc_occupancy(int block, int k, bool greeks, size_t smem, int* bps)
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s)
 {
     const int n_chunks = (f.G + kRowsPerChunk - 1) / kRowsPerChunk;
-    double* chunks = f.chunks;
     dim3 g1((f.row_words + 255) / 256, n_chunks);
-    reduce_rows_kernel<<<g1, 256, 0, s>>>(f.partials, f.G, f.row_words, f.acc_mode, chunks);
+    reduce_rows_kernel<<<g1, 256, 0, s>>>(f.partials, f.G, f.row_words, f.chunks);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    finalize_kernel<<<(f.row_words + 255) / 256, 256, 0, s>>>(chunks, n_chunks, f.row_words, f.I,
-                                                              f.J, f.n_paths, f.S0, f.want_sums,
-                                                              f.out, f.tile_counter);
+    finalize_kernel<<<(f.row_words + 255) / 256, 256, 0, s>>>(f.chunks, n_chunks, f.row_words, f.I, f.J,
+                                                              f.n_paths, f.S0, f.want_sums, f.out,
+                                                              f.tile_counter);
     return cudaGetLastError();
 }
 

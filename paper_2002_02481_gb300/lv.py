@@ -74,7 +74,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_price_greeks": [vp, d, d, d, d, i32, i64, u64, dp, dp, dp],
         "lv_price_greeks_device": [vp, d, d, d, d, i32, i64, u64, vp],
         "lv_price_greeks_sums_device": [vp, d, d, d, d, i32, i64, i64, u64, u32, vp],
-        "lv_debug_paths": [vp, d, d, d, d, i32, u64, i64, i64, fp, fp, fp],
+        "lv_debug_paths": [vp, d, d, d, d, i32, u64, i64, i64, fp, fp, fp, d, i64,
+                           c.POINTER(i32), c.POINTER(i64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -200,11 +201,22 @@ class Surface:
             self.h, S0, r, K, T, int(n_steps), int(path_begin), int(path_end), int(seed), int(stream_id),
             ctypes.c_void_p(d_sums_ptr)), "lv_price_greeks_sums_device")
 
-    def debug_paths(self, S0, r, K, T, n_steps, seed, path_begin, m):
+    def debug_paths(self, S0, r, K, T, n_steps, seed, path_begin, m, node_band=0.0, ev_cap=0):
+        """(x_N, V, xbar0) per path, plus the near-node decision log
+        (paths, steps, codes) when ev_cap > 0."""
         xN, V, xb = (np.zeros(m, dtype=np.float32) for _ in range(3))
-        _check(self.lib, self.lib.lv_debug_paths(self.h, S0, r, K, T, int(n_steps), int(seed), int(path_begin),
-                                                 int(m), _fp(xN), _fp(V), _fp(xb)), "lv_debug_paths")
-        return xN, V, xb
+        ev = np.zeros((max(ev_cap, 1), 3), dtype=np.int32)
+        n_ev = ctypes.c_int64(0)
+        _check(self.lib, self.lib.lv_debug_paths(
+            self.h, S0, r, K, T, int(n_steps), int(seed), int(path_begin), int(m), _fp(xN), _fp(V), _fp(xb),
+            float(node_band), int(ev_cap), ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+            ctypes.byref(n_ev)), "lv_debug_paths")
+        if ev_cap <= 0:
+            return xN, V, xb
+        if n_ev.value > ev_cap:
+            raise LVError(LV_EINTERNAL, "lv_debug_paths", f"decision log holds {ev_cap} < {n_ev.value} entries")
+        e = ev[:n_ev.value]
+        return xN, V, xb, (e[:, 0].astype(np.int64) + int(path_begin), e[:, 1].copy(), e[:, 2].copy())
 
     def bump_greeks(self, S0, r, K, T, n_steps, n_paths, seed, eps):
         p, d = ctypes.c_double(), ctypes.c_double()

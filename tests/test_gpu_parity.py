@@ -90,7 +90,7 @@ def test_large_grid_sample(lib):
             G.full_parity(surf, opt, lib, launch=(256, 32, 0), label="large"))
 
 
-@pytest.mark.parametrize("launch", [(128, 4, 0), (256, 8, 0), (512, 16, 0), (256, 32, 1), (64, 8, 2)])
+@pytest.mark.parametrize("launch", [(128, 4, 0), (256, 8, 0), (256, 16, 0), (256, 32, 1), (64, 8, 2)])
 def test_launch_shape_invariance(launch, lib):
     """Per-path arithmetic does not depend on the launch shape; results agree
     to reduction-order rounding."""

@@ -33,8 +33,10 @@ MUTANTS = {
                              "double s01 = (J > 1) ? sf->sigma[i * J + j] : 0.0;"),
     "cell rule strict": ("if (nodes[mid] <= x) lo = mid;", "if (nodes[mid] < x) lo = mid;"),
     "slope kept outside grid": ("if (inside)\n", "if (1)\n"),
-    "sigma at right point": ("        double t = (double)n * dt;\n        orc_sigma_eval(sf, exp(x[n]), t, &pt);",
-                             "        double t = (double)(n + 1) * dt;\n        orc_sigma_eval(sf, exp(x[n]), t, &pt);"),
+    "sigma at right point": ("        double t = (double)n * dt;\n        orc_sigma_decided(sf, exp(x[n]),",
+                             "        double t = (double)(n + 1) * dt;\n        orc_sigma_decided(sf, exp(x[n]),"),
+    "inside test drops the upper edge": ("int inside = (S >= sf->spot[0] && S <= sf->spot[I - 1]);",
+                                         "int inside = (S >= sf->spot[0]);"),
     "payoff sign": ("const double itm = (double)op->phi * (SN - op->K);",
                     "const double itm = (SN - op->K);"),
 }
