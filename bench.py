@@ -211,6 +211,12 @@ def run_ours(args):
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(lr) as clk:
+        # the sampler reads every 200 ms: keep the GPU loaded for 0.6 s first so that
+        # samples land on the same kind of load as the timed region that follows
+        t_end = time.perf_counter() + 0.6
+        while time.perf_counter() < t_end:
+            step()
+            torch.cuda.synchronize(dev)
         for _ in range(args.steps):
             flush.fill_(1)
             s0.record(stream)

@@ -54,11 +54,11 @@ struct lv_surface_s {
     int num_sms = 0;
     int I = 0, J = 0, Je = 0;
     std::vector<double> spot, time;
-    float* d_sig = nullptr;
+    float2* d_sig = nullptr;         // [Je][I-1] pairs (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j})
     float* d_node = nullptr;
     float2* d_ab = nullptr;
     double* d_tau = nullptr;
-    float* h_sig_stage = nullptr;    // pinned staging for sigma uploads
+    float2* h_sig_stage = nullptr;   // pinned staging for sigma uploads
     int log_uniform = 0;
     float cell_scale = 0.0f, cell_shift = 0.0f, s_lo = 0.0f, s_hi = 0.0f;
     int phi = 1;
@@ -84,13 +84,18 @@ lv_status check_sigma(const double* sigma, int64_t n)
     return LV_OK;
 }
 
-// sigma (spot-major, binary64) -> time-major binary32 rows, with row 0
-// repeated when the grid has a single time node.
-void pack_sigma(const lv_surface_s* h, const double* sigma, float* dst)
+// sigma (spot-major, binary64) -> time-major binary32 pairs per cell of a
+// time row: (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j}), the difference taken
+// in binary64; row 0 is repeated when the grid has a single time node.
+void pack_sigma(const lv_surface_s* h, const double* sigma, float2* dst)
 {
     for (int j = 0; j < h->Je; ++j) {
         const int jj = j < h->J ? j : h->J - 1;
-        for (int i = 0; i < h->I; ++i) dst[(size_t)j * h->I + i] = (float)sigma[(size_t)i * h->J + jj];
+        for (int i = 0; i + 1 < h->I; ++i) {
+            const double a = sigma[(size_t)i * h->J + jj];
+            const double b = sigma[(size_t)(i + 1) * h->J + jj];
+            dst[(size_t)j * (h->I - 1) + i] = make_float2((float)a, (float)(b - a));
+        }
     }
 }
 
@@ -128,24 +133,28 @@ struct Plan {
 
 size_t round_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
 
-lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps)
+// The per-path diagnostics kernel always runs checkpoints every 4 steps with
+// binary64 level 2 (per-path values do not depend on either).
+lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
+                        bool dbg = false)
 {
     *block = h->cfg_block ? h->cfg_block : 256;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
+    if (dbg) *k = 4;
     const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks);
     if (smem > 200 * 1024)
         return fail(LV_EINVAL, "grid and time table do not fit in shared memory (" +
                                std::to_string(smem) + " bytes)");
     int occ = 0;
-    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, h->acc_mode, smem, &occ));
+    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, smem, &occ));
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
     *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
     return LV_OK;
 }
 
-lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, Plan* p)
+lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, bool dbg, Plan* p)
 {
-    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps);
+    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg);
     if (st != LV_OK) return st;
     p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks);
     const int warps = p->block / 32;
@@ -214,7 +223,7 @@ struct McCall {
 lv::McParams base_params(const lv_surface_s* h, const McCall& c)
 {
     lv::McParams P{};
-    P.sig = h->d_sig;
+    P.sig2 = h->d_sig;
     P.node = h->d_node;
     P.ab = h->d_ab;
     P.tau = h->d_tau;
@@ -227,9 +236,11 @@ lv::McParams base_params(const lv_surface_s* h, const McCall& c)
     P.s_lo = h->s_lo;
     P.s_hi = h->s_hi;
     const double dt = c.T / (double)c.n_steps;
-    P.x0 = (float)std::log(c.S0);
-    P.rdt = (float)(c.r * dt);
-    P.hdt = (float)(0.5 * dt);
+    const double log2e = 1.4426950408889634;
+    P.x0 = (float)std::log2(c.S0);
+    P.rdt = (float)(log2e * c.r * dt);
+    P.hdt = (float)(log2e * 0.5 * dt);
+    P.sqdt2 = (float)(log2e * std::sqrt(dt));
     P.dt = (float)dt;
     P.sqdt = (float)std::sqrt(dt);
     P.K = (float)c.K;
@@ -256,7 +267,7 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     if (c.stream_id >= 65536u) return fail(LV_EINVAL, "stream_id must be < 65536");
     if (c.n_paths > 0x7fffffffLL) return fail(LV_EINVAL, "one call handles at most 2^31 - 1 paths");
     Plan p;
-    st = make_plan(h, c.n_steps, c.n_paths, c.greeks, &p);
+    st = make_plan(h, c.n_steps, c.n_paths, c.greeks, c.dbg_xN != nullptr, &p);
     if (st != LV_OK) return st;
     st = ensure_scratch(h, p.total);
     if (st != LV_OK) return st;
@@ -350,7 +361,7 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
     for (int i = 0; i < n_spot; ++i)
         dev = std::fmax(dev, std::fabs(std::log(spot_nodes[i]) - (l0 + i * dl)));
     h->log_uniform = dev <= 1e-6 * dl ? 1 : 0;
-    h->cell_scale = (float)(1.0 / dl);
+    h->cell_scale = (float)(std::log(2.0) / dl);   // index from y = log2 S
     h->cell_shift = (float)(-l0 / dl);
     h->s_lo = (float)spot_nodes[0];
     h->s_hi = (float)spot_nodes[n_spot - 1];
@@ -364,14 +375,14 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
     e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return bail(LV_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
 
-    const size_t nsig = (size_t)h->Je * h->I;
+    const size_t nsig = (size_t)h->Je * (h->I - 1);
     const size_t nres = 3 + (size_t)n_spot * n_time;
-    if (cudaMalloc(&h->d_sig, sizeof(float) * nsig) != cudaSuccess ||
+    if (cudaMalloc(&h->d_sig, sizeof(float2) * nsig) != cudaSuccess ||
         cudaMalloc(&h->d_node, sizeof(float) * n_spot) != cudaSuccess ||
         cudaMalloc(&h->d_ab, sizeof(float2) * n_spot) != cudaSuccess ||
         cudaMalloc(&h->d_tau, sizeof(double) * n_time) != cudaSuccess ||
         cudaMalloc(&h->d_res, sizeof(double) * nres) != cudaSuccess ||
-        cudaMallocHost(&h->h_sig_stage, sizeof(float) * nsig) != cudaSuccess ||
+        cudaMallocHost(&h->h_sig_stage, sizeof(float2) * nsig) != cudaSuccess ||
         cudaMallocHost(&h->h_res, sizeof(double) * nres) != cudaSuccess) {
         cudaGetLastError();
         return bail(LV_ENOMEM, "device or pinned allocation failed");
@@ -388,7 +399,7 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
         }
     }
     pack_sigma(h, sigma, h->h_sig_stage);
-    if (cudaMemcpy(h->d_sig, h->h_sig_stage, sizeof(float) * nsig, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (cudaMemcpy(h->d_sig, h->h_sig_stage, sizeof(float2) * nsig, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_node, node.data(), sizeof(float) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_ab, ab.data(), sizeof(float2) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_tau, time_nodes, sizeof(double) * n_time, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -418,7 +429,7 @@ lv_status lv_surface_set_sigma(lv_surface_t h, const double* sigma)
     // the staging buffer may still feed an earlier asynchronous copy
     LV_CUDA(cudaStreamSynchronize(h->stream));
     pack_sigma(h, sigma, h->h_sig_stage);
-    LV_CUDA(cudaMemcpyAsync(h->d_sig, h->h_sig_stage, sizeof(float) * (size_t)h->Je * h->I,
+    LV_CUDA(cudaMemcpyAsync(h->d_sig, h->h_sig_stage, sizeof(float2) * (size_t)h->Je * (h->I - 1),
                             cudaMemcpyHostToDevice, h->stream));
     return LV_OK;
 }
@@ -478,7 +489,7 @@ lv_status lv_get_launch(lv_surface_t h, int32_t n_steps, int32_t greeks, int32_t
     if (n_steps < 1 || n_steps > LV_MAX_STEPS) return fail(LV_EINVAL, "n_steps out of range");
     DeviceGuard g(h->device);
     int b = 0, kk = 0, bps = 0;
-    lv_status st = choose_launch(h, n_steps, greeks != 0, &b, &kk, &bps);
+    lv_status st = choose_launch(h, n_steps, greeks != 0, &b, &kk, &bps, false);
     if (st != LV_OK) return st;
     *block = b;
     *k = kk;
@@ -587,8 +598,8 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
     B.n_scen = n_scen;
     B.n_groups = n_groups;
     B.eps_half = (float)(0.5 * eps);
-    B.x0_up = (float)std::log(S0 + 0.5 * eps_S);
-    B.x0_dn = (float)std::log(S0 - 0.5 * eps_S);
+    B.x0_up = (float)std::log2(S0 + 0.5 * eps_S);
+    B.x0_dn = (float)std::log2(S0 - 0.5 * eps_S);
     B.partials = reinterpret_cast<double*>(base + off_part);
     B.row_words = row_words;
     if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
@@ -616,20 +627,24 @@ lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T
     if (!is_finite(node_band) || node_band < 0.0) return fail(LV_EINVAL, "node_band must be >= 0");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    // layout: [0, 256) the 64-bit log counter, then the per-path floats, then the
+    // log, each section 256-byte aligned
     const size_t f_bytes = sizeof(float) * 3 * (size_t)m;
     const size_t e_bytes = sizeof(int) * 3 * (size_t)ev_cap;
+    const size_t off_f = 256;
+    const size_t off_e = round_up(off_f + f_bytes, 256);
     char* d = nullptr;
-    if (cudaMalloc(&d, f_bytes + e_bytes + 16) != cudaSuccess) {
+    if (cudaMalloc(&d, off_e + e_bytes + 256) != cudaSuccess) {
         cudaGetLastError();
         return fail(LV_ENOMEM, "cannot allocate the per-path buffers");
     }
-    float* df = reinterpret_cast<float*>(d);
-    unsigned long long* dcount = reinterpret_cast<unsigned long long*>(d + f_bytes + e_bytes);
+    unsigned long long* dcount = reinterpret_cast<unsigned long long*>(d);
+    float* df = reinterpret_cast<float*>(d + off_f);
     McCall c{S0, r, K, T, n_steps, path_begin, m, seed, 0u, true, false, h->d_res};
     c.dbg_xN = df;
     c.dbg_V = df + m;
     c.dbg_xbar0 = df + 2 * m;
-    c.dbg_ev = reinterpret_cast<int*>(d + f_bytes);
+    c.dbg_ev = reinterpret_cast<int*>(d + off_e);
     c.dbg_ev_count = dcount;
     c.dbg_ev_cap = ev_cap;
     c.dbg_band = node_band;
@@ -645,7 +660,7 @@ lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         const int64_t n_copy = (int64_t)n_ev < ev_cap ? (int64_t)n_ev : ev_cap;
         if (e == cudaSuccess && n_copy > 0)
-            e = cudaMemcpy(out_ev, d + f_bytes, sizeof(int) * 3 * (size_t)n_copy, cudaMemcpyDeviceToHost);
+            e = cudaMemcpy(out_ev, d + off_e, sizeof(int) * 3 * (size_t)n_copy, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) {
             st = fail(LV_ECUDA, std::string("per-path copy: ") + cudaGetErrorString(e));
         } else {

@@ -35,33 +35,14 @@ __host__ __device__ inline BumpSmem bump_layout(int I, int Je, int N, int row_wo
 {
     BumpSmem L;
     size_t o = 0;
-    L.tab = o;  o += a16(sizeof(int2) * (size_t)N);
-    L.sig = o;  o += a16(sizeof(float) * (size_t)Je * I);
+    L.tab = o;  o += a16(sizeof(int4) * (size_t)N);
+    L.sig = o;  o += a16(sizeof(float2) * (size_t)Je * (I - 1));
     L.node = o; o += a16(sizeof(float) * (size_t)I);
     L.ab = o;   o += a16(sizeof(float2) * (size_t)I);
     L.acc = o;  o += a16(sizeof(double) * (size_t)row_words);
     L.tile = o; o += a16(sizeof(int) * 2);
     L.total = o;
     return L;
-}
-
-__device__ int2 bump_time_cell(const McParams& P, int n)
-{
-    const double t = (double)n * P.dt_d;
-    int j = 0;
-    double v = 0.0;
-    if (P.J > 1) {
-        int lo = 0, hi = P.J - 2;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.tau[mid] <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        j = lo;
-        v = (t - P.tau[j]) / (P.tau[j + 1] - P.tau[j]);
-        v = fmin(fmax(v, 0.0), 1.0);
-    }
-    return make_int2(j * P.I, __float_as_int((float)v));
 }
 
 constexpr int kM = 8;   // scenario slots per thread (even: pairs never split)
@@ -72,17 +53,17 @@ __global__ void __launch_bounds__(256) bump_kernel(const __grid_constant__ BumpP
     const McParams& P = Q.mc;
     const int B = blockDim.x, tid = threadIdx.x, lane = tid & 31;
     const BumpSmem L = bump_layout(P.I, P.Je, P.N, Q.row_words);
-    int2* s_tab = reinterpret_cast<int2*>(smem + L.tab);
-    float* s_sig = reinterpret_cast<float*>(smem + L.sig);
+    int4* s_tab = reinterpret_cast<int4*>(smem + L.tab);
+    float2* s_sig = reinterpret_cast<float2*>(smem + L.sig);
     float* s_node = reinterpret_cast<float*>(smem + L.node);
     float2* s_ab = reinterpret_cast<float2*>(smem + L.ab);
     double* s_acc = reinterpret_cast<double*>(smem + L.acc);
     int* s_tile = reinterpret_cast<int*>(smem + L.tile);
 
-    for (int e = tid; e < P.Je * P.I; e += B) s_sig[e] = P.sig[e];
+    for (int e = tid; e < P.Je * (P.I - 1); e += B) s_sig[e] = P.sig2[e];
     for (int e = tid; e < P.I; e += B) s_node[e] = P.node[e];
     for (int e = tid; e < P.I - 1; e += B) s_ab[e] = P.ab[e];
-    for (int n = tid; n < P.N; n += B) s_tab[n] = bump_time_cell(P, n);
+    for (int n = tid; n < P.N; n += B) s_tab[n] = step_time(P, n);
     for (int e = tid; e < Q.row_words; e += B) s_acc[e] = 0.0;
     if (tid == 0) s_tile[0] = (int)atomicAdd(P.tile_counter, 1u);
     __syncthreads();
@@ -130,15 +111,15 @@ __global__ void __launch_bounds__(256) bump_kernel(const __grid_constant__ BumpP
                 for (int q = 0; q < 4; ++q) {
                     const int n = n0 + q;
                     if (n >= P.N) break;
-                    const int2 tb = g.tab[n];
-                    const float v = __int_as_float(tb.y);
+                    const int4 tb = g.tab[n];
+                    const float v = __int_as_float(tb.w);
 #pragma unroll
                     for (int k = 0; k < kM; ++k) {
                         if (!used[k]) continue;
-                        StepEval e = eval_sigma<false>(P, g, x[k], tb.x, v);
+                        StepEval e = eval_sigma<false>(P, g, x[k], tb);
                         // time weight of the bumped node: column j (1 - v) or j + 1 (v)
-                        if (b_row[k] == tb.x || b_row[k] == tb.x + P.I) {
-                            const float wt = b_row[k] == tb.x ? 1.0f - v : v;
+                        if (b_row[k] == tb.z || b_row[k] == tb.z + P.I) {
+                            const float wt = b_row[k] == tb.z ? 1.0f - v : v;
                             const float ws = b_i[k] == e.i ? 1.0f - e.u : (b_i[k] == e.i + 1 ? e.u : 0.0f);
                             e.sigma = fmaf(b_h[k], ws * wt, e.sigma);
                         }
@@ -148,7 +129,7 @@ __global__ void __launch_bounds__(256) bump_kernel(const __grid_constant__ BumpP
             }
 #pragma unroll
             for (int k = 0; k < kM; ++k) {
-                const float itm = P.phi * (expf(x[k]) - P.K);
+                const float itm = P.phi * (exp2f(x[k]) - P.K);
                 V[k] = itm > 0.0f ? P.disc * itm : 0.0f;
             }
         } else {

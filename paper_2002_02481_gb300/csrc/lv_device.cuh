@@ -86,22 +86,45 @@ __device__ __forceinline__ void normals4(uint32_t blk, uint32_t c1, uint32_t c2,
     }
 }
 
+// Time data of step n: t_n = n dt, j_n = the largest j <= J-2 with
+// tau_j <= t_n, v_n = (t_n - tau_j) / (tau_{j+1} - tau_j) clamped to
+// [0, 1], decided in binary64. Returned as (j (I-1), (j+1) (I-1), j I, bits
+// of v): the rows of the sigma pairs for j and j + 1 and the bucket row.
+__device__ __forceinline__ int4 step_time(const McParams& P, int n)
+{
+    const double t = (double)n * P.dt_d;
+    int j = 0;
+    double v = 0.0;
+    if (P.J > 1) {
+        int lo = 0, hi = P.J - 2;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.tau[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        j = lo;
+        v = (t - P.tau[j]) / (P.tau[j + 1] - P.tau[j]);
+        v = fmin(fmax(v, 0.0), 1.0);
+    }
+    return make_int4(j * (P.I - 1), (j + 1) * (P.I - 1), j * P.I, __float_as_int((float)v));
+}
+
 // Shared-memory view of the grid for one block.
 struct SmemGrid {
-    const int2* tab;       // [N] per step: (j * I, bits of v)
-    const float* sig;      // [Je * I] time-major
+    const int4* tab;       // [N] per step: (j (I-1), (j+1) (I-1), j I, bits of v)
+    const float2* sig2;    // [Je][I-1]: (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j})
     const float* node;     // [I]
     const float2* ab;      // [I - 1]
 };
 
 // Spot cell: the largest i <= I-2 with s_i <= S. On log-uniform grids the
-// index comes from ln S directly (off by one only when S is within binary32
-// rounding of a node, where the clamped weight gives the same value); on
-// other grids a binary search over the nodes.
-__device__ __forceinline__ int spot_cell(const McParams& P, const SmemGrid& g, float x, float S)
+// index comes from y = log2 S directly (off by one only when S is within
+// binary32 rounding of a node, where the clamped weight gives the same
+// value); on other grids a binary search over the nodes.
+__device__ __forceinline__ int spot_cell(const McParams& P, const SmemGrid& g, float y, float S)
 {
     if (P.log_uniform) {
-        const int i = __float2int_rd(fmaf(x, P.cell_scale, P.cell_shift));
+        const int i = __float2int_rd(fmaf(y, P.cell_scale, P.cell_shift));
         return min(max(i, 0), P.I - 2);
     }
     int lo = 0, hi = P.I - 2;
@@ -114,7 +137,7 @@ __device__ __forceinline__ int spot_cell(const McParams& P, const SmemGrid& g, f
 }
 
 struct StepEval {
-    float S;       // e^{x_n}
+    float S;       // S_n = 2^{y_n}
     float sigma;   // sigma(S_n, t_n)
     float u;       // clamped spot weight
     int i;         // spot cell
@@ -123,33 +146,35 @@ struct StepEval {
 
 // Bilinear sigma at (S_n, t_n), Sec. IV-D; slope only when WANT_SLOPE.
 template <bool WANT_SLOPE>
-__device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid& g, float x,
-                                               int row, float v)
+__device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid& g, float y,
+                                               const int4& tb)
 {
     StepEval e;
-    e.S = ex2_approx(x * 1.4426950408889634f);
-    e.i = spot_cell(P, g, x, e.S);
+    e.S = ex2_approx(y);
+    e.i = spot_cell(P, g, y, e.S);
     const float2 ab = g.ab[e.i];
     e.u = __saturatef(fmaf(e.S, ab.x, ab.y));
-    const float* r0 = g.sig + row + e.i;
-    const float s00 = r0[0], s10 = r0[1], s01 = r0[P.I], s11 = r0[P.I + 1];
-    const float d0 = s10 - s00, d1 = s11 - s01;
-    const float top = fmaf(e.u, d0, s00);
-    const float bot = fmaf(e.u, d1, s01);
+    const float2 lo = g.sig2[tb.x + e.i];      // time row j:     sigma_{i,j},   its spot step
+    const float2 hi = g.sig2[tb.y + e.i];      // time row j + 1
+    const float v = __int_as_float(tb.w);
+    const float top = fmaf(e.u, lo.y, lo.x);
+    const float bot = fmaf(e.u, hi.y, hi.x);
     e.sigma = fmaf(v, bot - top, top);
     if (WANT_SLOPE) {
         const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
-        e.slope = inside ? fmaf(v, d1 - d0, d0) * ab.x : 0.0f;
+        e.slope = inside ? fmaf(v, hi.y - lo.y, lo.y) * ab.x : 0.0f;
     } else {
         e.slope = 0.0f;
     }
     return e;
 }
 
-// x_{n+1} = x_n + (r - sigma^2/2) dt + sigma sqrt(dt) Z  (Sec. IV-A, log-Euler)
-__device__ __forceinline__ float euler_step(const McParams& P, float x, float sigma, float z)
+// Log-Euler step (Sec. IV-A) on y = x log2(e):
+//   y_{n+1} = y_n + log2(e) [(r - sigma^2/2) dt + sigma sqrt(dt) Z]
+// with rdt = log2(e) r dt, hdt = log2(e) dt / 2, sqdt2 = log2(e) sqrt(dt).
+__device__ __forceinline__ float euler_step(const McParams& P, float y, float sigma, float z)
 {
-    return x + fmaf(sigma, P.sqdt * z, fmaf(-P.hdt * sigma, sigma, P.rdt));
+    return y + fmaf(sigma, P.sqdt2 * z, fmaf(-P.hdt * sigma, sigma, P.rdt));
 }
 
 }  // namespace lv

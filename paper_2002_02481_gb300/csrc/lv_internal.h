@@ -16,22 +16,24 @@ constexpr int LV_OUT_STDERR_DEV = 2;
 // __grid_constant__ kernel parameter.
 struct McParams {
     // grid (device copies, binary32)
-    const float* sig;      // [Je * I] time-major: sigma_ij at j * I + i; Je = max(J, 2)
+    const float2* sig2;    // [Je][I - 1] time-major pairs (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j});
+                           // Je = max(J, 2), row 1 repeats row 0 when J == 1
     const float* node;     // [I] spot nodes s_i
     const float2* ab;      // [I - 1] (1 / (s_{i+1} - s_i), -s_i / (s_{i+1} - s_i))
     const double* tau;     // [J] time nodes
     int I, J, Je;
     int log_uniform;       // spot nodes equally spaced in ln S
-    float cell_scale;      // 1 / d(ln s)
+    float cell_scale;      // ln 2 / d(ln s): cell index from y = log2 S
     float cell_shift;      // -ln(s_0) / d(ln s)
     float s_lo, s_hi;      // s_0, s_{I-1}
 
-    // option and scheme
-    float x0;              // ln S0
-    float rdt;             // r dt
-    float hdt;             // dt / 2
+    // option and scheme; the path state is y = log2 S
+    float x0;              // log2 S0
+    float rdt;             // log2(e) r dt
+    float hdt;             // log2(e) dt / 2
+    float sqdt2;           // log2(e) sqrt(dt)
     float dt;
-    float sqdt;            // sqrt(dt)
+    float sqdt;            // sqrt(dt) (natural units, for d x_{n+1} / d sigma_n)
     float K;
     float disc;            // e^{-rT}
     float phi;             // +1 call, -1 put
@@ -104,11 +106,13 @@ cudaError_t launch_bump_finalize(const double* partials, int G, int row_words, d
 
 size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks);
 
-// Launchers; return cudaSuccess or the launch error.
+// Launchers; return cudaSuccess or the launch error. An adjoint launch with
+// p.dbg_xN != null runs the logging instantiation with k = 4 and binary64
+// level 2 whatever k and p.acc_mode say: plan its scratch with k = 4.
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, size_t smem, int* blocks_per_sm);
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, size_t smem, int* blocks_per_sm);
 int ring_slots_per_warp();
 
 }  // namespace lv

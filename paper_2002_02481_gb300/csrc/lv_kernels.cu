@@ -57,8 +57,8 @@ __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int bloc
     const int W = block / 32;
     SmemLayout L;
     size_t o = 0;
-    L.tab = o;   o += align16(sizeof(int2) * (size_t)N);
-    L.sig = o;   o += align16(sizeof(float) * (size_t)Je * I);
+    L.tab = o;   o += align16(sizeof(int4) * (size_t)N);
+    L.sig = o;   o += align16(sizeof(float2) * (size_t)Je * (I - 1));
     L.node = o;  o += align16(sizeof(float) * (size_t)I);
     L.ab = o;    o += align16(sizeof(float2) * (size_t)I);
     L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
@@ -67,28 +67,6 @@ __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int bloc
     L.red = o;   o += align16(sizeof(double) * 3 * kMaxWarps);
     L.total = o;
     return L;
-}
-
-// (j_n * I, v_n) for step n: t_n = n dt, j_n = largest j <= J-2 with
-// tau_j <= t_n, v_n = (t_n - tau_j) / (tau_{j+1} - tau_j) clamped to [0, 1];
-// decided in binary64.
-__device__ int2 time_cell(const McParams& P, int n)
-{
-    const double t = (double)n * P.dt_d;
-    int j = 0;
-    double v = 0.0;
-    if (P.J > 1) {
-        int lo = 0, hi = P.J - 2;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.tau[mid] <= t) lo = mid;
-            else hi = mid - 1;
-        }
-        j = lo;
-        v = (t - P.tau[j]) / (P.tau[j + 1] - P.tau[j]);
-        v = fmin(fmax(v, 0.0), 1.0);
-    }
-    return make_int2(j * P.I, __float_as_int((float)v));
 }
 
 // Level-2 accumulator of one value: binary64 or Kahan-compensated binary32.
@@ -116,14 +94,14 @@ struct Acc {
 __device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* smem, const SmemLayout& L)
 {
     const int B = blockDim.x, tid = threadIdx.x;
-    int2* s_tab = reinterpret_cast<int2*>(smem + L.tab);
-    float* s_sig = reinterpret_cast<float*>(smem + L.sig);
+    int4* s_tab = reinterpret_cast<int4*>(smem + L.tab);
+    float2* s_sig = reinterpret_cast<float2*>(smem + L.sig);
     float* s_node = reinterpret_cast<float*>(smem + L.node);
     float2* s_ab = reinterpret_cast<float2*>(smem + L.ab);
-    for (int e = tid; e < P.Je * P.I; e += B) s_sig[e] = P.sig[e];
+    for (int e = tid; e < P.Je * (P.I - 1); e += B) s_sig[e] = P.sig2[e];
     for (int e = tid; e < P.I; e += B) s_node[e] = P.node[e];
     for (int e = tid; e < P.I - 1; e += B) s_ab[e] = P.ab[e];
-    for (int n = tid; n < P.N; n += B) s_tab[n] = time_cell(P, n);
+    for (int n = tid; n < P.N; n += B) s_tab[n] = step_time(P, n);
 }
 
 // Block sum of three per-thread binary64 values into row[0..2] (fixed order).
@@ -193,8 +171,8 @@ __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid&
             const int n = m * KCK + q;
             if (n < P.N) {
                 if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
-                const int2 tb = g.tab[n];
-                const StepEval e = eval_sigma<false>(P, g, x, tb.x, __int_as_float(tb.y));
+                const int4 tb = g.tab[n];
+                const StepEval e = eval_sigma<false>(P, g, x, tb);
                 if (DBG) log_cell_decision(P, g, e, rel, n);
                 x = euler_step(P, x, e.sigma, z[q & 3]);
             }
@@ -244,7 +222,7 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
     for (int e = lane; e < nIJ; e += 32) wrow[e] = 0.0;       // (also zero as a float2 pair)
     __syncthreads();
 
-    const SmemGrid g{ reinterpret_cast<const int2*>(smem + L.tab), reinterpret_cast<const float*>(smem + L.sig),
+    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab), reinterpret_cast<const float2*>(smem + L.sig),
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
     const int nseg = (P.N + KCK - 1) / KCK;
     const size_t cks = (size_t)gridDim.x * W * kRing * 32;   // checkpoint stride
@@ -274,8 +252,10 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
                 int cur = -1;
                 float A = 0.0f, AU = 0.0f, Bs = 0.0f, BU = 0.0f;
                 float z[4];
+                float x_next = ck[(size_t)(nseg - 1) * cks];
                 for (int m = nseg - 1; m >= 0; --m) {
-                    float x = ck[(size_t)m * cks];
+                    float x = x_next;
+                    if (m > 0) x_next = ck[(size_t)(m - 1) * cks];    // in flight during this segment
                     float hq[KCK], gq[KCK], uq[KCK];
                     int iq[KCK];
 #pragma unroll
@@ -283,8 +263,8 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
                         const int n = m * KCK + q;
                         if (n < P.N) {
                             if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
-                            const int2 tb = g.tab[n];
-                            const StepEval ev = eval_sigma<true>(P, g, x, tb.x, __int_as_float(tb.y));
+                            const int4 tb = g.tab[n];
+                            const StepEval ev = eval_sigma<true>(P, g, x, tb);
                             const float h = fmaf(P.sqdt, z[q & 3], -ev.sigma * P.dt);
                             hq[q] = h;
                             gq[q] = h * (ev.S * ev.slope);
@@ -297,20 +277,24 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
                     for (int q = KCK - 1; q >= 0; --q) {
                         const int n = m * KCK + q;
                         if (n < P.N) {
-                            const int2 tb = g.tab[n];
-                            const int key = tb.x + iq[q];
-                            const float v = __int_as_float(tb.y);
+                            const int4 tb = g.tab[n];
+                            const int key = tb.z + iq[q];
+                            const float v = __int_as_float(tb.w);
                             const float sbar = xbar * hq[q];
                             xbar = fmaf(xbar, gq[q], xbar);
                             if (key != cur) {
-                                if (cur >= 0) {
-                                    atomicAdd(&l1[cur], A - AU);
-                                    atomicAdd(&l1[cur + 1], AU);
-                                    atomicAdd(&l1[cur + P.I], Bs - BU);
-                                    atomicAdd(&l1[cur + P.I + 1], BU);
+                                {
+                                    if (cur >= 0) {
+                                        float* p0 = l1 + cur;
+                                        float* p1 = p0 + P.I;
+                                        atomicAdd(p0, A - AU);
+                                        atomicAdd(p0 + 1, AU);
+                                        atomicAdd(p1, Bs - BU);
+                                        atomicAdd(p1 + 1, BU);
+                                    }
+                                    A = AU = Bs = BU = 0.0f;
                                 }
                                 cur = key;
-                                A = AU = Bs = BU = 0.0f;
                             }
                             const float b = sbar * v;
                             const float a = sbar - b;
@@ -322,10 +306,12 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
                     }
                 }
                 if (cur >= 0) {
-                    atomicAdd(&l1[cur], A - AU);
-                    atomicAdd(&l1[cur + 1], AU);
-                    atomicAdd(&l1[cur + P.I], Bs - BU);
-                    atomicAdd(&l1[cur + P.I + 1], BU);
+                    float* p0 = l1 + cur;
+                    float* p1 = p0 + P.I;
+                    atomicAdd(p0, A - AU);
+                    atomicAdd(p0 + 1, AU);
+                    atomicAdd(p1, Bs - BU);
+                    atomicAdd(p1 + 1, BU);
                 }
                 aX.add(xbar);
                 if (DBG) P.dbg_xbar0[rel] = xbar;
@@ -348,14 +334,14 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
             const uint32_t c1 = (uint32_t)p;
             const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
             const float x = forward_path<KCK, true, DBG>(P, g, c1, c2, ckw + slot, cks, rel);
-            const float SN = expf(x);
+            const float SN = exp2f(x);
             const float itm = P.phi * (SN - P.K);
             const float V = itm > 0.0f ? P.disc * itm : 0.0f;
             xbarN = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
             aV.add(V);
             aV2.add(V * V);
             if (DBG) {
-                P.dbg_xN[rel] = x;
+                P.dbg_xN[rel] = x * 0.6931471805599453f;   // ln S_N
                 P.dbg_V[rel] = V;
                 P.dbg_xbar0[rel] = 0.0f;
             }
@@ -401,7 +387,7 @@ __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ M
     const SmemLayout L = smem_layout(P.I, P.Je, P.N, blockDim.x, false);
     stage_grid(P, smem, L);
     __syncthreads();
-    const SmemGrid g{ reinterpret_cast<const int2*>(smem + L.tab), reinterpret_cast<const float*>(smem + L.sig),
+    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab), reinterpret_cast<const float2*>(smem + L.sig),
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
     const int lane = threadIdx.x & 31;
     Acc<ACC> aV, aV2;
@@ -412,7 +398,7 @@ __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ M
             const uint32_t c1 = (uint32_t)p;
             const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
             const float x = forward_path<4, false, false>(P, g, c1, c2, nullptr, 0, rel);
-            const float itm = P.phi * (expf(x) - P.K);
+            const float itm = P.phi * (exp2f(x) - P.K);
             const float V = itm > 0.0f ? P.disc * itm : 0.0f;
             aV.add(V);
             aV2.add(V * V);
@@ -525,7 +511,10 @@ cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks
 {
     const int acc = p.acc_mode;
     if (!greeks) return acc ? launch_price<1>(p, grid, block, smem, s) : launch_price<0>(p, grid, block, smem, s);
-    if (p.dbg_xN) return launch_adjoint<4, 0, true>(p, grid, block, smem, s);
+    if (p.dbg_xN) {
+        if (k != 4) return cudaErrorInvalidValue;       // scratch must be planned with k = 4
+        return launch_adjoint<4, 0, true>(p, grid, block, smem, s);
+    }
     switch (k * 2 + acc) {
     case 8: return launch_adjoint<4, 0, false>(p, grid, block, smem, s);
     case 9: return launch_adjoint<4, 1, false>(p, grid, block, smem, s);
@@ -539,9 +528,10 @@ cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks
     }
 }
 
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, size_t smem, int* bps)
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, size_t smem, int* bps)
 {
     if (!greeks) return acc ? occupancy(price_kernel<1>, block, smem, bps) : occupancy(price_kernel<0>, block, smem, bps);
+    if (dbg) return occupancy(adjoint_kernel<4, 0, true>, block, smem, bps);
     switch (k * 2 + acc) {
     case 8: return occupancy(adjoint_kernel<4, 0, false>, block, smem, bps);
     case 9: return occupancy(adjoint_kernel<4, 1, false>, block, smem, bps);
