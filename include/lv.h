@@ -187,6 +187,29 @@ lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T
                          float* out_xN, float* out_V, float* out_xbar0,
                          double node_band, int64_t ev_cap, int32_t* out_ev, int64_t* out_n_ev);
 
+/* lv_price_greeks_device_noalloc -- lv_price_greeks_device for callers that
+ * cannot allocate device memory during the call: code running while someone
+ * else captures a CUDA graph, loops with a no-allocation rule, or runtimes
+ * that own every device allocation. The paper has no counterpart; it is a
+ * deployment variant of the same computation with the same results (up to
+ * reduction order) and the same output layout (LV_OUT_*), written to d_out
+ * (device memory owned by the caller) on the handle's stream, without
+ * synchronising.
+ *  - It calls no allocator: its scratch is a static 64 MiB device array that
+ *    every GPU loading this library keeps until the process exits. When a
+ *    launch at full width does not fit, fewer blocks run; a problem whose
+ *    single block does not fit (very large n_spot * n_time with many steps)
+ *    is rejected with LV_EINVAL and a message giving the bytes needed.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call on a device uses the same array, and the array keeps the
+ *    previous call's contents (the call clears what must start at zero):
+ *    calls that may overlap on the GPU race and give wrong results. Serialise
+ *    them, e.g. on one stream.
+ *  - n_paths in [1, 2^31 - 1]; other arguments as in lv_price_greeks. */
+lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, double r, double K, double T,
+                                         int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out);
+
 /* Thread-local description of the last failure on this host thread. */
 const char* lv_last_error(void);
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -676,3 +677,128 @@ lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of lv_price_greeks_device.
+//
+// Some callers cannot call cudaMalloc while they run: code inside a CUDA
+// graph being captured by someone else, a real-time loop with a no-allocation
+// rule, or an embedding runtime that owns every device allocation itself.
+// For them the adjoint can run on scratch memory the library reserves once
+// when its module is loaded: a file-scope __device__ array, kept by every
+// GPU that loads the library until the process exits.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)64 << 20;     // 64 MiB
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device. In host code the array's
+// name is only a host-side stand-in; its device address comes from
+// cudaGetSymbolAddress, taken once per device with that device current.
+void* g_static_addr[kMaxDevices] = {};
+std::mutex g_static_mu;
+
+lv_status static_scratch(int device, char** out)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(LV_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(LV_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+        g_static_addr[device] = p;
+    }
+    *out = static_cast<char*>(g_static_addr[device]);
+    return LV_OK;
+}
+
+// Scratch layout of one adjoint launch with `grid` blocks (same sections as
+// the allocating path); returns the bytes needed.
+size_t static_plan_bytes(const lv_surface_s* h, int grid, int block, int k, int n_steps, size_t* off_part,
+                         size_t* off_chunks, size_t* off_wrows, size_t* off_l1, size_t* off_ckpt)
+{
+    const size_t nIJ = (size_t)h->Je * h->I;
+    const size_t row_words = 3 + nIJ;
+    const size_t warps = (size_t)grid * (block / 32);
+    const size_t n_ck = (size_t)((n_steps + k - 1) / k);
+    size_t o = 256;                                               // [0, 256): tile counter
+    *off_part = o;   o = round_up(o + sizeof(double) * (size_t)grid * row_words, 256);
+    *off_chunks = o; o = round_up(o + sizeof(double) * (size_t)lv::finalize_chunks(grid) * row_words, 256);
+    *off_wrows = o;  o = round_up(o + sizeof(double) * warps * nIJ, 256);
+    *off_l1 = o;     o = round_up(o + sizeof(float) * (size_t)grid * nIJ, 256);
+    *off_ckpt = o;   o = round_up(o + sizeof(float) * n_ck * warps * lv::ring_slots_per_warp(), 256);
+    return o;
+}
+
+}  // namespace
+
+extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, double r, double K, double T,
+                                                    int32_t n_steps, int64_t n_paths, uint64_t seed,
+                                                    double* d_out)
+{
+    if (!h || !d_out) return fail(LV_EINVAL, "NULL argument");
+    lv_status st = check_option(S0, r, K, T, n_steps);
+    if (st != LV_OK) return st;
+    if (n_paths < 1 || n_paths > 0x7fffffffLL) return fail(LV_EINVAL, "n_paths must be in [1, 2^31 - 1]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    char* base = nullptr;
+    st = static_scratch(h->device, &base);
+    if (st != LV_OK) return st;
+
+    int block = 0, k = 0, bps = 0;
+    st = choose_launch(h, n_steps, true, &block, &k, &bps, false);
+    if (st != LV_OK) return st;
+    const int warps = block / 32;
+    const int64_t tiles = (n_paths + 31) / 32;
+    const int64_t want_blocks = (tiles + warps - 1) / warps;
+    const int64_t slots = (int64_t)bps * h->num_sms;
+    int grid = (int)(want_blocks < slots ? want_blocks : slots);
+    size_t off_part = 0, off_chunks = 0, off_wrows = 0, off_l1 = 0, off_ckpt = 0;
+    // fewer blocks until the launch fits in the static scratch
+    while (grid > 1 && static_plan_bytes(h, grid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
+                                         &off_ckpt) > kStaticScratchBytes)
+        grid = grid * 7 / 8;
+    const size_t need = static_plan_bytes(h, grid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
+                                          &off_ckpt);
+    if (need > kStaticScratchBytes)
+        return fail(LV_EINVAL, "grid of " + std::to_string(h->I) + " x " + std::to_string(h->J) + " nodes with " +
+                               std::to_string(n_steps) + " steps needs " + std::to_string(need) +
+                               " bytes of scratch for a single block; the static scratch holds " +
+                               std::to_string(kStaticScratchBytes));
+
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, d_out};
+    lv::McParams P = base_params(h, c);
+    P.n_tiles = (int)tiles;
+    P.tile_counter = reinterpret_cast<unsigned int*>(base);
+    P.partials = reinterpret_cast<double*>(base + off_part);
+    P.row_words = 3 + h->Je * h->I;
+    P.warp_rows = reinterpret_cast<double*>(base + off_wrows);
+    P.l1 = reinterpret_cast<float*>(base + off_l1);
+    P.ckpt = reinterpret_cast<float*>(base + off_ckpt);
+    P.n_ck = (n_steps + k - 1) / k;
+    P.flush_every = 8;
+    // the array keeps the previous call's contents: the tile counter must start at zero
+    // (every other section is written before it is read)
+    LV_CUDA(cudaMemsetAsync(P.tile_counter, 0, sizeof(unsigned int), h->stream));
+    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, block, true);
+    LV_CUDA(lv::launch_mc(P, grid, block, k, true, smem, h->stream));
+    lv::FinalizeParams F{};
+    F.partials = P.partials;
+    F.G = grid;
+    F.row_words = P.row_words;
+    F.I = h->I;
+    F.J = h->J;
+    F.n_paths = n_paths;
+    F.S0 = S0;
+    F.want_sums = 0;
+    F.chunks = reinterpret_cast<double*>(base + off_chunks);
+    F.out = d_out;
+    F.tile_counter = P.tile_counter;
+    LV_CUDA(lv::launch_finalize(F, h->stream));
+    return LV_OK;
+}
