@@ -160,6 +160,15 @@ lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, doubl
                                       int32_t n_steps, int64_t path_begin, int64_t path_end,
                                       uint64_t seed, uint32_t stream_id, double* d_sums);
 
+/* Turn raw sums (layout LV_SUM_*, e.g. the element-wise sum of the
+ * lv_price_greeks_sums_device results of disjoint path ranges, one per GPU)
+ * over n_paths paths into [3 + n_spot * n_time] doubles of layout LV_OUT_*
+ * (Sec. IV-C: means over paths; delta = mean d V / d x_0 / S0). d_sums and
+ * d_out are device memory owned by the caller; enqueued on the handle's
+ * stream without synchronising. */
+lv_status lv_finalize_sums_device(lv_surface_t h, const double* d_sums, int64_t n_paths, double S0,
+                                  double* d_out);
+
 /* lv_bump_greeks -- central bump-and-reprice (Sec. III), the baseline the
  * adjoint is measured against: every grid value sigma_ij +/- eps/2 and
  * S0 +/- eps_S/2 with eps_S = 1e-4 * S0, each pair of scenarios on the same

@@ -554,6 +554,18 @@ lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, doubl
     return run_mc(h, c);
 }
 
+lv_status lv_finalize_sums_device(lv_surface_t h, const double* d_sums, int64_t n_paths, double S0,
+                                  double* d_out)
+{
+    if (!h || !d_sums || !d_out) return fail(LV_EINVAL, "NULL argument");
+    if (n_paths < 1) return fail(LV_EINVAL, "n_paths must be >= 1");
+    if (!is_finite(S0) || !(S0 > 0.0)) return fail(LV_EINVAL, "S0 must be finite and > 0");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    LV_CUDA(lv::launch_finalize_sums(d_sums, h->I * h->J, n_paths, S0, d_out, h->stream));
+    return LV_OK;
+}
+
 lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
                          int64_t n_paths, uint64_t seed, double eps, double* out_price,
                          double* out_delta, double* out_vega)

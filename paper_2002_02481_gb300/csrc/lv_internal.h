@@ -83,6 +83,8 @@ struct FinalizeParams {
 };
 
 int finalize_chunks(int G);
+cudaError_t launch_finalize_sums(const double* sums, int IJ, long long n_paths, double S0, double* out,
+                                 cudaStream_t s);
 
 // Batched central bump-and-reprice (lv_bump.cu).
 struct BumpParams {

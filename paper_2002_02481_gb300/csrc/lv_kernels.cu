@@ -560,4 +560,31 @@ cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s)
 
 int finalize_chunks(int G) { return (G + kRowsPerChunk - 1) / kRowsPerChunk; }
 
+namespace {
+
+// Raw sums (LV_SUM_* layout, vega spot-major) -> price, delta, stderr, vega.
+__global__ void finalize_sums_kernel(const double* __restrict__ sums, int IJ, long long n_paths, double S0,
+                                     double* __restrict__ out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const double P = (double)n_paths;
+    if (e == 0) {
+        const double mean = sums[0] / P;
+        const double var = n_paths > 1 ? (sums[1] / P - mean * mean) * P / (P - 1.0) : 0.0;
+        out[LV_OUT_PRICE_DEV] = mean;
+        out[LV_OUT_STDERR_DEV] = var > 0.0 ? sqrt(var / P) : 0.0;
+        out[LV_OUT_DELTA_DEV] = sums[2] / (P * S0);
+    }
+    if (e < IJ) out[3 + e] = sums[3 + e] / P;
+}
+
+}  // namespace
+
+cudaError_t launch_finalize_sums(const double* sums, int IJ, long long n_paths, double S0, double* out,
+                                 cudaStream_t s)
+{
+    finalize_sums_kernel<<<(IJ + 255) / 256, 256, 0, s>>>(sums, IJ, n_paths, S0, out);
+    return cudaGetLastError();
+}
+
 }  // namespace lv

@@ -74,6 +74,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_price_greeks": [vp, d, d, d, d, i32, i64, u64, dp, dp, dp],
         "lv_price_greeks_device": [vp, d, d, d, d, i32, i64, u64, vp],
         "lv_price_greeks_sums_device": [vp, d, d, d, d, i32, i64, i64, u64, u32, vp],
+        "lv_finalize_sums_device": [vp, vp, i64, d, vp],
         "lv_debug_paths": [vp, d, d, d, d, i32, u64, i64, i64, fp, fp, fp, d, i64,
                            c.POINTER(i32), c.POINTER(i64)],
     }
@@ -200,6 +201,11 @@ class Surface:
         _check(self.lib, self.lib.lv_price_greeks_sums_device(
             self.h, S0, r, K, T, int(n_steps), int(path_begin), int(path_end), int(seed), int(stream_id),
             ctypes.c_void_p(d_sums_ptr)), "lv_price_greeks_sums_device")
+
+    def finalize_sums_device(self, d_sums_ptr: int, n_paths: int, S0: float, d_out_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_finalize_sums_device(self.h, ctypes.c_void_p(d_sums_ptr), int(n_paths),
+                                                          float(S0), ctypes.c_void_p(d_out_ptr)),
+               "lv_finalize_sums_device")
 
     def debug_paths(self, S0, r, K, T, n_steps, seed, path_begin, m, node_band=0.0, ev_cap=0):
         """(x_N, V, xbar0) per path, plus the near-node decision log

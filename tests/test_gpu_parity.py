@@ -129,6 +129,20 @@ def test_path_range_sharding(lib):
     # and the raw sums agree with the oracle's
     ref = oracle.run_sums(surf, opt, 0, P)
     assert abs(w[0] - ref[oracle.SUM_V]) <= 1e-5 * abs(ref[oracle.SUM_V])
+    # finalizing the combined sums on the device gives the single-call result
+    fin = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gs.finalize_sums_device((a + b).data_ptr(), P, opt.S0, fin.data_ptr())
+    one = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gs.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed, one.data_ptr())
+    torch.cuda.synchronize()
+    f, o = fin.cpu().numpy(), one.cpu().numpy()
+    assert abs(f[0] - o[0]) <= 1e-12 * abs(o[0]) and abs(f[1] - o[1]) <= 1e-9 * abs(o[1])
+    assert abs(f[2] - o[2]) <= 1e-9 * abs(o[2])
+    assert np.max(np.abs(f[3:] - o[3:])) <= 1e-6 * np.max(np.abs(o[3:]))
+    # and the sharded helper (one rank here) agrees too
+    from paper_2002_02481_gb300.shard import price_greeks_sharded
+    sh = price_greeks_sharded(gs, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed).cpu().numpy()
+    assert abs(sh[0] - o[0]) <= 1e-12 * abs(o[0]) and np.max(np.abs(sh[3:] - o[3:])) <= 1e-6 * np.max(np.abs(o[3:]))
 
 
 def test_device_output_matches_host_output(lib):
