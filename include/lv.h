@@ -111,7 +111,7 @@ lv_status lv_set_stream(lv_surface_t h, void* cuda_stream);
 /* LV_ACC_FP64 (default) or LV_ACC_KAHAN. */
 lv_status lv_set_accumulation(lv_surface_t h, int32_t mode);
 
-/* Launch shape: threads per block (64..256, multiple of 32), checkpoint
+/* Launch shape: threads per block (32..128, multiple of 32), checkpoint
  * interval k of the reverse sweep (4, 8, 16 or 32 steps) and resident
  * blocks per SM; 0 keeps the tuned or default value. Results do not depend
  * on it beyond reduction-order rounding. */
@@ -218,6 +218,58 @@ lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T
  *  - n_paths in [1, 2^31 - 1]; other arguments as in lv_price_greeks. */
 lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, double r, double K, double T,
                                          int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out);
+
+/* ---------------------------------------------------------------- book
+ * A book of European options on several local-vol grids, priced with all
+ * their deltas and vega buckets in one persistent launch (the Monte Carlo
+ * of Sec. IV-C over many instruments). Option o uses Philox stream
+ * stream_id (< 65536) and paths [0, n_paths): its results equal those of
+ * lv_price_greeks_sums_device(surface, S0, r, K, T, n_steps, 0, n_paths,
+ * seed, stream_id) finalized, up to reduction order. */
+typedef struct {
+    int32_t surface;     /* index into the surfaces given to lv_book_create */
+    int32_t phi;         /* +1 call, -1 put */
+    double K;            /* >= 0 */
+    double T;            /* > 0 */
+    int32_t n_steps;     /* 1 .. LV_MAX_STEPS */
+    int64_t n_paths;     /* 1 .. 2^31 - 1 */
+    uint32_t stream_id;  /* < 65536 */
+} lv_instrument;
+
+/* Build a book of 1 .. 65535 options: the grids of `surfaces` (all on the current device) are
+ * copied, so the surfaces may be destroyed afterwards; `insts` is copied.
+ * Outputs of lv_book_run are laid out per option, in the given order, as
+ * [3 + n_spot * n_time] doubles (LV_OUT_*); lv_book_output_offsets gives
+ * the first index of each. A tuned launch shape is read from the file named
+ * by the environment variable LV_TUNE_CACHE when it holds one for this GPU
+ * and book shape. */
+lv_status lv_book_create(const lv_surface_t* surfaces, int32_t n_surfaces, const lv_instrument* insts,
+                         int32_t n_insts, lv_book_t* out);
+void lv_book_destroy(lv_book_t b);
+
+/* offsets [n_insts + 1]: option o's results occupy [offsets[o], offsets[o+1]). */
+lv_status lv_book_output_offsets(lv_book_t b, int64_t* offsets);
+
+/* Stream for later runs (NULL: a stream the book creates; the legacy
+ * default stream cannot be captured into a graph). */
+lv_status lv_book_set_stream(lv_book_t b, void* cuda_stream);
+
+/* Run the book for (S0, r, seed): host output [offsets[n_insts]] doubles.
+ * The first run captures the whole run (parameter upload, zeroing, the
+ * persistent kernel, the finalize and the copy back) into a CUDA graph;
+ * later runs replay it. Synchronises the book's stream. */
+lv_status lv_book_run(lv_book_t b, double S0, double r, uint64_t seed, double* out);
+
+/* Same without graph or host copy: results to d_out (device, caller-owned),
+ * enqueued on the book's stream without synchronising. */
+lv_status lv_book_run_device(lv_book_t b, double S0, double r, uint64_t seed, double* d_out);
+
+/* Autotuner: times the book over launch shapes (threads per block,
+ * checkpoint interval, paths per work item), keeps the fastest, and appends
+ * it to the LV_TUNE_CACHE file when that variable is set. Outputs the
+ * chosen shape and its time in milliseconds (any pointer may be NULL). */
+lv_status lv_book_tune(lv_book_t b, double S0, double r, uint64_t seed, int32_t* out_block, int32_t* out_k,
+                       int32_t* out_item_paths, double* out_ms);
 
 /* Thread-local description of the last failure on this host thread. */
 const char* lv_last_error(void);

@@ -22,6 +22,12 @@ lv_status fail(lv_status s, const std::string& msg)
     return s;
 }
 
+}  // namespace
+
+lv_status lv::set_error(lv_status s, const std::string& msg) { return fail(s, msg); }
+
+namespace {
+
 #define LV_CUDA(call)                                                                     \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
@@ -50,29 +56,6 @@ bool is_finite(double a) { return std::isfinite(a); }
 
 }  // namespace
 
-struct lv_surface_s {
-    int device = 0;
-    int num_sms = 0;
-    int I = 0, J = 0, Je = 0;
-    std::vector<double> spot, time;
-    float2* d_sig = nullptr;         // [Je][I-1] pairs (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j})
-    float* d_node = nullptr;
-    float2* d_ab = nullptr;
-    double* d_tau = nullptr;
-    float2* h_sig_stage = nullptr;   // pinned staging for sigma uploads
-    int log_uniform = 0;
-    float cell_scale = 0.0f, cell_shift = 0.0f, s_lo = 0.0f, s_hi = 0.0f;
-    int phi = 1;
-    cudaStream_t stream = nullptr;
-    int acc_mode = LV_ACC_FP64;
-    int cfg_block = 0, cfg_k = 0, cfg_bps = 0;
-    void* d_scratch = nullptr;
-    size_t scratch_bytes = 0;
-    double* d_res = nullptr;         // [3 + I*J] result of the host-output calls
-    double* h_res = nullptr;         // pinned copy of it
-    cudaEvent_t ev_start = nullptr;  // optional events around the Monte Carlo kernel
-    cudaEvent_t ev_end = nullptr;
-};
 
 namespace {
 
@@ -139,7 +122,7 @@ size_t round_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
                         bool dbg = false)
 {
-    *block = h->cfg_block ? h->cfg_block : 256;
+    *block = h->cfg_block ? h->cfg_block : 128;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
     if (dbg) *k = 4;
     const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks);
@@ -462,8 +445,8 @@ lv_status lv_set_accumulation(lv_surface_t h, int32_t mode)
 lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks_per_sm)
 {
     if (!h) return fail(LV_EINVAL, "handle is NULL");
-    if (block != 0 && (block < 64 || block > 256 || block % 32 != 0))
-        return fail(LV_EINVAL, "block must be 0 or a multiple of 32 in [64, 256]");
+    if (block != 0 && (block < 32 || block > 128 || block % 32 != 0))
+        return fail(LV_EINVAL, "block must be 0 or a multiple of 32 in [32, 128]");
     if (k != 0 && k != 4 && k != 8 && k != 16 && k != 32)
         return fail(LV_EINVAL, "k must be 0, 4, 8, 16 or 32");
     if (blocks_per_sm < 0) return fail(LV_EINVAL, "blocks_per_sm must be >= 0");

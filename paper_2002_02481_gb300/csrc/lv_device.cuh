@@ -177,4 +177,134 @@ __device__ __forceinline__ float euler_step(const McParams& P, float y, float si
     return y + fmaf(sigma, P.sqdt2 * z, fmaf(-P.hdt * sigma, sigma, P.rdt));
 }
 
+// Near-node decision log of the DBG instantiation: (path, step, 2 i + inside).
+__device__ __forceinline__ void log_cell_decision(const McParams& P, const SmemGrid& g, const StepEval& e,
+                                                  long long rel, int n)
+{
+    const float lo = g.node[e.i], hi = g.node[e.i + 1];
+    if (fabsf(e.S - lo) <= P.dbg_band * lo || fabsf(e.S - hi) <= P.dbg_band * hi) {
+        const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
+        const unsigned long long k = atomicAdd(P.dbg_ev_count, 1ull);
+        if (k < (unsigned long long)P.dbg_ev_cap) {
+            P.dbg_ev[3 * k + 0] = (int)rel;
+            P.dbg_ev[3 * k + 1] = n;
+            P.dbg_ev[3 * k + 2] = 2 * e.i + (inside ? 1 : 0);
+        }
+    }
+}
+
+// Forward pass of one path from x0; checkpoints every KCK steps when STORE.
+template <int KCK, bool STORE, bool DBG>
+__device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
+                                              float* ck, size_t cks, long long rel)
+{
+    float x = P.x0;
+    float z[4];
+    const int nseg = (P.N + KCK - 1) / KCK;
+    for (int m = 0; m < nseg; ++m) {
+        if (STORE) ck[(size_t)m * cks] = x;
+#pragma unroll
+        for (int q = 0; q < KCK; ++q) {
+            const int n = m * KCK + q;
+            if (n < P.N) {
+                if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
+                const int4 tb = g.tab[n];
+                const StepEval e = eval_sigma<false>(P, g, x, tb);
+                if (DBG) log_cell_decision(P, g, e, rel, n);
+                x = euler_step(P, x, e.sigma, z[q & 3]);
+            }
+        }
+    }
+    return x;
+}
+
+// Philox counter words of path `rel` of the call: c1 = path bits 0..31,
+// c2 = path bits 32..47 | stream_id << 16 (the path index is path_begin + rel).
+__device__ __forceinline__ void path_counter(const McParams& P, long long rel, uint32_t& c1, uint32_t& c2)
+{
+    const unsigned long long p = (unsigned long long)(P.path_begin + rel);
+    c1 = (uint32_t)p;
+    c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
+}
+
+// Reverse sweep of one path (Sec. III / IV-C, back-propagation through the
+// Euler scheme) from its terminal adjoint xbar = d V / d x_N. Per checkpoint
+// segment, last to first: recompute KCK steps from the checkpoint keeping
+// h_n = d x_{n+1} / d sigma_n = sqrt(dt) Z_n - sigma_n dt,
+// g_n = h_n S_n d sigma / d S, the cell and the spot weight in registers; then
+// walk them back: sigma_bar_n = xbar_{n+1} h_n, xbar_n = xbar_{n+1} (1 + g_n),
+// and spread sigma_bar_n over the corner buckets (i, j), (i+1, j), (i, j+1),
+// (i+1, j+1) with the bilinear weights. Corner sums are kept in registers
+// while the cell is unchanged and then added to the block's binary32 buckets
+// `l1` (time-major, row j * I) with red.global.add.f32. Returns d V / d x_0.
+template <int KCK>
+__device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
+                                              const float* ck, size_t cks, float xbar, float* l1)
+{
+    const int nseg = (P.N + KCK - 1) / KCK;
+    int cur = -1;
+    float A = 0.0f, AU = 0.0f, Bs = 0.0f, BU = 0.0f;
+    float z[4];
+    float x_next = ck[(size_t)(nseg - 1) * cks];
+    for (int m = nseg - 1; m >= 0; --m) {
+        float x = x_next;
+        if (m > 0) x_next = ck[(size_t)(m - 1) * cks];    // in flight during this segment
+        float hq[KCK], gq[KCK], uq[KCK];
+        int iq[KCK];
+#pragma unroll
+        for (int q = 0; q < KCK; ++q) {
+            const int n = m * KCK + q;
+            if (n < P.N) {
+                if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
+                const int4 tb = g.tab[n];
+                const StepEval ev = eval_sigma<true>(P, g, x, tb);
+                const float h = fmaf(P.sqdt, z[q & 3], -ev.sigma * P.dt);
+                hq[q] = h;
+                gq[q] = h * (ev.S * ev.slope);
+                uq[q] = ev.u;
+                iq[q] = ev.i;
+                x = euler_step(P, x, ev.sigma, z[q & 3]);
+            }
+        }
+#pragma unroll
+        for (int q = KCK - 1; q >= 0; --q) {
+            const int n = m * KCK + q;
+            if (n < P.N) {
+                const int4 tb = g.tab[n];
+                const int key = tb.z + iq[q];
+                const float v = __int_as_float(tb.w);
+                const float sbar = xbar * hq[q];
+                xbar = fmaf(xbar, gq[q], xbar);
+                if (key != cur) {
+                    if (cur >= 0) {
+                        float* p0 = l1 + cur;
+                        float* p1 = p0 + P.I;
+                        atomicAdd(p0, A - AU);
+                        atomicAdd(p0 + 1, AU);
+                        atomicAdd(p1, Bs - BU);
+                        atomicAdd(p1 + 1, BU);
+                    }
+                    A = AU = Bs = BU = 0.0f;
+                    cur = key;
+                }
+                const float b = sbar * v;
+                const float a = sbar - b;
+                A += a;
+                AU = fmaf(a, uq[q], AU);
+                Bs += b;
+                BU = fmaf(b, uq[q], BU);
+            }
+        }
+    }
+    if (cur >= 0) {
+        float* p0 = l1 + cur;
+        float* p1 = p0 + P.I;
+        atomicAdd(p0, A - AU);
+        atomicAdd(p0 + 1, AU);
+        atomicAdd(p1, Bs - BU);
+        atomicAdd(p1 + 1, BU);
+    }
+    return xbar;
+}
+
 }  // namespace lv

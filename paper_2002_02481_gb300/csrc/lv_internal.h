@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace lv {
 
 // Output layout of the finalized result (same values as LV_OUT_* in lv.h).
@@ -118,3 +120,88 @@ cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, size_
 int ring_slots_per_warp();
 
 }  // namespace lv
+
+// Book of options (lv_book.cu): device tables and launch parameters.
+namespace lv {
+
+struct BookSurf {
+    int I, J, Je, log_uniform;
+    float cell_scale, cell_shift, s_lo, s_hi;
+    long long off_sig2, off_node, off_ab, off_tau;   // offsets into the book's grid arrays
+};
+
+struct BookInst {
+    int surf, N, phi, stream_id;
+    double K, T;
+    long long n_paths;
+    long long out_off;                               // first double of this option's sums / outputs
+};
+
+struct BookItem {
+    int inst, first_tile, n_tiles;                    // tiles of 32 paths
+};
+
+struct BookRun {
+    double log2_S0, r;
+    unsigned long long seed;
+};
+
+struct BookParams {
+    const BookSurf* surfs;
+    const BookInst* insts;
+    const BookItem* items;
+    int n_items;
+    const float2* sig2;
+    const float* node;
+    const float2* ab;
+    const double* tau;
+    const BookRun* run;
+    unsigned int* item_counter;
+    double* sums;          // per option [3 + I J] binary64 sums (zeroed before a run)
+    float* l1;             // [gridDim.x][max_IJe] binary32 buckets per block
+    float* ckpt;           // [ceil(max_N / k)][gridDim.x * warps * ring slots]
+    int max_I, max_Je, max_N, max_IJe;
+};
+
+size_t book_smem_bytes(int maxI, int maxJe, int maxN, int block);
+int book_ring_slots_per_warp();
+cudaError_t book_prepare(int k);
+cudaError_t book_occupancy(int block, int k, size_t smem, int* blocks_per_sm);
+cudaError_t launch_book(const BookParams& b, int grid, int block, int k, size_t smem, cudaStream_t s);
+cudaError_t launch_book_finalize(const BookParams& b, int n_inst, int max_IJ, double* out, cudaStream_t s);
+
+}  // namespace lv
+
+#include <string>
+
+#include "lv.h"
+
+namespace lv {
+// Records the thread-local message lv_last_error() returns; returns s.
+lv_status set_error(lv_status s, const std::string& msg);
+}  // namespace lv
+
+// Surface handle (host side; shared by the runtime's source files).
+struct lv_surface_s {
+    int device = 0;
+    int num_sms = 0;
+    int I = 0, J = 0, Je = 0;
+    std::vector<double> spot, time;
+    float2* d_sig = nullptr;         // [Je][I-1] pairs (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j})
+    float* d_node = nullptr;
+    float2* d_ab = nullptr;
+    double* d_tau = nullptr;
+    float2* h_sig_stage = nullptr;   // pinned staging for sigma uploads
+    int log_uniform = 0;
+    float cell_scale = 0.0f, cell_shift = 0.0f, s_lo = 0.0f, s_hi = 0.0f;
+    int phi = 1;
+    cudaStream_t stream = nullptr;
+    int acc_mode = LV_ACC_FP64;
+    int cfg_block = 0, cfg_k = 0, cfg_bps = 0;
+    void* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    double* d_res = nullptr;         // [3 + I*J] result of the host-output calls
+    double* h_res = nullptr;         // pinned copy of it
+    cudaEvent_t ev_start = nullptr;  // optional events around the Monte Carlo kernel
+    cudaEvent_t ev_end = nullptr;
+};

@@ -44,12 +44,20 @@ namespace {
 
 constexpr int kRing = 4;       // checkpoint slot groups of 32 per warp
 constexpr int kQueue = 64;     // per-warp FIFO capacity (entries)
-constexpr int kMaxWarps = 8;   // blockDim.x <= 256
+constexpr int kMaxWarps = 8;   // blockDim.x <= 256 (the adjoint kernel runs at most 128)
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
+// Level-2 accumulator of one value: binary64 or Kahan-compensated binary32.
+// The slots live in shared memory (one per thread and value), which keeps
+// them out of the registers the reverse sweep needs.
+struct AccSlot {
+    double d;
+    float s, c;
+};
+
 struct SmemLayout {
-    size_t tab, sig, node, ab, qslot, qrel, qxb, red, total;
+    size_t tab, sig, node, ab, qslot, qrel, qxb, acc, red, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks)
@@ -64,32 +72,31 @@ __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int bloc
     L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
     L.qrel = o;  if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
     L.qxb = o;   if (greeks) o += align16(sizeof(float) * (size_t)W * kQueue);
+    L.acc = o;   o += align16(sizeof(AccSlot) * 3 * (size_t)block);
     L.red = o;   o += align16(sizeof(double) * 3 * kMaxWarps);
     L.total = o;
     return L;
 }
 
-// Level-2 accumulator of one value: binary64 or Kahan-compensated binary32.
+// Adds x to a level-2 slot.
 template <int ACC>
-struct Acc {
-    double d = 0.0;
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float x)
-    {
-        if (ACC == 1) {
-            const float y = x - c;
-            const float t = s + y;
-            c = (t - s) - y;
-            s = t;
-        } else {
-            d += (double)x;
-        }
+__device__ __forceinline__ void acc_add(AccSlot& a, float x)
+{
+    if (ACC == 1) {
+        const float y = x - a.c;
+        const float t = a.s + y;
+        a.c = (t - a.s) - y;
+        a.s = t;
+    } else {
+        a.d += (double)x;
     }
-    __device__ __forceinline__ double value() const
-    {
-        return ACC == 1 ? (double)s - (double)c : d;
-    }
-};
+}
+
+template <int ACC>
+__device__ __forceinline__ double acc_value(const AccSlot& a)
+{
+    return ACC == 1 ? (double)a.s - (double)a.c : a.d;
+}
 
 __device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* smem, const SmemLayout& L)
 {
@@ -140,47 +147,6 @@ __device__ __forceinline__ int claim_tile(unsigned int* counter)
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
-// Near-node decision log of the DBG instantiation: (path, step, 2 i + inside).
-__device__ __forceinline__ void log_cell_decision(const McParams& P, const SmemGrid& g, const StepEval& e,
-                                                  long long rel, int n)
-{
-    const float lo = g.node[e.i], hi = g.node[e.i + 1];
-    if (fabsf(e.S - lo) <= P.dbg_band * lo || fabsf(e.S - hi) <= P.dbg_band * hi) {
-        const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
-        const unsigned long long k = atomicAdd(P.dbg_ev_count, 1ull);
-        if (k < (unsigned long long)P.dbg_ev_cap) {
-            P.dbg_ev[3 * k + 0] = (int)rel;
-            P.dbg_ev[3 * k + 1] = n;
-            P.dbg_ev[3 * k + 2] = 2 * e.i + (inside ? 1 : 0);
-        }
-    }
-}
-
-// Forward pass of one path from x0; checkpoints every KCK steps when STORE.
-template <int KCK, bool STORE, bool DBG>
-__device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
-                                              float* ck, size_t cks, long long rel)
-{
-    float x = P.x0;
-    float z[4];
-    const int nseg = (P.N + KCK - 1) / KCK;
-    for (int m = 0; m < nseg; ++m) {
-        if (STORE) ck[(size_t)m * cks] = x;
-#pragma unroll
-        for (int q = 0; q < KCK; ++q) {
-            const int n = m * KCK + q;
-            if (n < P.N) {
-                if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
-                const int4 tb = g.tab[n];
-                const StepEval e = eval_sigma<false>(P, g, x, tb);
-                if (DBG) log_cell_decision(P, g, e, rel, n);
-                x = euler_step(P, x, e.sigma, z[q & 3]);
-            }
-        }
-    }
-    return x;
-}
-
 template <int ACC>
 __device__ __forceinline__ void drain_buckets(float* l1, int nIJ, double* wrow)
 {
@@ -203,7 +169,7 @@ __device__ __forceinline__ void drain_buckets(float* l1, int nIJ, double* wrow)
 }
 
 template <int KCK, int ACC, bool DBG>
-__global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__ McParams P)
+__global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__ McParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = blockDim.x, W = B >> 5;
@@ -224,11 +190,11 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
 
     const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab), reinterpret_cast<const float2*>(smem + L.sig),
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
-    const int nseg = (P.N + KCK - 1) / KCK;
     const size_t cks = (size_t)gridDim.x * W * kRing * 32;   // checkpoint stride
     float* const ckw = P.ckpt + (size_t)wid * kRing * 32;     // this warp's slots
 
-    Acc<ACC> aV, aV2, aX;
+    AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
+    acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
     int q_head = 0, q_count = 0, batches = 0;
     unsigned fwd_count = 0;
     int tile = claim_tile(P.tile_counter);
@@ -245,75 +211,10 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
                 const int slot = q_slot[e];
                 const long long rel = q_rel[e];
                 float xbar = q_xb[e];
-                const unsigned long long p = (unsigned long long)(P.path_begin + rel);
-                const uint32_t c1 = (uint32_t)p;
-                const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
-                const float* ck = ckw + slot;
-                int cur = -1;
-                float A = 0.0f, AU = 0.0f, Bs = 0.0f, BU = 0.0f;
-                float z[4];
-                float x_next = ck[(size_t)(nseg - 1) * cks];
-                for (int m = nseg - 1; m >= 0; --m) {
-                    float x = x_next;
-                    if (m > 0) x_next = ck[(size_t)(m - 1) * cks];    // in flight during this segment
-                    float hq[KCK], gq[KCK], uq[KCK];
-                    int iq[KCK];
-#pragma unroll
-                    for (int q = 0; q < KCK; ++q) {
-                        const int n = m * KCK + q;
-                        if (n < P.N) {
-                            if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
-                            const int4 tb = g.tab[n];
-                            const StepEval ev = eval_sigma<true>(P, g, x, tb);
-                            const float h = fmaf(P.sqdt, z[q & 3], -ev.sigma * P.dt);
-                            hq[q] = h;
-                            gq[q] = h * (ev.S * ev.slope);
-                            uq[q] = ev.u;
-                            iq[q] = ev.i;
-                            x = euler_step(P, x, ev.sigma, z[q & 3]);
-                        }
-                    }
-#pragma unroll
-                    for (int q = KCK - 1; q >= 0; --q) {
-                        const int n = m * KCK + q;
-                        if (n < P.N) {
-                            const int4 tb = g.tab[n];
-                            const int key = tb.z + iq[q];
-                            const float v = __int_as_float(tb.w);
-                            const float sbar = xbar * hq[q];
-                            xbar = fmaf(xbar, gq[q], xbar);
-                            if (key != cur) {
-                                {
-                                    if (cur >= 0) {
-                                        float* p0 = l1 + cur;
-                                        float* p1 = p0 + P.I;
-                                        atomicAdd(p0, A - AU);
-                                        atomicAdd(p0 + 1, AU);
-                                        atomicAdd(p1, Bs - BU);
-                                        atomicAdd(p1 + 1, BU);
-                                    }
-                                    A = AU = Bs = BU = 0.0f;
-                                }
-                                cur = key;
-                            }
-                            const float b = sbar * v;
-                            const float a = sbar - b;
-                            A += a;
-                            AU = fmaf(a, uq[q], AU);
-                            Bs += b;
-                            BU = fmaf(b, uq[q], BU);
-                        }
-                    }
-                }
-                if (cur >= 0) {
-                    float* p0 = l1 + cur;
-                    float* p1 = p0 + P.I;
-                    atomicAdd(p0, A - AU);
-                    atomicAdd(p0 + 1, AU);
-                    atomicAdd(p1, Bs - BU);
-                    atomicAdd(p1 + 1, BU);
-                }
-                aX.add(xbar);
+                uint32_t c1, c2;
+                path_counter(P, rel, c1, c2);
+                xbar = reverse_path<KCK>(P, g, c1, c2, ckw + slot, cks, xbar, l1);
+                acc_add<ACC>(acc[2 * B], xbar);
                 if (DBG) P.dbg_xbar0[rel] = xbar;
             }
             q_head = (q_head + nb) & (kQueue - 1);
@@ -330,16 +231,15 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
         const int slot = g_next * 32 + lane;
         float xbarN = 0.0f;
         if (active) {
-            const unsigned long long p = (unsigned long long)(P.path_begin + rel);
-            const uint32_t c1 = (uint32_t)p;
-            const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
+            uint32_t c1, c2;
+            path_counter(P, rel, c1, c2);
             const float x = forward_path<KCK, true, DBG>(P, g, c1, c2, ckw + slot, cks, rel);
             const float SN = exp2f(x);
             const float itm = P.phi * (SN - P.K);
             const float V = itm > 0.0f ? P.disc * itm : 0.0f;
             xbarN = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
-            aV.add(V);
-            aV2.add(V * V);
+            acc_add<ACC>(acc[0], V);
+            acc_add<ACC>(acc[B], V * V);
             if (DBG) {
                 P.dbg_xN[rel] = x * 0.6931471805599453f;   // ln S_N
                 P.dbg_V[rel] = V;
@@ -377,7 +277,7 @@ __global__ void __launch_bounds__(256, 3) adjoint_kernel(const __grid_constant__
         }
         row[3 + e] = s;
     }
-    block_scalars(aV.value(), aV2.value(), aX.value(), s_red, row);
+    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
 }
 
 template <int ACC>
@@ -390,22 +290,23 @@ __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ M
     const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab), reinterpret_cast<const float2*>(smem + L.sig),
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
     const int lane = threadIdx.x & 31;
-    Acc<ACC> aV, aV2;
+    AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + threadIdx.x;
+    acc[0] = acc[blockDim.x] = AccSlot{0.0, 0.0f, 0.0f};
     for (int tile = claim_tile(P.tile_counter); tile < P.n_tiles; tile = claim_tile(P.tile_counter)) {
         const long long rel = (long long)tile * 32 + lane;
         if (rel < P.n_paths) {
-            const unsigned long long p = (unsigned long long)(P.path_begin + rel);
-            const uint32_t c1 = (uint32_t)p;
-            const uint32_t c2 = ((uint32_t)(p >> 32) & 0xffffu) | (P.stream_id << 16);
+            uint32_t c1, c2;
+            path_counter(P, rel, c1, c2);
             const float x = forward_path<4, false, false>(P, g, c1, c2, nullptr, 0, rel);
             const float itm = P.phi * (exp2f(x) - P.K);
             const float V = itm > 0.0f ? P.disc * itm : 0.0f;
-            aV.add(V);
-            aV2.add(V * V);
+            acc_add<ACC>(acc[0], V);
+            acc_add<ACC>(acc[blockDim.x], V * V);
         }
     }
     double* s_red = reinterpret_cast<double*>(smem + L.red);
-    block_scalars(aV.value(), aV2.value(), 0.0, s_red, P.partials + (size_t)blockIdx.x * P.row_words);
+    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[blockDim.x]), 0.0, s_red,
+                  P.partials + (size_t)blockIdx.x * P.row_words);
 }
 
 // Level 3, stage 1: rows [chunk * RCH, (chunk + 1) * RCH) summed in order,

@@ -231,3 +231,81 @@ class Surface:
                                                  float(eps), ctypes.byref(p), ctypes.byref(d), _dp(vega)),
                "lv_bump_greeks")
         return p.value, d.value, vega.reshape(self.n_spot, self.n_time)
+
+
+class Instrument(ctypes.Structure):
+    """lv_instrument of include/lv.h."""
+    _fields_ = [("surface", ctypes.c_int32), ("phi", ctypes.c_int32), ("K", ctypes.c_double),
+                ("T", ctypes.c_double), ("n_steps", ctypes.c_int32), ("n_paths", ctypes.c_int64),
+                ("stream_id", ctypes.c_uint32)]
+
+
+def _declare_book(lib):
+    c = ctypes
+    vp, d, i32, i64, u64 = c.c_void_p, c.c_double, c.c_int32, c.c_int64, c.c_uint64
+    sigs = {
+        "lv_book_create": [c.POINTER(vp), i32, c.POINTER(Instrument), i32, c.POINTER(vp)],
+        "lv_book_destroy": [vp],
+        "lv_book_output_offsets": [vp, c.POINTER(i64)],
+        "lv_book_set_stream": [vp, vp],
+        "lv_book_run": [vp, d, d, u64, c.POINTER(d)],
+        "lv_book_run_device": [vp, d, d, u64, vp],
+        "lv_book_tune": [vp, d, d, u64, c.POINTER(i32), c.POINTER(i32), c.POINTER(i32), c.POINTER(d)],
+    }
+    for name, args in sigs.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = None if name == "lv_book_destroy" else c.c_int
+    return lib
+
+
+class Book:
+    """A book of options on several surfaces (lv_book_t)."""
+
+    def __init__(self, surfaces, items, lib: Optional[ctypes.CDLL] = None):
+        self.lib = _declare_book(lib or load())
+        arr = (ctypes.c_void_p * len(surfaces))(*[s.h.value for s in surfaces])
+        ins = (Instrument * len(items))(*[Instrument(it.surface, it.phi, it.K, it.T, it.n_steps, it.n_paths,
+                                                     it.stream_id) for it in items])
+        self.n = len(items)
+        self.h = ctypes.c_void_p()
+        _check(self.lib, self.lib.lv_book_create(arr, len(surfaces), ins, self.n, ctypes.byref(self.h)),
+               "lv_book_create")
+        off = (ctypes.c_int64 * (self.n + 1))()
+        _check(self.lib, self.lib.lv_book_output_offsets(self.h, off), "lv_book_output_offsets")
+        self.offsets = list(off)
+
+    def close(self) -> None:
+        if self.h:
+            self.lib.lv_book_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, S0, r, seed) -> np.ndarray:
+        out = np.zeros(self.offsets[-1], dtype=np.float64)
+        _check(self.lib, self.lib.lv_book_run(self.h, S0, r, int(seed), _dp(out)), "lv_book_run")
+        return out
+
+    def run_device(self, S0, r, seed, d_out_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_book_run_device(self.h, S0, r, int(seed), ctypes.c_void_p(d_out_ptr)),
+               "lv_book_run_device")
+
+    def set_stream(self, stream_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_book_set_stream(self.h, ctypes.c_void_p(stream_ptr or None)),
+               "lv_book_set_stream")
+
+    def tune(self, S0, r, seed):
+        b, k, p, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(self.lib, self.lib.lv_book_tune(self.h, S0, r, int(seed), ctypes.byref(b), ctypes.byref(k),
+                                               ctypes.byref(p), ctypes.byref(ms)), "lv_book_tune")
+        return b.value, k.value, p.value, ms.value
+
+    def result(self, out: np.ndarray, o: int):
+        """(price, delta, stderr, vega flat) of option o from a run's output."""
+        r = out[self.offsets[o]:self.offsets[o + 1]]
+        return r[0], r[1], r[2], r[3:]
