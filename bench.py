@@ -185,6 +185,74 @@ def load_peaks():
         return {"sm_max_mhz": 2070.0}, "fallback"
 
 
+def time_call(fn, ev0, ev1, reps=3, warm=1):
+    """Median kernel time (ms, from the library's kernel events) of fn()."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        fn()
+        ev1.synchronize()
+        ts.append(ev0.elapsed_time(ev1))
+    return statistics.median(ts)
+
+
+def other_workloads(lib, dev, ev0, ev1):
+    """Kernel times of the other configurations (a few runs each)."""
+    import torch
+
+    from paper_2002_02481_gb300 import lv
+
+    res = {}
+    stream = torch.cuda.current_stream(dev)
+
+    def single(name, surf, opt, launch=None, acc=0):
+        S = lv.Surface.from_workload(surf, lib)
+        S.set_stream(stream.cuda_stream)
+        S.set_accumulation(acc)
+        if launch:
+            S.set_launch(*launch)
+        S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+        d = torch.zeros(3 + surf.n_spot * surf.n_time, dtype=torch.float64, device=dev)
+        ms = time_call(lambda: S.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths,
+                                                      opt.seed, d.data_ptr()), ev0, ev1)
+        res[name] = {"adjoint_kernel_ms": ms, "path_steps_per_s": opt.n_paths * opt.n_steps / (ms * 1e-3),
+                     "launch": list(S.get_launch(opt.n_steps, True))}
+        S.close()
+
+    single("small 20x10, 52 steps, 2^14 paths", *W.config_small())
+    for which in ("small", "paper"):
+        surf, opt = W.config_precision(which)
+        for acc, nm in ((0, "binary64"), (1, "Kahan")):
+            single(f"precision {which} grid, 156 steps, 2^24 paths, level 2 {nm}", surf, opt, acc=acc)
+    surf, opt = W.config_large()
+    for k in (8, 32):
+        single(f"large 100x100, 1260 steps, 2^26 paths, k={k}", surf, opt, launch=(128, k, 0))
+    # the book: 8 grids x 64 options, one persistent launch, graph replay
+    handles = [lv.Surface.from_workload(sf, lib) for sf in W.book_surfaces()]
+    items = W.book_items()
+    book = lv.Book(handles, items, lib)
+    for h in handles:
+        h.close()
+    blk, k, item_paths, tune_ms = book.tune(100.0, 0.0, 1)
+    book.run(100.0, 0.0, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = 5
+    for rep in range(reps):
+        book.run(100.0, 0.0, 1 + rep)
+    wall = (time.perf_counter() - t0) / reps
+    ps = sum(it.n_paths * it.n_steps for it in items)
+    res["book 8 grids x 64 options, graph replay"] = {
+        "ms_per_run_wall": wall * 1e3, "path_steps": ps, "path_steps_per_s": ps / wall,
+        "paths": sum(it.n_paths for it in items), "tuned": {"block": blk, "k": k, "item_paths": item_paths,
+                                                            "kernel_ms": tune_ms}}
+    book.close()
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -293,6 +361,11 @@ def run_ours(args):
                "h2d_bytes_per_step": int(sig_np.nbytes), "d2h_bytes_per_step": int(8 * n_out),
                "ms_per_step": e2e_s * 1e3}
 
+    workloads = None
+    if rk == 0 and not args.no_extra:
+        S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+        workloads = other_workloads(lib, dev, ev0, ev1)
+
     if rk == 0:
         peaks, src = load_peaks()
         clocks = clk.summary()
@@ -327,10 +400,45 @@ def run_ours(args):
             "forward_only": {"kernel_ms": statistics.mean(fwd_ms),
                              "value": P * opt.n_steps / (statistics.mean(fwd_ms) * 1e-3), "unit": "path-steps/s"},
             "bump_reprice": bump,
+            "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def precision_study():
+    """Config-3 study: FP32 paths with binary64 or Kahan binary32 level-2
+    accumulation, against the FP64 oracle over the same 2^24 paths (seed 1),
+    error stated per output. Prints one JSON line."""
+    import torch
+
+    import oracle
+    from paper_2002_02481_gb300 import lv
+
+    lib = lv.load()
+    out = {"study": "precision", "paths": 1 << 24, "n_steps": 156, "reference": "FP64 CPU oracle, same paths"}
+    for which in ("small", "paper"):
+        surf, opt = W.config_precision(which)
+        t0 = time.perf_counter()
+        ref = oracle.price_greeks(surf, opt)
+        cpu_s = time.perf_counter() - t0
+        row = {"oracle_s": cpu_s, "oracle_threads": oracle.default_threads()}
+        for acc, nm in ((0, "binary64"), (1, "Kahan")):
+            S = lv.Surface.from_workload(surf, lib)
+            S.set_accumulation(acc)
+            p, d, v = S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+            S.close()
+            vm = float(np.max(np.abs(ref["vega"])))
+            row[nm] = {"price_rel": abs(p - ref["price"]) / abs(ref["price"]),
+                       "delta_rel": abs(d - ref["delta"]) / abs(ref["delta"]),
+                       "vega_max_abs_err_of_max": float(np.max(np.abs(v - ref["vega"]))) / vm,
+                       "vega_rms_err_of_max": float(np.sqrt(np.mean((v - ref["vega"]) ** 2))) / vm,
+                       "price": p, "delta": d}
+        row["oracle"] = {"price": ref["price"], "delta": ref["delta"], "stderr": ref["stderr"]}
+        out[f"{which} grid {surf.n_spot}x{surf.n_time}"] = row
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -341,9 +449,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-bump", action="store_true", help="skip the bump-and-reprice timing")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="2^24-path precision workloads: binary64 vs Kahan level 2 against the FP64 oracle")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_study:
+        return precision_study()
     return run_ours(args)
 
 

@@ -80,7 +80,7 @@ def test_book_matches_single_option_calls(lib):
     dd = d.cpu().numpy()
     for o in range(len(items)):
         _close(out2[book.offsets[o]:book.offsets[o + 1]], dd[book.offsets[o]:book.offsets[o + 1]], f"replay {o}")
-    assert not np.allclose(out2[:3], out[:3])
+    assert not np.allclose(out2, out)          # other S0, r and seed: other results
     # autotuner: keeps a shape that still reproduces the results
     blk, k, item_paths, ms = book.tune(S0, r, seed)
     assert blk in (64, 128) and k in (4, 8) and item_paths > 0 and ms > 0
