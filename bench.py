@@ -157,14 +157,12 @@ def run_reference(args):
 
 
 def kernel_source_hash() -> str:
-    """Hash of the adjoint kernel's source (device helpers + kernel text)."""
+    """Hash of the source files the adjoint kernel is built from (any edit to
+    them invalidates a recorded traffic figure)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2002_02481_gb300", "csrc")
-    dev = open(os.path.join(csrc, "lv_device.cuh")).read()
-    k = open(os.path.join(csrc, "lv_kernels.cu")).read()
-    a = k.index("template <int KCK, int ACC, bool DBG>\n__global__")
-    b = k.index("template <int ACC>\n__global__", a)
-    return hashlib.sha256((dev + k[a:b]).encode()).hexdigest()[:16]
+    text = "".join(open(os.path.join(csrc, f)).read() for f in ("lv_device.cuh", "lv_kernels.cu", "lv_internal.h"))
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def profiled_traffic():

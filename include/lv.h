@@ -123,6 +123,15 @@ lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks
  * alone; NULL, NULL switches this off. */
 lv_status lv_set_kernel_events(lv_surface_t h, void* start_event, void* end_event);
 
+/* Autotuner for one option: times lv_price_greeks_device on this problem
+ * over launch shapes (threads per block 64 / 128, checkpoint interval 4 / 8
+ * / 16), keeps the fastest in the handle (as lv_set_launch would) and
+ * appends it to the file named by LV_TUNE_CACHE when that variable is set;
+ * later handles with the same grid size and step count then start from it.
+ * Runs the problem about 18 times. Outputs may be NULL. */
+lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps, int64_t n_paths,
+                  uint64_t seed, int32_t* out_block, int32_t* out_k, double* out_ms);
+
 /* Read back the launch shape the next call will use for (n_steps, greeks). */
 lv_status lv_get_launch(lv_surface_t h, int32_t n_steps, int32_t greeks,
                         int32_t* block, int32_t* k, int32_t* blocks_per_sm);

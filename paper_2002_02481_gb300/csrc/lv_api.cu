@@ -3,7 +3,10 @@
 // the host-output wrappers.
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -25,6 +28,55 @@ lv_status fail(lv_status s, const std::string& msg)
 }  // namespace
 
 lv_status lv::set_error(lv_status s, const std::string& msg) { return fail(s, msg); }
+
+namespace {
+std::mutex g_tune_mu;
+}  // namespace
+
+bool lv::tune_cache_lookup(const std::string& key, int vals[3])
+{
+    const char* path = std::getenv("LV_TUNE_CACHE");
+    if (!path || !*path) return false;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (std::fgets(line, sizeof line, f)) {
+        char kbuf[512];
+        int a = 0, b = 0, c = 0;
+        double ms = 0.0;
+        if (std::sscanf(line, "%511s %d %d %d %lf", kbuf, &a, &b, &c, &ms) == 5 && key == kbuf) {
+            vals[0] = a;
+            vals[1] = b;
+            vals[2] = c;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void lv::tune_cache_append(const std::string& key, const int vals[3], double ms)
+{
+    const char* path = std::getenv("LV_TUNE_CACHE");
+    if (!path || !*path) return;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), vals[0], vals[1], vals[2], ms);
+    std::fclose(f);
+}
+
+std::string lv::gpu_name(int device)
+{
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
+    std::string n(prop.name);
+    for (char& ch : n)
+        if (ch == ' ') ch = '_';
+    return n;
+}
 
 namespace {
 
@@ -109,7 +161,8 @@ lv_status check_option(double S0, double r, double K, double T, int32_t n_steps)
 }
 
 struct Plan {
-    int block = 256, k = 8, bps = 1, grid = 1;
+    int block = 128, k = 4, bps = 1, grid = 1;
+    bool grid_smem = true;
     size_t smem = 0;
     int n_tiles = 0, n_ck = 0, row_words = 0, n_chunks = 0;
     size_t off_counter = 0, off_part = 0, off_chunks = 0, off_wrows = 0, off_l1 = 0, off_ckpt = 0, total = 0;
@@ -119,18 +172,39 @@ size_t round_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
 
 // The per-path diagnostics kernel always runs checkpoints every 4 steps with
 // binary64 level 2 (per-path values do not depend on either).
+std::string adjoint_tune_key(const lv_surface_s* h, int32_t n_steps)
+{
+    int nb = 0;
+    for (int n = n_steps; n > 1; n >>= 1) ++nb;
+    return "adjoint|" + lv::gpu_name(h->device) + "|" + std::to_string(h->I) + "x" + std::to_string(h->J) +
+           "|N2^" + std::to_string(nb);
+}
+
+// Shared memory a block may use and still leave room for the five resident
+// blocks the register budget allows; larger grids are read through L1.
+constexpr size_t kGridSmemLimit = 44 * 1024;
+
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
-                        bool dbg = false)
+                        bool dbg = false, bool* grid_smem = nullptr)
 {
     *block = h->cfg_block ? h->cfg_block : 128;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
+    if (greeks && !dbg && !h->cfg_block && !h->cfg_k) {
+        int v[3];
+        if (lv::tune_cache_lookup(adjoint_tune_key(h, n_steps), v) && v[0] >= 32 && v[0] <= 128 &&
+            v[0] % 32 == 0 && (v[1] == 4 || v[1] == 8 || v[1] == 16 || v[1] == 32)) {
+            *block = v[0];
+            *k = v[1];
+        }
+    }
     if (dbg) *k = 4;
-    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks);
+    const bool gs = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, true) <= kGridSmemLimit;
+    if (grid_smem) *grid_smem = gs;
+    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, gs);
     if (smem > 200 * 1024)
-        return fail(LV_EINVAL, "grid and time table do not fit in shared memory (" +
-                               std::to_string(smem) + " bytes)");
+        return fail(LV_EINVAL, "time table does not fit in shared memory (" + std::to_string(smem) + " bytes)");
     int occ = 0;
-    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, smem, &occ));
+    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, gs, smem, &occ));
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
     *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
     return LV_OK;
@@ -138,9 +212,9 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
 
 lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, bool dbg, Plan* p)
 {
-    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg);
+    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem);
     if (st != LV_OK) return st;
-    p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks);
+    p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem);
     const int warps = p->block / 32;
     const int64_t tiles = (n_paths + 31) / 32;            // warps claim tiles of 32 paths
     p->n_tiles = (int)tiles;
@@ -157,7 +231,8 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     p->off_counter = o; o += 256;
     p->off_part = o;    o = round_up(o + sizeof(double) * (size_t)p->grid * p->row_words, 256);
     p->off_chunks = o;  o = round_up(o + sizeof(double) * (size_t)p->n_chunks * p->row_words, 256);
-    p->off_wrows = o;   if (greeks) o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
+    p->off_wrows = o;                   // per-warp rows: Kahan mode only
+    if (greeks && h->acc_mode == LV_ACC_KAHAN) o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
     p->off_l1 = o;      if (greeks) o = round_up(o + sizeof(float) * (size_t)p->grid * nIJ, 256);
     p->off_ckpt = o;
     o = round_up(o + sizeof(float) * (size_t)p->n_ck * total_warps * lv::ring_slots_per_warp(), 256);
@@ -266,6 +341,7 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     P.ckpt = reinterpret_cast<float*>(base + p.off_ckpt);
     P.n_ck = p.n_ck;
     P.flush_every = 8;
+    P.grid_smem = p.grid_smem ? 1 : 0;
     P.dbg_xN = c.dbg_xN;
     P.dbg_V = c.dbg_V;
     P.dbg_xbar0 = c.dbg_xbar0;
@@ -473,7 +549,7 @@ lv_status lv_get_launch(lv_surface_t h, int32_t n_steps, int32_t greeks, int32_t
     if (n_steps < 1 || n_steps > LV_MAX_STEPS) return fail(LV_EINVAL, "n_steps out of range");
     DeviceGuard g(h->device);
     int b = 0, kk = 0, bps = 0;
-    lv_status st = choose_launch(h, n_steps, greeks != 0, &b, &kk, &bps, false);
+    lv_status st = choose_launch(h, n_steps, greeks != 0, &b, &kk, &bps, false, nullptr);
     if (st != LV_OK) return st;
     *block = b;
     *k = kk;
@@ -535,6 +611,65 @@ lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, doubl
     if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
     McCall c{S0, r, K, T, n_steps, path_begin, path_end - path_begin, seed, stream_id, true, true, d_sums};
     return run_mc(h, c);
+}
+
+lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps, int64_t n_paths,
+                  uint64_t seed, int32_t* out_block, int32_t* out_k, double* out_ms)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    lv_status st = check_option(S0, r, K, T, n_steps);
+    if (st != LV_OK) return st;
+    if (n_paths < 1 || n_paths > 0x7fffffffLL) return fail(LV_EINVAL, "n_paths must be in [1, 2^31 - 1]");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    const int blocks[] = {64, 128};
+    const int ks[] = {4, 8, 16};
+    const int keep_b = h->cfg_block, keep_k = h->cfg_k, keep_s = h->cfg_bps;
+    cudaEvent_t e0, e1;
+    LV_CUDA(cudaEventCreate(&e0));
+    LV_CUDA(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bb = 128, bk = 4;
+    for (int blk : blocks)
+        for (int k : ks) {
+            h->cfg_block = blk;
+            h->cfg_k = k;
+            h->cfg_bps = 0;
+            McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, h->d_res};
+            if (run_mc(h, c) != LV_OK) continue;             // warm-up (and scratch growth)
+            float t = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, h->stream);
+                if (run_mc(h, c) != LV_OK) break;
+                cudaEventRecord(e1, h->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t = std::fmin(t, ms);
+            }
+            if (t < best) {
+                best = t;
+                bb = blk;
+                bk = k;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!(best < 1e299)) {
+        h->cfg_block = keep_b;
+        h->cfg_k = keep_k;
+        h->cfg_bps = keep_s;
+        return fail(LV_EINTERNAL, "no launch shape ran");
+    }
+    h->cfg_block = bb;
+    h->cfg_k = bk;
+    h->cfg_bps = 0;
+    const int v[3] = {bb, bk, 0};
+    lv::tune_cache_append(adjoint_tune_key(h, n_steps), v, best);
+    if (out_block) *out_block = bb;
+    if (out_k) *out_k = bk;
+    if (out_ms) *out_ms = best;
+    return LV_OK;
 }
 
 lv_status lv_finalize_sums_device(lv_surface_t h, const double* d_sums, int64_t n_paths, double S0,
@@ -746,7 +881,8 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     if (st != LV_OK) return st;
 
     int block = 0, k = 0, bps = 0;
-    st = choose_launch(h, n_steps, true, &block, &k, &bps, false);
+    bool grid_smem = true;
+    st = choose_launch(h, n_steps, true, &block, &k, &bps, false, &grid_smem);
     if (st != LV_OK) return st;
     const int warps = block / 32;
     const int64_t tiles = (n_paths + 31) / 32;
@@ -777,10 +913,11 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     P.ckpt = reinterpret_cast<float*>(base + off_ckpt);
     P.n_ck = (n_steps + k - 1) / k;
     P.flush_every = 8;
+    P.grid_smem = grid_smem ? 1 : 0;
     // the array keeps the previous call's contents: the tile counter must start at zero
     // (every other section is written before it is read)
     LV_CUDA(cudaMemsetAsync(P.tile_counter, 0, sizeof(unsigned int), h->stream));
-    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, block, true);
+    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, block, true, grid_smem);
     LV_CUDA(lv::launch_mc(P, grid, block, k, true, smem, h->stream));
     lv::FinalizeParams F{};
     F.partials = P.partials;

@@ -227,47 +227,27 @@ lv_status check_run(double S0, double r)
 
 std::string tune_key(const lv_book_s* b)
 {
-    cudaDeviceProp prop{};
-    cudaGetDeviceProperties(&prop, b->device);
     int nb = 0;
     for (int n = b->max_N; n > 1; n >>= 1) ++nb;
-    return std::string("book|") + prop.name + "|IJ" + std::to_string(b->max_IJ) + "|N2^" + std::to_string(nb) +
+    return "book|" + lv::gpu_name(b->device) + "|IJ" + std::to_string(b->max_IJ) + "|N2^" + std::to_string(nb) +
            "|insts" + std::to_string(b->insts.size());
 }
 
-// Last matching "key block k item_tiles ms" line of the cache file, if any.
 bool read_tuned(const std::string& key, int* block, int* k, int* item_tiles)
 {
-    const char* path = std::getenv("LV_TUNE_CACHE");
-    if (!path || !*path) return false;
-    FILE* f = std::fopen(path, "r");
-    if (!f) return false;
-    char line[1024];
-    bool found = false;
-    while (std::fgets(line, sizeof line, f)) {
-        char kbuf[512];
-        int bb = 0, kk = 0, it = 0;
-        double ms = 0.0;
-        if (std::sscanf(line, "%511s %d %d %d %lf", kbuf, &bb, &kk, &it, &ms) == 5 && key == kbuf &&
-            (kk == 4 || kk == 8) && bb >= 32 && bb <= 128 && bb % 32 == 0 && it >= 1) {
-            *block = bb;
-            *k = kk;
-            *item_tiles = it;
-            found = true;
-        }
-    }
-    std::fclose(f);
-    return found;
+    int v[3];
+    if (!lv::tune_cache_lookup(key, v)) return false;
+    if (!(v[1] == 4 || v[1] == 8) || v[0] < 32 || v[0] > 128 || v[0] % 32 != 0 || v[2] < 1) return false;
+    *block = v[0];
+    *k = v[1];
+    *item_tiles = v[2];
+    return true;
 }
 
 void write_tuned(const std::string& key, int block, int k, int item_tiles, double ms)
 {
-    const char* path = std::getenv("LV_TUNE_CACHE");
-    if (!path || !*path) return;
-    FILE* f = std::fopen(path, "a");
-    if (!f) return;
-    std::fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), block, k, item_tiles, ms);
-    std::fclose(f);
+    const int v[3] = {block, k, item_tiles};
+    lv::tune_cache_append(key, v, ms);
 }
 
 }  // namespace

@@ -58,6 +58,7 @@ struct McParams {
     float* ckpt;           // [n_ck][gridDim.x * warps * ring_slots_per_warp()] checkpoints of x
     int n_ck;
     int flush_every;       // reverse batches between level-1 -> level-2 drains
+    int grid_smem;         // 1: sigma pairs staged in shared memory, 0: read through L1
     int acc_mode;          // 0 binary64, 1 Kahan binary32
 
     // per-path outputs and near-node decision log (debug entry point only;
@@ -108,7 +109,7 @@ cudaError_t launch_bump_finalize(const double* partials, int G, int row_words, d
                                  long long n_paths, double eps, double eps_S, double* out,
                                  unsigned int* tile_counter, cudaStream_t s);
 
-size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks);
+size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem);
 
 // Launchers; return cudaSuccess or the launch error. An adjoint launch with
 // p.dbg_xN != null runs the logging instantiation with k = 4 and binary64
@@ -116,7 +117,8 @@ size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks);
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, size_t smem, int* blocks_per_sm);
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, size_t smem,
+                         int* blocks_per_sm);
 int ring_slots_per_warp();
 
 }  // namespace lv
@@ -179,6 +181,12 @@ cudaError_t launch_book_finalize(const BookParams& b, int n_inst, int max_IJ, do
 namespace lv {
 // Records the thread-local message lv_last_error() returns; returns s.
 lv_status set_error(lv_status s, const std::string& msg);
+
+// Launch-shape cache shared by the autotuners: lines "key v0 v1 v2 ms" in
+// the file named by LV_TUNE_CACHE (the last line of a key wins).
+bool tune_cache_lookup(const std::string& key, int vals[3]);
+void tune_cache_append(const std::string& key, const int vals[3], double ms);
+std::string gpu_name(int device);
 }  // namespace lv
 
 // Surface handle (host side; shared by the runtime's source files).

@@ -25,10 +25,11 @@
 // Bucket accumulation: run-length sums in registers while the cell is
 // unchanged (level 0); binary32 reductions (red.global.add.f32, resolved in
 // L2 without a retry loop) into a per-block bucket array in global memory
-// (level 1); every few batches a warp drains that array (atomicExch) into a
-// row it owns, binary64 or Kahan-compensated binary32 (level 2); at the end
-// each block folds its warps' rows into one binary64 row, and a separate
-// fixed-order binary64 reduction over blocks gives the outputs (level 3).
+// (level 1); every few batches a warp drains that array (atomicExch) into
+// level 2: the block's binary64 row through binary64 reductions, or in Kahan
+// mode a compensated binary32 row the warp owns; at the end each block folds
+// what is left into its binary64 row, and a separate fixed-order binary64
+// reduction over blocks gives the outputs (level 3).
 //
 // The DBG instantiation additionally writes per-path results and logs
 // every forward step whose spot lies within a relative band of its cell's
@@ -60,13 +61,13 @@ struct SmemLayout {
     size_t tab, sig, node, ab, qslot, qrel, qxb, acc, red, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks)
+__host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks, bool grid_smem)
 {
     const int W = block / 32;
     SmemLayout L;
     size_t o = 0;
     L.tab = o;   o += align16(sizeof(int4) * (size_t)N);
-    L.sig = o;   o += align16(sizeof(float2) * (size_t)Je * (I - 1));
+    L.sig = o;   if (grid_smem) o += align16(sizeof(float2) * (size_t)Je * (I - 1));
     L.node = o;  o += align16(sizeof(float) * (size_t)I);
     L.ab = o;    o += align16(sizeof(float2) * (size_t)I);
     L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
@@ -98,6 +99,10 @@ __device__ __forceinline__ double acc_value(const AccSlot& a)
     return ACC == 1 ? (double)a.s - (double)a.c : a.d;
 }
 
+// Stages the time table, the spot nodes, the cell coefficients and (when GS)
+// the sigma pairs in shared memory; large grids are read from global memory
+// through L1 instead, which leaves room for more resident blocks.
+template <bool GS>
 __device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* smem, const SmemLayout& L)
 {
     const int B = blockDim.x, tid = threadIdx.x;
@@ -105,7 +110,8 @@ __device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* sme
     float2* s_sig = reinterpret_cast<float2*>(smem + L.sig);
     float* s_node = reinterpret_cast<float*>(smem + L.node);
     float2* s_ab = reinterpret_cast<float2*>(smem + L.ab);
-    for (int e = tid; e < P.Je * (P.I - 1); e += B) s_sig[e] = P.sig2[e];
+    if (GS)
+        for (int e = tid; e < P.Je * (P.I - 1); e += B) s_sig[e] = P.sig2[e];
     for (int e = tid; e < P.I; e += B) s_node[e] = P.node[e];
     for (int e = tid; e < P.I - 1; e += B) s_ab[e] = P.ab[e];
     for (int n = tid; n < P.N; n += B) s_tab[n] = step_time(P, n);
@@ -163,19 +169,19 @@ __device__ __forceinline__ void drain_buckets(float* l1, int nIJ, double* wrow)
             p.x = t;
             *k = p;
         } else {
-            wrow[e] += (double)v;
+            atomicAdd(&wrow[e], (double)v);       // the block's row, shared by its warps
         }
     }
 }
 
-template <int KCK, int ACC, bool DBG>
+template <int KCK, int ACC, bool DBG, bool GS>
 __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__ McParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = blockDim.x, W = B >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true);
-    stage_grid(P, smem, L);
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
+    stage_grid<GS>(P, smem, L);
     float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);    // this block's level-1 buckets
     int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQueue;
     int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
@@ -184,11 +190,21 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
     const int nIJ = P.Je * P.I;
     for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
     const int wid = blockIdx.x * W + warp;                    // global warp id
-    double* wrow = P.warp_rows + (size_t)wid * nIJ;           // this warp's level-2 row
-    for (int e = lane; e < nIJ; e += 32) wrow[e] = 0.0;       // (also zero as a float2 pair)
+    // level 2: binary64 mode drains into the block's own row with binary64
+    // reductions; Kahan pairs cannot be updated atomically, so each warp owns one
+    double* const row = P.partials + (size_t)blockIdx.x * P.row_words;
+    double* wrow;
+    if (ACC == 1) {
+        wrow = P.warp_rows + (size_t)wid * nIJ;
+        for (int e = lane; e < nIJ; e += 32) wrow[e] = 0.0;   // zero as a float2 pair too
+    } else {
+        wrow = row + 3;
+        for (int e = tid; e < nIJ; e += B) wrow[e] = 0.0;
+    }
     __syncthreads();
 
-    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab), reinterpret_cast<const float2*>(smem + L.sig),
+    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
+                      GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
     const size_t cks = (size_t)gridDim.x * W * kRing * 32;   // checkpoint stride
     float* const ckw = P.ckpt + (size_t)wid * kRing * 32;     // this warp's slots
@@ -260,34 +276,34 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
         tile = claim_tile(P.tile_counter);
     }
 
-    // fold: remaining level-1 buckets and every warp row of this block into
-    // the block's binary64 row (after the barrier nothing adds any more)
+    // fold: remaining level-1 buckets (and, in Kahan mode, every warp row of
+    // this block) into the block's binary64 row (after the barrier nothing adds)
     __syncthreads();
-    double* row = P.partials + (size_t)blockIdx.x * P.row_words;
     const double* rows0 = P.warp_rows + (size_t)blockIdx.x * W * nIJ;
     for (int e = tid; e < nIJ; e += B) {
-        double s = (double)l1[e];
-        for (int w = 0; w < W; ++w) {
-            if (ACC == 1) {
+        if (ACC == 1) {
+            double s = (double)l1[e];
+            for (int w = 0; w < W; ++w) {
                 const float2 k = reinterpret_cast<const float2*>(rows0 + (size_t)w * nIJ)[e];
                 s += (double)k.x - (double)k.y;
-            } else {
-                s += rows0[(size_t)w * nIJ + e];
             }
+            row[3 + e] = s;
+        } else {
+            row[3 + e] += (double)l1[e];
         }
-        row[3 + e] = s;
     }
     block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
 }
 
-template <int ACC>
+template <int ACC, bool GS>
 __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ McParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, blockDim.x, false);
-    stage_grid(P, smem, L);
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, blockDim.x, false, GS);
+    stage_grid<GS>(P, smem, L);
     __syncthreads();
-    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab), reinterpret_cast<const float2*>(smem + L.sig),
+    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
+                      GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
     const int lane = threadIdx.x & 31;
     AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + threadIdx.x;
@@ -364,29 +380,16 @@ cudaError_t set_smem_attr(K kernel)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
-template <int KCK, int ACC, bool DBG>
-cudaError_t launch_adjoint(const McParams& p, int grid, int block, size_t smem, cudaStream_t s)
+template <typename K>
+cudaError_t launch_configured(K kernel, bool& configured, const McParams& p, int grid, int block, size_t smem,
+                              cudaStream_t s)
 {
-    static bool configured = false;
     if (!configured) {
-        cudaError_t e = set_smem_attr(adjoint_kernel<KCK, ACC, DBG>);
+        cudaError_t e = set_smem_attr(kernel);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    adjoint_kernel<KCK, ACC, DBG><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <int ACC>
-cudaError_t launch_price(const McParams& p, int grid, int block, size_t smem, cudaStream_t s)
-{
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = set_smem_attr(price_kernel<ACC>);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    price_kernel<ACC><<<grid, block, smem, s>>>(p);
+    kernel<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -398,11 +401,44 @@ cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kernel, block, smem);
 }
 
+// Calls f(kernel, flag) with the instantiation for (greeks, k, acc, dbg, gs).
+template <bool GS, typename F>
+cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, F&& f)
+{
+    if (!greeks) {
+        static bool c0 = false, c1 = false;
+        return acc ? f(price_kernel<1, GS>, c1) : f(price_kernel<0, GS>, c0);
+    }
+    if (dbg) {
+        static bool cd = false;
+        if (k != 4) return cudaErrorInvalidValue;       // scratch must be planned with k = 4
+        return f(adjoint_kernel<4, 0, true, GS>, cd);
+    }
+    static bool c[8] = {};
+    switch (k * 2 + acc) {
+    case 8: return f(adjoint_kernel<4, 0, false, GS>, c[0]);
+    case 9: return f(adjoint_kernel<4, 1, false, GS>, c[1]);
+    case 16: return f(adjoint_kernel<8, 0, false, GS>, c[2]);
+    case 17: return f(adjoint_kernel<8, 1, false, GS>, c[3]);
+    case 32: return f(adjoint_kernel<16, 0, false, GS>, c[4]);
+    case 33: return f(adjoint_kernel<16, 1, false, GS>, c[5]);
+    case 64: return f(adjoint_kernel<32, 0, false, GS>, c[6]);
+    case 65: return f(adjoint_kernel<32, 1, false, GS>, c[7]);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename F>
+cudaError_t with_kernel(bool greeks, int k, int acc, bool dbg, bool gs, F&& f)
+{
+    return gs ? with_kernel_gs<true>(greeks, k, acc, dbg, f) : with_kernel_gs<false>(greeks, k, acc, dbg, f);
+}
+
 }  // namespace
 
-size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks)
+size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem)
 {
-    return smem_layout(I, Je, N, block, greeks).total;
+    return smem_layout(I, Je, N, block, greeks, grid_smem).total;
 }
 
 int ring_slots_per_warp() { return kRing * 32; }
@@ -410,40 +446,16 @@ int ring_slots_per_warp() { return kRing * 32; }
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s)
 {
-    const int acc = p.acc_mode;
-    if (!greeks) return acc ? launch_price<1>(p, grid, block, smem, s) : launch_price<0>(p, grid, block, smem, s);
-    if (p.dbg_xN) {
-        if (k != 4) return cudaErrorInvalidValue;       // scratch must be planned with k = 4
-        return launch_adjoint<4, 0, true>(p, grid, block, smem, s);
-    }
-    switch (k * 2 + acc) {
-    case 8: return launch_adjoint<4, 0, false>(p, grid, block, smem, s);
-    case 9: return launch_adjoint<4, 1, false>(p, grid, block, smem, s);
-    case 16: return launch_adjoint<8, 0, false>(p, grid, block, smem, s);
-    case 17: return launch_adjoint<8, 1, false>(p, grid, block, smem, s);
-    case 32: return launch_adjoint<16, 0, false>(p, grid, block, smem, s);
-    case 33: return launch_adjoint<16, 1, false>(p, grid, block, smem, s);
-    case 64: return launch_adjoint<32, 0, false>(p, grid, block, smem, s);
-    case 65: return launch_adjoint<32, 1, false>(p, grid, block, smem, s);
-    default: return cudaErrorInvalidValue;
-    }
+    return with_kernel(greeks, k, p.acc_mode, p.dbg_xN != nullptr, p.grid_smem != 0,
+                       [&](auto kernel, bool& configured) {
+                           return launch_configured(kernel, configured, p, grid, block, smem, s);
+                       });
 }
 
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, size_t smem, int* bps)
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, size_t smem, int* bps)
 {
-    if (!greeks) return acc ? occupancy(price_kernel<1>, block, smem, bps) : occupancy(price_kernel<0>, block, smem, bps);
-    if (dbg) return occupancy(adjoint_kernel<4, 0, true>, block, smem, bps);
-    switch (k * 2 + acc) {
-    case 8: return occupancy(adjoint_kernel<4, 0, false>, block, smem, bps);
-    case 9: return occupancy(adjoint_kernel<4, 1, false>, block, smem, bps);
-    case 16: return occupancy(adjoint_kernel<8, 0, false>, block, smem, bps);
-    case 17: return occupancy(adjoint_kernel<8, 1, false>, block, smem, bps);
-    case 32: return occupancy(adjoint_kernel<16, 0, false>, block, smem, bps);
-    case 33: return occupancy(adjoint_kernel<16, 1, false>, block, smem, bps);
-    case 64: return occupancy(adjoint_kernel<32, 0, false>, block, smem, bps);
-    case 65: return occupancy(adjoint_kernel<32, 1, false>, block, smem, bps);
-    default: return cudaErrorInvalidValue;
-    }
+    return with_kernel(greeks, k, acc, dbg, grid_smem,
+                       [&](auto kernel, bool&) { return occupancy(kernel, block, smem, bps); });
 }
 
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s)

@@ -69,6 +69,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_set_accumulation": [vp, i32],
         "lv_set_launch": [vp, i32, i32, i32],
         "lv_set_kernel_events": [vp, vp, vp],
+        "lv_tune": [vp, d, d, d, d, i32, i64, u64, c.POINTER(i32), c.POINTER(i32), c.POINTER(d)],
         "lv_get_launch": [vp, i32, i32, c.POINTER(i32), c.POINTER(i32), c.POINTER(i32)],
         "lv_price": [vp, d, d, d, d, i32, i64, u64, dp, dp],
         "lv_price_greeks": [vp, d, d, d, d, i32, i64, u64, dp, dp, dp],
@@ -170,6 +171,12 @@ class Surface:
     def set_kernel_events(self, start_ptr: int, end_ptr: int) -> None:
         _check(self.lib, self.lib.lv_set_kernel_events(self.h, ctypes.c_void_p(start_ptr or None),
                                                        ctypes.c_void_p(end_ptr or None)), "lv_set_kernel_events")
+
+    def tune(self, S0, r, K, T, n_steps, n_paths, seed):
+        b, k, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        _check(self.lib, self.lib.lv_tune(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
+                                          ctypes.byref(b), ctypes.byref(k), ctypes.byref(ms)), "lv_tune")
+        return b.value, k.value, ms.value
 
     def get_launch(self, n_steps: int, greeks: bool = True):
         b, k, s = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
