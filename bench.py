@@ -269,6 +269,8 @@ def run_ours(args):
     S = lv.Surface.from_workload(surf, lib)
     stream = torch.cuda.current_stream(dev)
     S.set_stream(stream.cuda_stream)
+    # launch shape from the project's autotuner, on this workload
+    tuned = S.tune(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
     n_out = 3 + surf.n_spot * surf.n_time
     d_out = torch.zeros(n_out, dtype=torch.float64, device=dev)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -391,6 +393,7 @@ def run_ours(args):
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "30x60", "n_steps": opt.n_steps, "n_paths_per_gpu": P,
+                       "launch": {"block": tuned[0], "k": tuned[1], "source": "lv_tune"},
                        "l2": "256 MB buffer rewritten between timed steps (outside the timed region)",
                        "parallelism": f"path-range shards x{ws}"},
             "clocks": clocks, "gpu_launches": 3 * args.steps, "roofline": roofline,

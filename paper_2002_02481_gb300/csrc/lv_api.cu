@@ -216,7 +216,7 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     if (st != LV_OK) return st;
     p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem);
     const int warps = p->block / 32;
-    const int64_t tiles = (n_paths + 31) / 32;            // warps claim tiles of 32 paths
+    const int64_t tiles = (n_paths + lv::paths_per_tile(greeks) - 1) / lv::paths_per_tile(greeks);   // claimed by warps
     p->n_tiles = (int)tiles;
     const int64_t want_blocks = (tiles + warps - 1) / warps;
     const int64_t slots = (int64_t)p->bps * h->num_sms;
@@ -885,7 +885,7 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     st = choose_launch(h, n_steps, true, &block, &k, &bps, false, &grid_smem);
     if (st != LV_OK) return st;
     const int warps = block / 32;
-    const int64_t tiles = (n_paths + 31) / 32;
+    const int64_t tiles = (n_paths + lv::paths_per_tile(true) - 1) / lv::paths_per_tile(true);
     const int64_t want_blocks = (tiles + warps - 1) / warps;
     const int64_t slots = (int64_t)bps * h->num_sms;
     int grid = (int)(want_blocks < slots ? want_blocks : slots);

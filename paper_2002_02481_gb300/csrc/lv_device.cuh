@@ -218,6 +218,49 @@ __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid&
     return x;
 }
 
+// Forward passes of two paths, interleaved so the scheduler has two
+// independent dependency chains; each path's arithmetic is exactly that of
+// forward_path (its checkpoints and terminal state are bit-identical), and
+// the per-step time data is loaded once for both. Path b is logged only
+// when log_b (it may lie past the end of the call's range).
+template <int KCK, bool STORE, bool DBG>
+__device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid& g, uint32_t c1a, uint32_t c2a,
+                                              uint32_t c1b, uint32_t c2b, float* cka, float* ckb, size_t cks,
+                                              long long rel_a, long long rel_b, bool log_b, float& ya_out,
+                                              float& yb_out)
+{
+    float ya = P.x0, yb = P.x0;
+    float za[4], zb[4];
+    const int nseg = (P.N + KCK - 1) / KCK;
+    for (int m = 0; m < nseg; ++m) {
+        if (STORE) {
+            cka[(size_t)m * cks] = ya;
+            ckb[(size_t)m * cks] = yb;
+        }
+#pragma unroll
+        for (int q = 0; q < KCK; ++q) {
+            const int n = m * KCK + q;
+            if (n < P.N) {
+                if ((q & 3) == 0) {
+                    normals4((uint32_t)(n >> 2), c1a, c2a, P.k0, P.k1, za);
+                    normals4((uint32_t)(n >> 2), c1b, c2b, P.k0, P.k1, zb);
+                }
+                const int4 tb = g.tab[n];
+                const StepEval ea = eval_sigma<false>(P, g, ya, tb);
+                const StepEval eb = eval_sigma<false>(P, g, yb, tb);
+                if (DBG) {
+                    log_cell_decision(P, g, ea, rel_a, n);
+                    if (log_b) log_cell_decision(P, g, eb, rel_b, n);
+                }
+                ya = euler_step(P, ya, ea.sigma, za[q & 3]);
+                yb = euler_step(P, yb, eb.sigma, zb[q & 3]);
+            }
+        }
+    }
+    ya_out = ya;
+    yb_out = yb;
+}
+
 // Philox counter words of path `rel` of the call: c1 = path bits 0..31,
 // c2 = path bits 32..47 | stream_id << 16 (the path index is path_begin + rel).
 __device__ __forceinline__ void path_counter(const McParams& P, long long rel, uint32_t& c1, uint32_t& c2)

@@ -49,7 +49,7 @@ struct McParams {
     long long n_paths;
 
     // work decomposition and scratch
-    int n_tiles;           // ceil(n_paths / 32): tiles of 32 paths claimed by warps
+    int n_tiles;           // ceil(n_paths / paths_per_tile()): tiles claimed by warps
     unsigned int* tile_counter;   // zero before the launch, reset by the finalize
     double* partials;      // [gridDim.x][row_words] per-block binary64 rows
     int row_words;         // 3 + Je * I (adjoint) or 3 (price only)
@@ -120,6 +120,7 @@ cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
 cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, size_t smem,
                          int* blocks_per_sm);
 int ring_slots_per_warp();
+int paths_per_tile(bool greeks);   // paths a warp claims at a time (adjoint / price kernel)
 
 }  // namespace lv
 

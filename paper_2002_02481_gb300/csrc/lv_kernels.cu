@@ -43,8 +43,10 @@ namespace lv {
 
 namespace {
 
-constexpr int kRing = 4;       // checkpoint slot groups of 32 per warp
-constexpr int kQueue = 64;     // per-warp FIFO capacity (entries)
+constexpr int kTile = 32;      // paths per warp tile of the adjoint kernel (one per lane)
+constexpr int kPriceTile = 64; // paths per warp tile of the price kernel (two per lane)
+constexpr int kRing = 4;       // checkpoint slot groups of kTile per warp
+constexpr int kQueue = 64;     // per-warp FIFO capacity (entries; < 32 + kTile never overflows)
 constexpr int kMaxWarps = 8;   // blockDim.x <= 256 (the adjoint kernel runs at most 128)
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -206,8 +208,8 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
     const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
                       GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
-    const size_t cks = (size_t)gridDim.x * W * kRing * 32;   // checkpoint stride
-    float* const ckw = P.ckpt + (size_t)wid * kRing * 32;     // this warp's slots
+    const size_t cks = (size_t)gridDim.x * W * kRing * kTile;   // checkpoint stride
+    float* const ckw = P.ckpt + (size_t)wid * kRing * kTile;     // this warp's slots
 
     AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
     acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
     while (true) {
         const int g_next = (int)(fwd_count % kRing);
         const bool more = tile < P.n_tiles;
-        const bool reuse = more && q_count > 0 && (q_slot[q_head] >> 5) == g_next;
+        const bool reuse = more && q_count > 0 && q_slot[q_head] / kTile == g_next;
         if (q_count >= 32 || (!more && q_count > 0) || reuse) {
             // ---------------- reverse batch over up to 32 queued paths
             const int nb = min(32, q_count);
@@ -242,9 +244,9 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
         if (!more) break;
 
         // ---------------- forward tile of 32 paths into slot group g_next
-        const long long rel = (long long)tile * 32 + lane;
+        const long long rel = (long long)tile * kTile + lane;
         const bool active = rel < P.n_paths;
-        const int slot = g_next * 32 + lane;
+        const int slot = g_next * kTile + lane;
         float xbarN = 0.0f;
         if (active) {
             uint32_t c1, c2;
@@ -309,15 +311,24 @@ __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ M
     AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + threadIdx.x;
     acc[0] = acc[blockDim.x] = AccSlot{0.0, 0.0f, 0.0f};
     for (int tile = claim_tile(P.tile_counter); tile < P.n_tiles; tile = claim_tile(P.tile_counter)) {
-        const long long rel = (long long)tile * 32 + lane;
-        if (rel < P.n_paths) {
-            uint32_t c1, c2;
-            path_counter(P, rel, c1, c2);
-            const float x = forward_path<4, false, false>(P, g, c1, c2, nullptr, 0, rel);
-            const float itm = P.phi * (exp2f(x) - P.K);
-            const float V = itm > 0.0f ? P.disc * itm : 0.0f;
+        const long long rel_a = (long long)tile * kPriceTile + lane, rel_b = rel_a + 32;
+        if (rel_a < P.n_paths) {
+            uint32_t c1a, c2a, c1b, c2b;
+            path_counter(P, rel_a, c1a, c2a);
+            path_counter(P, rel_b, c1b, c2b);
+            float ya, yb;
+            forward_path2<4, false, false>(P, g, c1a, c2a, c1b, c2b, nullptr, nullptr, 0, rel_a, rel_b, false, ya,
+                                           yb);
+            float itm = P.phi * (exp2f(ya) - P.K);
+            float V = itm > 0.0f ? P.disc * itm : 0.0f;
             acc_add<ACC>(acc[0], V);
             acc_add<ACC>(acc[blockDim.x], V * V);
+            if (rel_b < P.n_paths) {
+                itm = P.phi * (exp2f(yb) - P.K);
+                V = itm > 0.0f ? P.disc * itm : 0.0f;
+                acc_add<ACC>(acc[0], V);
+                acc_add<ACC>(acc[blockDim.x], V * V);
+            }
         }
     }
     double* s_red = reinterpret_cast<double*>(smem + L.red);
@@ -441,7 +452,8 @@ size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_sme
     return smem_layout(I, Je, N, block, greeks, grid_smem).total;
 }
 
-int ring_slots_per_warp() { return kRing * 32; }
+int ring_slots_per_warp() { return kRing * kTile; }
+int paths_per_tile(bool greeks) { return greeks ? kTile : kPriceTile; }
 
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s)
