@@ -858,7 +858,8 @@ size_t static_plan_bytes(const lv_surface_s* h, int grid, int block, int k, int 
     size_t o = 256;                                               // [0, 256): tile counter
     *off_part = o;   o = round_up(o + sizeof(double) * (size_t)grid * row_words, 256);
     *off_chunks = o; o = round_up(o + sizeof(double) * (size_t)lv::finalize_chunks(grid) * row_words, 256);
-    *off_wrows = o;  o = round_up(o + sizeof(double) * warps * nIJ, 256);
+    *off_wrows = o;                                               // per-warp rows: Kahan mode only
+    if (h->acc_mode == LV_ACC_KAHAN) o = round_up(o + sizeof(double) * warps * nIJ, 256);
     *off_l1 = o;     o = round_up(o + sizeof(float) * (size_t)grid * nIJ, 256);
     *off_ckpt = o;   o = round_up(o + sizeof(float) * n_ck * warps * lv::ring_slots_per_warp(), 256);
     return o;
@@ -890,10 +891,21 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     const int64_t slots = (int64_t)bps * h->num_sms;
     int grid = (int)(want_blocks < slots ? want_blocks : slots);
     size_t off_part = 0, off_chunks = 0, off_wrows = 0, off_l1 = 0, off_ckpt = 0;
-    // fewer blocks until the launch fits in the static scratch
-    while (grid > 1 && static_plan_bytes(h, grid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
-                                         &off_ckpt) > kStaticScratchBytes)
-        grid = grid * 7 / 8;
+    // the most blocks (at most the full-width grid) whose scratch fits in the static array;
+    // the plan's size grows with the grid, so bisect
+    if (static_plan_bytes(h, grid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1, &off_ckpt) >
+        kStaticScratchBytes) {
+        int lo = 1, hi = grid - 1;
+        while (lo < hi) {
+            const int mid = lo + (hi - lo + 1) / 2;
+            if (static_plan_bytes(h, mid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
+                                  &off_ckpt) <= kStaticScratchBytes)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        grid = lo;
+    }
     const size_t need = static_plan_bytes(h, grid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
                                           &off_ckpt);
     if (need > kStaticScratchBytes)
