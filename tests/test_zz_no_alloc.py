@@ -68,3 +68,28 @@ def test_rejects_arguments_outside_the_domain():
                                             out.data_ptr())
     assert st == lv.LV_EINVAL and b"n_paths" in lib.lv_last_error()
     s.close()
+
+
+def test_large_grid_fits_the_array_in_passes():
+    """A 100 x 100 grid at 1,260 steps: a full-width launch overflows the
+    array, so the plan runs fewer blocks; the results still match the
+    allocating entry point."""
+    lib, lv, torch = _lib()
+    surf = W.random_surface(5, 100, 100, s_lo=20.0, s_hi=300.0, t_hi=5.0)
+    opt = W.Option(S0=100.0, r=0.0, K=100.0, T=5.0, n_steps=1260, n_paths=1 << 15, seed=3)
+    s = lv.Surface.from_workload(surf, lib)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    n = 3 + surf.n_spot * surf.n_time
+    ref = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, ref.data_ptr())
+    out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    st = lib.lv_price_greeks_device_noalloc(s.h, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths,
+                                            opt.seed, out.data_ptr())
+    assert st == lv.LV_OK, lib.lv_last_error().decode()
+    torch.cuda.synchronize()
+    r, o = ref.cpu().numpy(), out.cpu().numpy()
+    assert np.all(np.isfinite(o))
+    assert abs(o[0] - r[0]) <= 1e-12 * abs(r[0])
+    assert abs(o[1] - r[1]) <= 1e-9 * abs(r[1])
+    assert np.max(np.abs(o[3:] - r[3:])) <= 1e-6 * np.max(np.abs(r[3:]))
+    s.close()
