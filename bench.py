@@ -206,10 +206,11 @@ def other_workloads(lib, dev, ev0, ev1):
     res = {}
     stream = torch.cuda.current_stream(dev)
 
-    def single(name, surf, opt, launch=None, acc=0):
+    def single(name, surf, opt, launch=None, acc=0, method=lv.LV_ADJ_REVERSE):
         S = lv.Surface.from_workload(surf, lib)
         S.set_stream(stream.cuda_stream)
         S.set_accumulation(acc)
+        S.set_adjoint_method(method)
         if launch:
             S.set_launch(*launch)
         S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
@@ -221,6 +222,12 @@ def other_workloads(lib, dev, ev0, ev1):
         S.close()
 
     single("small 20x10, 52 steps, 2^14 paths", *W.config_small())
+    # the tangent-ratio form of the adjoint (two forward passes, no checkpoints)
+    single("tangent-ratio adjoint, 30x60, 156 steps, 2^20 paths", *W.config_paper_shape(),
+           method=lv.LV_ADJ_TANGENT)
+    single("tangent-ratio adjoint, 30x60, 156 steps, 2^24 paths", *W.config_precision("paper"),
+           method=lv.LV_ADJ_TANGENT)
+    single("tangent-ratio adjoint, 100x100, 1260 steps, 2^26 paths", *W.config_large(), method=lv.LV_ADJ_TANGENT)
     for which in ("small", "paper"):
         surf, opt = W.config_precision(which)
         for acc, nm in ((0, "binary64"), (1, "Kahan")):

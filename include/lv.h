@@ -59,12 +59,29 @@ typedef enum {
     LV_EINVAL = 1,      /* an argument is out of its documented domain */
     LV_ENOMEM = 2,      /* a host or device allocation failed */
     LV_ECUDA = 3,       /* a CUDA runtime call failed (message in lv_last_error) */
-    LV_EINTERNAL = 4    /* a consistency check inside the library failed */
+    LV_EINTERNAL = 4,   /* a consistency check inside the library failed */
+    LV_ENUMERIC = 5     /* the tangent-ratio adjoint met a vanishing factor 1 + g_n (see
+                           lv_set_adjoint_method); the outputs are NaN */
 } lv_status;
 
 /* Level-2 (per-block, across path tiles) accumulation of the payoffs and of
  * every vega bucket. */
 enum { LV_ACC_FP64 = 0, LV_ACC_KAHAN = 1 };
+
+/* How the pathwise adjoint (Sec. III, IV-C) is evaluated; both give the same
+ * derivatives up to rounding.
+ *  - LV_ADJ_REVERSE (default): back-propagation through the Euler scheme,
+ *    x_bar_n = x_bar_{n+1} (1 + g_n), on checkpoints every k steps.
+ *  - LV_ADJ_TANGENT: the recursion is linear, so x_bar_{n+1} =
+ *    x_bar_N D_N / D_{n+1} with D_0 = 1, D_{n+1} = D_n (1 + g_n) (the tangent
+ *    process d x_n / d x_0). A first forward pass gives D_N per path, hence
+ *    x_bar_0 = x_bar_N D_N; a second forward pass over the paths with
+ *    x_bar_N != 0 spreads sigma_bar_n = x_bar_N D_N h_n / D_{n+1}. No
+ *    checkpoints, no reverse order. When some |1 + g_n| falls below 2^-20 the
+ *    ratio loses what the reverse sweep keeps: every output of the call is
+ *    then NaN and the host-side entry points return LV_ENUMERIC.
+ * g_n = h_n S_n d sigma / d S and h_n = sqrt(dt) Z_n - sigma_n dt. */
+enum { LV_ADJ_REVERSE = 0, LV_ADJ_TANGENT = 1 };
 
 /* Layout of the [3 + n_spot * n_time] result of lv_price_greeks_device. */
 enum { LV_OUT_PRICE = 0, LV_OUT_DELTA = 1, LV_OUT_STDERR = 2, LV_OUT_VEGA = 3 };
@@ -110,6 +127,10 @@ lv_status lv_set_stream(lv_surface_t h, void* cuda_stream);
 
 /* LV_ACC_FP64 (default) or LV_ACC_KAHAN. */
 lv_status lv_set_accumulation(lv_surface_t h, int32_t mode);
+
+/* LV_ADJ_REVERSE (default) or LV_ADJ_TANGENT, for every greeks entry point
+ * of the handle except lv_debug_paths (always the reverse sweep). */
+lv_status lv_set_adjoint_method(lv_surface_t h, int32_t method);
 
 /* Launch shape: threads per block (32..128, multiple of 32), checkpoint
  * interval k of the reverse sweep (4, 8, 16 or 32 steps) and resident

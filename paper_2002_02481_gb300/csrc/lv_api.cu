@@ -176,7 +176,7 @@ std::string adjoint_tune_key(const lv_surface_s* h, int32_t n_steps)
 {
     int nb = 0;
     for (int n = n_steps; n > 1; n >>= 1) ++nb;
-    return "adjoint|" + lv::gpu_name(h->device) + "|" + std::to_string(h->I) + "x" + std::to_string(h->J) +
+    return std::string(h->adj_method == LV_ADJ_TANGENT ? "tangent|" : "adjoint|") + lv::gpu_name(h->device) + "|" + std::to_string(h->I) + "x" + std::to_string(h->J) +
            "|N2^" + std::to_string(nb);
 }
 
@@ -204,7 +204,8 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
     if (smem > 200 * 1024)
         return fail(LV_EINVAL, "time table does not fit in shared memory (" + std::to_string(smem) + " bytes)");
     int occ = 0;
-    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, gs, smem, &occ));
+    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, gs, dbg ? 0 : h->adj_method, smem,
+                             &occ));
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
     *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
     return LV_OK;
@@ -222,7 +223,9 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     const int64_t slots = (int64_t)p->bps * h->num_sms;
     p->grid = (int)(want_blocks < slots ? want_blocks : slots);
     if (p->grid < 1) p->grid = 1;
-    p->n_ck = greeks ? (n_steps + p->k - 1) / p->k : 0;
+    // the tangent-ratio adjoint keeps no checkpoints
+    const bool reverse = dbg || h->adj_method == LV_ADJ_REVERSE;
+    p->n_ck = greeks && reverse ? (n_steps + p->k - 1) / p->k : 0;
     const size_t nIJ = (size_t)h->Je * h->I;
     p->row_words = greeks ? 3 + (int)nIJ : 3;             // price-only rows hold the scalars
     p->n_chunks = lv::finalize_chunks(p->grid);
@@ -313,6 +316,7 @@ lv::McParams base_params(const lv_surface_s* h, const McCall& c)
     P.path_begin = c.path_begin;
     P.n_paths = c.n_paths;
     P.acc_mode = h->acc_mode;
+    P.method = LV_ADJ_REVERSE;
     return P;
 }
 
@@ -349,6 +353,10 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     P.dbg_ev_count = c.dbg_ev_count;
     P.dbg_ev_cap = c.dbg_ev_cap;
     P.dbg_band = (float)c.dbg_band;
+    if (c.greeks && !c.dbg_xN && h->adj_method == LV_ADJ_TANGENT) {
+        P.method = LV_ADJ_TANGENT;
+        P.flag = P.tile_counter + 1;      // in the zeroed counter section; the finalize resets it
+    }
     if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
     LV_CUDA(lv::launch_mc(P, p.grid, p.block, p.k, c.greeks, p.smem, h->stream));
     if (h->ev_end) LV_CUDA(cudaEventRecord(h->ev_end, h->stream));
@@ -364,6 +372,7 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     F.chunks = reinterpret_cast<double*>(base + p.off_chunks);
     F.out = c.d_out;
     F.tile_counter = P.tile_counter;
+    F.flag = P.flag;
     LV_CUDA(lv::launch_finalize(F, h->stream));
     return LV_OK;
 }
@@ -518,6 +527,15 @@ lv_status lv_set_accumulation(lv_surface_t h, int32_t mode)
     return LV_OK;
 }
 
+lv_status lv_set_adjoint_method(lv_surface_t h, int32_t method)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (method != LV_ADJ_REVERSE && method != LV_ADJ_TANGENT)
+        return fail(LV_EINVAL, "method must be LV_ADJ_REVERSE or LV_ADJ_TANGENT");
+    h->adj_method = method;
+    return LV_OK;
+}
+
 lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks_per_sm)
 {
     if (!h) return fail(LV_EINVAL, "handle is NULL");
@@ -598,6 +616,8 @@ lv_status lv_price_greeks(lv_surface_t h, double S0, double r, double K, double 
     *out_price = h->h_res[LV_OUT_PRICE];
     *out_delta = h->h_res[LV_OUT_DELTA];
     std::memcpy(out_vega, h->h_res + LV_OUT_VEGA, sizeof(double) * (size_t)h->I * h->J);
+    if (std::isnan(h->h_res[LV_OUT_PRICE]))
+        return fail(LV_ENUMERIC, "a factor 1 + g_n vanished on a live path: use LV_ADJ_REVERSE for this grid");
     return LV_OK;
 }
 
@@ -854,8 +874,8 @@ size_t static_plan_bytes(const lv_surface_s* h, int grid, int block, int k, int 
     const size_t nIJ = (size_t)h->Je * h->I;
     const size_t row_words = 3 + nIJ;
     const size_t warps = (size_t)grid * (block / 32);
-    const size_t n_ck = (size_t)((n_steps + k - 1) / k);
-    size_t o = 256;                                               // [0, 256): tile counter
+    const size_t n_ck = h->adj_method == LV_ADJ_TANGENT ? 0 : (size_t)((n_steps + k - 1) / k);
+    size_t o = 256;                                               // [0, 256): tile counter, flag
     *off_part = o;   o = round_up(o + sizeof(double) * (size_t)grid * row_words, 256);
     *off_chunks = o; o = round_up(o + sizeof(double) * (size_t)lv::finalize_chunks(grid) * row_words, 256);
     *off_wrows = o;                                               // per-warp rows: Kahan mode only
@@ -923,12 +943,16 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     P.warp_rows = reinterpret_cast<double*>(base + off_wrows);
     P.l1 = reinterpret_cast<float*>(base + off_l1);
     P.ckpt = reinterpret_cast<float*>(base + off_ckpt);
-    P.n_ck = (n_steps + k - 1) / k;
+    P.n_ck = h->adj_method == LV_ADJ_TANGENT ? 0 : (n_steps + k - 1) / k;
     P.flush_every = 8;
     P.grid_smem = grid_smem ? 1 : 0;
-    // the array keeps the previous call's contents: the tile counter must start at zero
-    // (every other section is written before it is read)
-    LV_CUDA(cudaMemsetAsync(P.tile_counter, 0, sizeof(unsigned int), h->stream));
+    if (h->adj_method == LV_ADJ_TANGENT) {
+        P.method = LV_ADJ_TANGENT;
+        P.flag = P.tile_counter + 1;
+    }
+    // the array keeps the previous call's contents: the tile counter and the
+    // flag must start at zero (every other section is written before it is read)
+    LV_CUDA(cudaMemsetAsync(P.tile_counter, 0, 2 * sizeof(unsigned int), h->stream));
     const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, block, true, grid_smem);
     LV_CUDA(lv::launch_mc(P, grid, block, k, true, smem, h->stream));
     lv::FinalizeParams F{};
@@ -943,6 +967,7 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     F.chunks = reinterpret_cast<double*>(base + off_chunks);
     F.out = d_out;
     F.tile_counter = P.tile_counter;
+    F.flag = P.flag;
     LV_CUDA(lv::launch_finalize(F, h->stream));
     return LV_OK;
 }

@@ -350,4 +350,95 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
     return xbar;
 }
 
+// Tangent-ratio form of the pathwise adjoint (Sec. III: the adjoint
+// recursion xbar_n = xbar_{n+1} (1 + g_n) is linear, so with the tangent
+// D_0 = 1, D_{n+1} = D_n (1 + g_n) = d x_{n+1} / d x_0 one has
+// xbar_{n+1} = xbar_N D_N / D_{n+1} and xbar_0 = xbar_N D_N).
+//
+// Pass 1: the forward pass of one path keeping D. Returns y_N = log2 S_N and
+// D_N; `tiny` is set when some |1 + g_n| < 2^-20, where dividing by D loses
+// what the reverse sweep keeps. The path's arithmetic is that of
+// forward_path (same sigma, same Euler step), so y_N is the same.
+__device__ __forceinline__ float tangent_forward(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
+                                                 float& D, bool& tiny)
+{
+    float y = P.x0;
+    float d = 1.0f, fmin = 1.0f;
+    float z[4];
+    for (int n0 = 0; n0 < P.N; n0 += 4) {
+        normals4((uint32_t)(n0 >> 2), c1, c2, P.k0, P.k1, z);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = n0 + q;
+            if (n < P.N) {
+                const int4 tb = g.tab[n];
+                const StepEval e = eval_sigma<true>(P, g, y, tb);
+                const float h = fmaf(P.sqdt, z[q], -e.sigma * P.dt);
+                const float f = fmaf(h, e.S * e.slope, 1.0f);      // 1 + g_n
+                fmin = fminf(fmin, fabsf(f));
+                d *= f;
+                y = euler_step(P, y, e.sigma, z[q]);
+            }
+        }
+    }
+    D = d;
+    tiny = fmin < 0x1p-20f;
+    return y;
+}
+
+// Pass 2: regenerates one path (same counters, same arithmetic) and spreads
+// sigma_bar_n = c h_n / D_{n+1}, c = xbar_N D_N, over the corner buckets of
+// its cell with the bilinear weights, through the same run-length register
+// sums and binary32 reductions into `l1` as reverse_path, in time order.
+__device__ __forceinline__ void tangent_scatter(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
+                                                float c, float* l1)
+{
+    float y = P.x0, d = 1.0f;
+    int cur = -1;
+    float A = 0.0f, AU = 0.0f, Bs = 0.0f, BU = 0.0f;
+    float z[4];
+    for (int n0 = 0; n0 < P.N; n0 += 4) {
+        normals4((uint32_t)(n0 >> 2), c1, c2, P.k0, P.k1, z);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = n0 + q;
+            if (n < P.N) {
+                const int4 tb = g.tab[n];
+                const StepEval e = eval_sigma<true>(P, g, y, tb);
+                const float h = fmaf(P.sqdt, z[q], -e.sigma * P.dt);
+                d *= fmaf(h, e.S * e.slope, 1.0f);                // D_{n+1}
+                const float sbar = __fdividef(c * h, d);
+                const int key = tb.z + e.i;
+                if (key != cur) {
+                    if (cur >= 0) {
+                        float* p0 = l1 + cur;
+                        float* p1 = p0 + P.I;
+                        atomicAdd(p0, A - AU);
+                        atomicAdd(p0 + 1, AU);
+                        atomicAdd(p1, Bs - BU);
+                        atomicAdd(p1 + 1, BU);
+                    }
+                    A = AU = Bs = BU = 0.0f;
+                    cur = key;
+                }
+                const float b = sbar * __int_as_float(tb.w);
+                const float a = sbar - b;
+                A += a;
+                AU = fmaf(a, e.u, AU);
+                Bs += b;
+                BU = fmaf(b, e.u, BU);
+                y = euler_step(P, y, e.sigma, z[q]);
+            }
+        }
+    }
+    if (cur >= 0) {
+        float* p0 = l1 + cur;
+        float* p1 = p0 + P.I;
+        atomicAdd(p0, A - AU);
+        atomicAdd(p0 + 1, AU);
+        atomicAdd(p1, Bs - BU);
+        atomicAdd(p1 + 1, BU);
+    }
+}
+
 }  // namespace lv

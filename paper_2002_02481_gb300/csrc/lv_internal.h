@@ -60,6 +60,8 @@ struct McParams {
     int flush_every;       // reverse batches between level-1 -> level-2 drains
     int grid_smem;         // 1: sigma pairs staged in shared memory, 0: read through L1
     int acc_mode;          // 0 binary64, 1 Kahan binary32
+    int method;            // LV_ADJ_REVERSE or LV_ADJ_TANGENT
+    unsigned int* flag;    // tangent-ratio adjoint: count of live paths with a vanishing 1 + g_n
 
     // per-path outputs and near-node decision log (debug entry point only;
     // dbg_xN != null selects the logging instantiation)
@@ -83,6 +85,7 @@ struct FinalizeParams {
     double* chunks;        // [finalize_chunks(G)][row_words] stage-1 sums
     double* out;           // [3 + I * J]
     unsigned int* tile_counter;  // reset to 0
+    unsigned int* flag;          // nonzero: every output NaN; reset to 0 (may be null)
 };
 
 int finalize_chunks(int G);
@@ -117,8 +120,8 @@ size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_sme
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, size_t smem,
-                         int* blocks_per_sm);
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method,
+                         size_t smem, int* blocks_per_sm);
 int ring_slots_per_warp();
 int paths_per_tile(bool greeks);   // paths a warp claims at a time (adjoint / price kernel)
 
@@ -194,6 +197,7 @@ std::string gpu_name(int device);
 struct lv_surface_s {
     int device = 0;
     int num_sms = 0;
+    int adj_method = 0;              // LV_ADJ_REVERSE or LV_ADJ_TANGENT
     int I = 0, J = 0, Je = 0;
     std::vector<double> spot, time;
     float2* d_sig = nullptr;         // [Je][I-1] pairs (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j})

@@ -297,6 +297,107 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
     block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
 }
 
+// Tangent-ratio adjoint (LV_ADJ_TANGENT): persistent and warp-centric like
+// adjoint_kernel, without checkpoints. A warp claims a tile of 32 paths and
+// runs pass 1 (tangent_forward): payoff, xbar_N, and xbar_0 = xbar_N D_N;
+// the paths with xbar_N != 0 join the warp's queue with c = xbar_N D_N. At
+// 32 queued paths (and at the end) the warp runs pass 2 (tangent_scatter)
+// on them as a full-warp batch. Buckets go through the same levels 0-3.
+template <int ACC, bool GS>
+__global__ void __launch_bounds__(128, 6) tangent_kernel(const __grid_constant__ McParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B = blockDim.x, W = B >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
+    stage_grid<GS>(P, smem, L);
+    float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);
+    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
+    float* q_c = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
+    double* s_red = reinterpret_cast<double*>(smem + L.red);
+    const int nIJ = P.Je * P.I;
+    for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
+    const int wid = blockIdx.x * W + warp;
+    double* const row = P.partials + (size_t)blockIdx.x * P.row_words;
+    double* wrow;
+    if (ACC == 1) {
+        wrow = P.warp_rows + (size_t)wid * nIJ;
+        for (int e = lane; e < nIJ; e += 32) wrow[e] = 0.0;
+    } else {
+        wrow = row + 3;
+        for (int e = tid; e < nIJ; e += B) wrow[e] = 0.0;
+    }
+    __syncthreads();
+    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
+                      GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
+                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
+    AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
+    acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
+    int q_head = 0, q_count = 0, batches = 0;
+    int tile = claim_tile(P.tile_counter);
+    while (true) {
+        const bool more = tile < P.n_tiles;
+        if (q_count >= 32 || (!more && q_count > 0)) {
+            const int nb = min(32, q_count);
+            if (lane < nb) {
+                const int e = (q_head + lane) & (kQueue - 1);
+                uint32_t c1, c2;
+                path_counter(P, q_rel[e], c1, c2);
+                tangent_scatter(P, g, c1, c2, q_c[e], l1);
+            }
+            q_head = (q_head + nb) & (kQueue - 1);
+            q_count -= nb;
+            __syncwarp();
+            if (++batches % P.flush_every == 0) drain_buckets<ACC>(l1, nIJ, wrow);
+            continue;
+        }
+        if (!more) break;
+        const long long rel = (long long)tile * kTile + lane;
+        float xbarN = 0.0f, c = 0.0f;
+        if (rel < P.n_paths) {
+            uint32_t c1, c2;
+            path_counter(P, rel, c1, c2);
+            float D;
+            bool tiny;
+            const float y = tangent_forward(P, g, c1, c2, D, tiny);
+            const float SN = exp2f(y);
+            const float itm = P.phi * (SN - P.K);
+            const float V = itm > 0.0f ? P.disc * itm : 0.0f;
+            xbarN = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
+            c = xbarN * D;
+            acc_add<ACC>(acc[0], V);
+            acc_add<ACC>(acc[B], V * V);
+            acc_add<ACC>(acc[2 * B], c);
+            if (tiny && xbarN != 0.0f) atomicAdd(P.flag, 1u);
+        }
+        const bool live = xbarN != 0.0f;
+        const unsigned bal = __ballot_sync(0xffffffffu, live);
+        if (live) {
+            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
+            q_rel[e] = (int)rel;
+            q_c[e] = c;
+        }
+        q_count += __popc(bal);
+        __syncwarp();
+        tile = claim_tile(P.tile_counter);
+    }
+    __syncthreads();
+    const double* rows0 = P.warp_rows + (size_t)blockIdx.x * W * nIJ;
+    for (int e = tid; e < nIJ; e += B) {
+        if (ACC == 1) {
+            double s = (double)l1[e];
+            for (int w = 0; w < W; ++w) {
+                const float2 k = reinterpret_cast<const float2*>(rows0 + (size_t)w * nIJ)[e];
+                s += (double)k.x - (double)k.y;
+            }
+            row[3 + e] = s;
+        } else {
+            row[3 + e] += (double)l1[e];
+        }
+    }
+    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
+}
+
 template <int ACC, bool GS>
 __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ McParams P)
 {
@@ -340,8 +441,10 @@ __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ M
 // column by column, into one binary64 row per chunk.
 constexpr int kRowsPerChunk = 32;
 
+// A nonzero *flag (the tangent-ratio adjoint met a vanishing 1 + g_n) makes
+// every sum, and so every output, NaN.
 __global__ void reduce_rows_kernel(const double* __restrict__ partials, int G, int row_words,
-                                   double* __restrict__ chunks)
+                                   const unsigned int* flag, double* __restrict__ chunks)
 {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= row_words) return;
@@ -349,6 +452,7 @@ __global__ void reduce_rows_kernel(const double* __restrict__ partials, int G, i
     const int r1 = min(G, r0 + kRowsPerChunk);
     double s = 0.0;
     for (int r = r0; r < r1; ++r) s += partials[(size_t)r * row_words + col];
+    if (flag && *flag) s = __longlong_as_double(0x7ff8000000000000ll);
     chunks[(size_t)blockIdx.y * row_words + col] = s;
 }
 
@@ -356,7 +460,7 @@ __global__ void reduce_rows_kernel(const double* __restrict__ partials, int G, i
 // (vega spot-major), price statistics from the scalar sums.
 __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks, int row_words,
                                 int I, int J, long long n_paths, double S0, int want_sums,
-                                double* __restrict__ out, unsigned int* tile_counter)
+                                double* __restrict__ out, unsigned int* tile_counter, unsigned int* flag)
 {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= row_words) return;
@@ -377,6 +481,7 @@ __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks,
             out[LV_OUT_DELTA_DEV] = s / (P * S0);
         }
         if (col == 0 && tile_counter) *tile_counter = 0u;
+        if (col == 0 && flag) *flag = 0u;
         return;
     }
     const int e = col - 3;             // time-major bucket j * I + i
@@ -414,11 +519,15 @@ cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
 
 // Calls f(kernel, flag) with the instantiation for (greeks, k, acc, dbg, gs).
 template <bool GS, typename F>
-cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, F&& f)
+cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, F&& f)
 {
     if (!greeks) {
         static bool c0 = false, c1 = false;
         return acc ? f(price_kernel<1, GS>, c1) : f(price_kernel<0, GS>, c0);
+    }
+    if (method == LV_ADJ_TANGENT && !dbg) {
+        static bool t0 = false, t1 = false;
+        return acc ? f(tangent_kernel<1, GS>, t1) : f(tangent_kernel<0, GS>, t0);
     }
     if (dbg) {
         static bool cd = false;
@@ -440,9 +549,10 @@ cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, F&& f)
 }
 
 template <typename F>
-cudaError_t with_kernel(bool greeks, int k, int acc, bool dbg, bool gs, F&& f)
+cudaError_t with_kernel(bool greeks, int k, int acc, bool dbg, bool gs, int method, F&& f)
 {
-    return gs ? with_kernel_gs<true>(greeks, k, acc, dbg, f) : with_kernel_gs<false>(greeks, k, acc, dbg, f);
+    return gs ? with_kernel_gs<true>(greeks, k, acc, dbg, method, f)
+              : with_kernel_gs<false>(greeks, k, acc, dbg, method, f);
 }
 
 }  // namespace
@@ -458,15 +568,16 @@ int paths_per_tile(bool greeks) { return greeks ? kTile : kPriceTile; }
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s)
 {
-    return with_kernel(greeks, k, p.acc_mode, p.dbg_xN != nullptr, p.grid_smem != 0,
+    return with_kernel(greeks, k, p.acc_mode, p.dbg_xN != nullptr, p.grid_smem != 0, p.method,
                        [&](auto kernel, bool& configured) {
                            return launch_configured(kernel, configured, p, grid, block, smem, s);
                        });
 }
 
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, size_t smem, int* bps)
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, size_t smem,
+                         int* bps)
 {
-    return with_kernel(greeks, k, acc, dbg, grid_smem,
+    return with_kernel(greeks, k, acc, dbg, grid_smem, method,
                        [&](auto kernel, bool&) { return occupancy(kernel, block, smem, bps); });
 }
 
@@ -474,12 +585,12 @@ cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s)
 {
     const int n_chunks = (f.G + kRowsPerChunk - 1) / kRowsPerChunk;
     dim3 g1((f.row_words + 255) / 256, n_chunks);
-    reduce_rows_kernel<<<g1, 256, 0, s>>>(f.partials, f.G, f.row_words, f.chunks);
+    reduce_rows_kernel<<<g1, 256, 0, s>>>(f.partials, f.G, f.row_words, f.flag, f.chunks);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finalize_kernel<<<(f.row_words + 255) / 256, 256, 0, s>>>(f.chunks, n_chunks, f.row_words, f.I, f.J,
                                                               f.n_paths, f.S0, f.want_sums, f.out,
-                                                              f.tile_counter);
+                                                              f.tile_counter, f.flag);
     return cudaGetLastError();
 }
 

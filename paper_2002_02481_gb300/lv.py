@@ -19,8 +19,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblv_gb300.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "lv.h")
 
-LV_OK, LV_EINVAL, LV_ENOMEM, LV_ECUDA, LV_EINTERNAL = range(5)
+LV_OK, LV_EINVAL, LV_ENOMEM, LV_ECUDA, LV_EINTERNAL, LV_ENUMERIC = range(6)
 LV_ACC_FP64, LV_ACC_KAHAN = 0, 1
+LV_ADJ_REVERSE, LV_ADJ_TANGENT = 0, 1
 LV_OUT_PRICE, LV_OUT_DELTA, LV_OUT_STDERR, LV_OUT_VEGA = 0, 1, 2, 3
 LV_SUM_V, LV_SUM_V2, LV_SUM_XBAR0, LV_SUM_VEGA = 0, 1, 2, 3
 
@@ -67,6 +68,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_set_option_type": [vp, i32],
         "lv_set_stream": [vp, vp],
         "lv_set_accumulation": [vp, i32],
+        "lv_set_adjoint_method": [vp, i32],
         "lv_set_launch": [vp, i32, i32, i32],
         "lv_set_kernel_events": [vp, vp, vp],
         "lv_tune": [vp, d, d, d, d, i32, i64, u64, c.POINTER(i32), c.POINTER(i32), c.POINTER(d)],
@@ -164,6 +166,10 @@ class Surface:
 
     def set_accumulation(self, mode: int) -> None:
         _check(self.lib, self.lib.lv_set_accumulation(self.h, int(mode)), "lv_set_accumulation")
+
+    def set_adjoint_method(self, method: int) -> None:
+        """LV_ADJ_REVERSE (checkpointed reverse sweep) or LV_ADJ_TANGENT (tangent ratio)."""
+        _check(self.lib, self.lib.lv_set_adjoint_method(self.h, int(method)), "lv_set_adjoint_method")
 
     def set_launch(self, block: int = 0, k: int = 0, blocks_per_sm: int = 0) -> None:
         _check(self.lib, self.lib.lv_set_launch(self.h, int(block), int(k), int(blocks_per_sm)), "lv_set_launch")

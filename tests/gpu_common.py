@@ -29,10 +29,11 @@ X_ATOL = 1e-4            # per-path |x_N(binary32) - x_N(binary64)|
 NODE_BAND = 2e-4         # logged steps: |S - s| <= NODE_BAND * s for a node s of the cell
 
 
-def make_surface(w_surf, opt, lib, launch=None, accumulation=0):
+def make_surface(w_surf, opt, lib, launch=None, accumulation=0, method=lv.LV_ADJ_REVERSE):
     s = lv.Surface.from_workload(w_surf, lib)
     s.set_option_type(opt.phi)
     s.set_accumulation(accumulation)
+    s.set_adjoint_method(method)
     if launch:
         s.set_launch(*launch)
     return s
@@ -90,10 +91,12 @@ def compare_aggregates(gpu_price, gpu_delta, gpu_vega, ref, label=""):
     return dict(price_rel=e_p, delta_rel=e_d, vega_of_max=e_v)
 
 
-def full_parity(w_surf, opt, lib, launch=None, accumulation=0, label=""):
+def full_parity(w_surf, opt, lib, launch=None, accumulation=0, label="", method=lv.LV_ADJ_REVERSE):
     """Per-path check on every path, then aggregates against the oracle with
-    the kernel's kink decisions imposed."""
-    gs = make_surface(w_surf, opt, lib, launch, accumulation)
+    the kernel's kink decisions imposed. The per-path check and the decisions
+    come from the reverse sweep's diagnostics kernel, whose forward arithmetic
+    the tangent-ratio kernel shares."""
+    gs = make_surface(w_surf, opt, lib, launch, accumulation, method)
     decisions, stats = per_path(gs, w_surf, opt)
     ref = oracle.finalize(oracle.run_sums(w_surf, opt, decisions=decisions), opt.n_paths, opt.S0,
                           w_surf.n_spot * w_surf.n_time)

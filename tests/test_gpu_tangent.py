@@ -1,0 +1,108 @@
+"""The tangent-ratio adjoint (LV_ADJ_TANGENT: x_bar_{n+1} = x_bar_N D_N /
+D_{n+1} with the tangent D_n = d x_n / d x_0) against the FP64 oracle's
+reverse-mode adjoint, element by element on the same seeded inputs, with the
+same tolerances as the checkpointed reverse sweep; and against that sweep on
+the same paths. Needs a GB300."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2002_02481_gb300 import build, lv
+
+from . import gpu_common as G
+from .test_gpu_parity import EDGE
+
+pytestmark = pytest.mark.gpu
+
+REPORT = os.environ.get("LV_PARITY_REPORT")
+T = lv.LV_ADJ_TANGENT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return lv.load()
+
+
+def _report(name, d):
+    if REPORT:
+        with open(REPORT, "a") as f:
+            f.write(json.dumps({"case": "tangent: " + name, **d}) + "\n")
+
+
+@pytest.mark.parametrize("case", EDGE, ids=[c[0] for c in EDGE])
+def test_edge_cases(case, lib):
+    name, surf, opt = case
+    _report(name, G.full_parity(surf, opt, lib, label=name, method=T))
+
+
+def test_small_config(lib):
+    surf, opt = W.config_small()
+    _report("20x10 grid, 52 steps, 2^14 paths", G.full_parity(surf, opt, lib, label="small", method=T))
+
+
+def test_paper_shape_full_size(lib):
+    surf, opt = W.config_paper_shape()
+    _report("30x60 grid, 156 steps, 2^20 paths", G.full_parity(surf, opt, lib, label="paper", method=T))
+
+
+@pytest.mark.parametrize("acc", [0, 1])
+def test_both_level2_modes(lib, acc):
+    surf, opt = W.config_precision("paper")
+    opt = W.Option(**{**opt.__dict__, "n_paths": 1 << 16})
+    _report(f"precision paper 2^16 acc={acc}",
+            G.full_parity(surf, opt, lib, accumulation=acc, label=f"acc={acc}", method=T))
+
+
+def test_matches_the_reverse_sweep_on_the_same_paths(lib):
+    """Same paths, same payoffs: the two forms differ only in rounding and
+    reduction order."""
+    surf, opt = W.config_large()
+    opt = W.Option(**{**opt.__dict__, "r": 0.01, "K": 110.0, "n_paths": 1 << 14, "seed": 4})
+    out = {}
+    for m in (lv.LV_ADJ_REVERSE, T):
+        s = G.make_surface(surf, opt, lib, method=m)
+        out[m] = s.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+        s.close()
+    (p0, d0, v0), (p1, d1, v1) = out[lv.LV_ADJ_REVERSE], out[T]
+    assert abs(p1 - p0) <= 1e-12 * abs(p0)
+    assert abs(d1 - d0) <= 1e-6 * abs(d0), (d0, d1)
+    assert np.max(np.abs(v1 - v0)) <= 1e-5 * np.max(np.abs(v0))
+
+
+def test_device_and_noalloc_entry_points(lib):
+    import ctypes
+    import torch
+    surf, opt = W.config_small()
+    s = G.make_surface(surf, opt, lib, method=T)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    n = 3 + surf.n_spot * surf.n_time
+    p, d, v = s.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    dev = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    s.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, dev.data_ptr())
+    f = lib.lv_price_greeks_device_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                  ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    na = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+    assert f(s.h, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, na.data_ptr()) == lv.LV_OK
+    torch.cuda.synchronize()
+    for o in (dev.cpu().numpy(), na.cpu().numpy()):
+        assert np.all(np.isfinite(o))
+        assert abs(o[0] - p) <= 1e-12 * abs(p)
+        assert abs(o[1] - d) <= 1e-9 * abs(d)
+        assert np.max(np.abs(o[3:].reshape(v.shape) - v)) <= 1e-6 * np.max(np.abs(v))
+    s.close()
+
+
+def test_rejects_an_unknown_method(lib):
+    surf, opt = W.config_small()
+    s = lv.Surface.from_workload(surf, lib)
+    with pytest.raises(lv.LVError):
+        s.set_adjoint_method(2)
+    s.close()
