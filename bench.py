@@ -254,6 +254,17 @@ def other_workloads(lib, dev, ev0, ev1):
         "ms_per_run_wall": wall * 1e3, "path_steps": ps, "path_steps_per_s": ps / wall,
         "paths": sum(it.n_paths for it in items), "tuned": {"block": blk, "k": k, "item_paths": item_paths,
                                                             "kernel_ms": tune_ms}}
+    # the same book as aggregated risk per surface (position weights +-1)
+    book.set_weights([1.0 if it.phi > 0 else -1.0 for it in items])
+    book.run_risk(100.0, 0.0, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for rep in range(reps):
+        book.run_risk(100.0, 0.0, 1 + rep)
+    wall = (time.perf_counter() - t0) / reps
+    res["book aggregated risk per surface, graph replay"] = {
+        "ms_per_run_wall": wall * 1e3, "path_steps": ps, "path_steps_per_s": ps / wall,
+        "outputs": book.risk_offsets[-1], "per_option_outputs": book.offsets[-1]}
     book.close()
     return res
 

@@ -301,6 +301,31 @@ lv_status lv_book_run_device(lv_book_t b, double S0, double r, uint64_t seed, do
 lv_status lv_book_tune(lv_book_t b, double S0, double r, uint64_t seed, int32_t* out_block, int32_t* out_k,
                        int32_t* out_item_paths, double* out_ms);
 
+/* Book-level aggregated risk (the portfolio view of the first-order risk of
+ * Sec. I and V: one set of vega buckets per surface instead of one per
+ * option). With position weights w_o (lv_book_set_weights; 1 by default),
+ * per surface s over its options o:
+ *   [0] sum_o w_o price_o, [1] sum_o w_o delta_o,
+ *   [2] sqrt(sum_o w_o^2 stderr_o^2)  (options on distinct Philox streams are
+ *       independent; options sharing a stream and surface are not, and this
+ *       figure then understates the error),
+ *   [3 + i * n_time + j] sum_o w_o vega_o[i][j].
+ * The persistent kernel adds each work item's vega buckets, scaled by
+ * w_o / n_paths_o, into its surface's binary64 sums; no per-option vega is
+ * written. Weights: [n_insts] finite doubles, copied; later runs use them. */
+lv_status lv_book_set_weights(lv_book_t b, const double* weights);
+
+/* offsets [n_surfaces + 1]: surface s's risk occupies [offsets[s], offsets[s+1]). */
+lv_status lv_book_risk_offsets(lv_book_t b, int64_t* offsets);
+
+/* Run the book and return the aggregated risk: host output
+ * [offsets[n_surfaces]] doubles (graph-captured like lv_book_run). */
+lv_status lv_book_run_risk(lv_book_t b, double S0, double r, uint64_t seed, double* out);
+
+/* Same without graph or host copy, to d_out (device, caller-owned),
+ * enqueued on the book's stream without synchronising. */
+lv_status lv_book_run_risk_device(lv_book_t b, double S0, double r, uint64_t seed, double* d_out);
+
 /* Thread-local description of the last failure on this host thread. */
 const char* lv_last_error(void);
 

@@ -220,12 +220,17 @@ __global__ void __launch_bounds__(128, 5) book_kernel(const __grid_constant__ Bo
             for (int w = 0; w < W; ++w) t += s_red[3 * w + tid];
             atomicAdd(&sums[tid], t);
         }
+        // vega buckets: the option's own sums, or (aggregated risk) its surface's,
+        // scaled by the option's weight over its path count
+        const BookInst& inst = B.insts[it.inst];
+        double* vsum = B.risk ? B.risk + B.surfs[inst.surf].risk_off + 3 : sums + 3;
+        const double vscale = B.risk ? inst.scale : 1.0;
         const int nIJ = P.Je * P.I;
         for (int e = tid; e < nIJ; e += Bk) {
             const float v = l1[e];
             if (v != 0.0f) {
                 const int j = e / P.I, i = e - j * P.I;
-                if (j < P.J) atomicAdd(&sums[3 + i * P.J + j], (double)v);   // spot-major sums
+                if (j < P.J) atomicAdd(&vsum[i * P.J + j], (double)v * vscale);   // spot-major sums
                 l1[e] = 0.0f;
             }
         }
@@ -254,6 +259,41 @@ __global__ void book_finalize_kernel(const BookInst* __restrict__ insts, const B
             d[LV_OUT_DELTA_DEV] = s[2] / (P * exp2(run->log2_S0));
         } else if (e >= 3) {
             d[e] = s[e] / P;
+        }
+    }
+}
+
+// Aggregated risk per surface: the weighted option scalars (from each
+// option's sums) and the vega part already summed with weights w / n_paths.
+__global__ void book_risk_finalize_kernel(const BookInst* __restrict__ insts, const BookSurf* __restrict__ surfs,
+                                          int n_inst, const double* __restrict__ sums,
+                                          const double* __restrict__ risk, const BookRun* run,
+                                          double* __restrict__ out)
+{
+    const int sf = blockIdx.y;
+    const BookSurf& S = surfs[sf];
+    const int IJ = S.I * S.J;
+    double* d = out + S.risk_off;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < IJ + 3; e += gridDim.x * blockDim.x) {
+        if (e >= 3) {
+            d[e] = risk[S.risk_off + e];
+        } else if (e == 0) {
+            const double S0 = exp2(run->log2_S0);
+            double price = 0.0, delta = 0.0, var = 0.0;
+            for (int o = 0; o < n_inst; ++o) {
+                const BookInst& q = insts[o];
+                if (q.surf != sf) continue;
+                const double* s = sums + q.out_off;
+                const double P = (double)q.n_paths;
+                const double mean = s[0] / P;
+                const double v = q.n_paths > 1 ? (s[1] / P - mean * mean) * P / (P - 1.0) : 0.0;
+                price += q.w * mean;
+                delta += q.w * s[2] / (P * S0);
+                var += q.w * q.w * (v > 0.0 ? v / P : 0.0);
+            }
+            d[LV_OUT_PRICE_DEV] = price;
+            d[LV_OUT_DELTA_DEV] = delta;
+            d[LV_OUT_STDERR_DEV] = sqrt(var);
         }
     }
 }
@@ -298,6 +338,14 @@ cudaError_t launch_book(const BookParams& b, int grid, int block, int k, size_t 
     case 8: return book_launch_k<8>(b, grid, block, smem, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_book_risk_finalize(const BookParams& b, int n_surf, int n_inst, int max_IJ, double* out,
+                                      cudaStream_t s)
+{
+    dim3 grid((max_IJ + 3 + 255) / 256, n_surf);
+    book_risk_finalize_kernel<<<grid, 256, 0, s>>>(b.insts, b.surfs, n_inst, b.sums, b.risk, b.run, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_book_finalize(const BookParams& b, int n_inst, int max_IJ, double* out, cudaStream_t s)

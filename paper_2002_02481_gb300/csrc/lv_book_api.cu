@@ -33,6 +33,7 @@ struct lv_book_s {
     std::vector<lv::BookInst> insts;        // in the caller's order
     std::vector<lv::BookSurf> surfs;
     std::vector<int64_t> offsets;           // [n + 1]
+    std::vector<int64_t> risk_offsets;      // [n_surfaces + 1]
     int max_I = 0, max_J = 0, max_Je = 0, max_N = 0, max_IJe = 0, max_IJ = 0;
     int64_t total_paths = 0;
     // device tables and grids
@@ -49,6 +50,9 @@ struct lv_book_s {
     double* d_sums = nullptr;
     double* d_out = nullptr;
     double* h_out = nullptr;                // pinned
+    double* d_risk = nullptr;               // aggregated runs: per-surface sums
+    double* d_rout = nullptr;               // aggregated runs: per-surface outputs
+    double* h_rout = nullptr;               // pinned
     // scratch for the current launch shape
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -62,6 +66,7 @@ struct lv_book_s {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec_risk = nullptr;
 };
 
 namespace {
@@ -82,7 +87,9 @@ struct BookDevice {
 void drop_graph(lv_book_s* b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->exec_risk) cudaGraphExecDestroy(b->exec_risk);
     b->exec = nullptr;
+    b->exec_risk = nullptr;
 }
 
 void free_book(lv_book_s* b)
@@ -99,9 +106,12 @@ void free_book(lv_book_s* b)
     cudaFree(b->d_run);
     cudaFree(b->d_sums);
     cudaFree(b->d_out);
+    cudaFree(b->d_risk);
+    cudaFree(b->d_rout);
     cudaFree(b->d_scratch);
     cudaFreeHost(b->h_run);
     cudaFreeHost(b->h_out);
+    cudaFreeHost(b->h_rout);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;
 }
@@ -190,6 +200,7 @@ lv::BookParams params(const lv_book_s* b)
     P.run = b->d_run;
     P.item_counter = b->d_counter;
     P.sums = b->d_sums;
+    P.risk = nullptr;
     P.l1 = b->d_l1;
     P.ckpt = b->d_ckpt;
     P.max_I = b->max_I;
@@ -208,6 +219,22 @@ lv_status enqueue_run(lv_book_s* b, double* d_out)
     const lv::BookParams P = params(b);
     LV_BCUDA(lv::launch_book(P, b->grid, b->block, b->k, b->smem, b->stream));
     LV_BCUDA(lv::launch_book_finalize(P, (int)b->insts.size(), b->max_IJ, d_out, b->stream));
+    return LV_OK;
+}
+
+// Enqueue one aggregated-risk run: per-option scalar sums, per-surface vega sums.
+lv_status enqueue_risk(lv_book_s* b, double* d_out)
+{
+    const size_t n_out = (size_t)b->offsets.back();
+    const size_t n_risk = (size_t)b->risk_offsets.back();
+    LV_BCUDA(cudaMemsetAsync(b->d_sums, 0, sizeof(double) * n_out, b->stream));
+    LV_BCUDA(cudaMemsetAsync(b->d_risk, 0, sizeof(double) * n_risk, b->stream));
+    LV_BCUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream));
+    lv::BookParams P = params(b);
+    P.risk = b->d_risk;
+    LV_BCUDA(lv::launch_book(P, b->grid, b->block, b->k, b->smem, b->stream));
+    LV_BCUDA(lv::launch_book_risk_finalize(P, (int)b->surfs.size(), (int)b->insts.size(), b->max_IJ, d_out,
+                                           b->stream));
     return LV_OK;
 }
 
@@ -248,6 +275,52 @@ void write_tuned(const std::string& key, int block, int k, int item_tiles, doubl
 {
     const int v[3] = {block, k, item_tiles};
     lv::tune_cache_append(key, v, ms);
+}
+
+// One run through a CUDA graph captured on first use (per-option outputs, or
+// with `risk` the aggregated per-surface risk): parameter upload, zeroing,
+// the persistent kernel, the finalize and the copy back; then a host copy.
+lv_status run_captured(lv_book_s* b, double S0, double r, uint64_t seed, bool risk, double* out)
+{
+    if (!b || !out) return set_error(LV_EINVAL, "NULL argument");
+    lv_status st = check_run(S0, r);
+    if (st != LV_OK) return st;
+    BookDevice guard(b->device);
+    LV_BCUDA(cudaStreamSynchronize(b->stream));
+    set_run(b, S0, r, seed);
+    const size_t n_out = risk ? (size_t)b->risk_offsets.back() : (size_t)b->offsets.back();
+    cudaGraphExec_t& exec = risk ? b->exec_risk : b->exec;
+    double* d_res = risk ? b->d_rout : b->d_out;
+    double* h_res = risk ? b->h_rout : b->h_out;
+    if (!exec) {
+        LV_BCUDA(lv::book_prepare(b->k));
+        cudaGraph_t graph = nullptr;
+        LV_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        lv_status cst = LV_OK;
+        cudaError_t e = cudaMemcpyAsync(b->d_run, b->h_run, sizeof(lv::BookRun), cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) cst = set_error(LV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+        if (cst == LV_OK) cst = risk ? enqueue_risk(b, d_res) : enqueue_run(b, d_res);
+        if (cst == LV_OK) {
+            e = cudaMemcpyAsync(h_res, d_res, sizeof(double) * n_out, cudaMemcpyDeviceToHost, b->stream);
+            if (e != cudaSuccess) cst = set_error(LV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
+        }
+        const cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
+        if (cst != LV_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return cst;
+        }
+        if (ee != cudaSuccess) return set_error(LV_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ee));
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            exec = nullptr;
+            return set_error(LV_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+        }
+    }
+    LV_BCUDA(cudaGraphLaunch(exec, b->stream));
+    LV_BCUDA(cudaStreamSynchronize(b->stream));
+    std::memcpy(out, h_res, sizeof(double) * n_out);
+    return LV_OK;
 }
 
 }  // namespace
@@ -304,6 +377,7 @@ lv_status lv_book_create(const lv_surface_t* surfaces, int32_t n_surfaces, const
         bs.off_node = n_node;
         bs.off_ab = n_ab;
         bs.off_tau = n_tau;
+        bs.risk_off = s == 0 ? 0 : b->surfs.back().risk_off + 3 + (long long)b->surfs.back().I * b->surfs.back().J;
         n_sig += (long long)h->Je * (h->I - 1);
         n_node += h->I;
         n_ab += h->I;
@@ -327,6 +401,8 @@ lv_status lv_book_create(const lv_surface_t* surfaces, int32_t n_surfaces, const
         bi.T = q.T;
         bi.n_paths = q.n_paths;
         bi.out_off = b->offsets.back();
+        bi.w = 1.0;
+        bi.scale = 1.0 / (double)q.n_paths;
         b->insts.push_back(bi);
         const lv::BookSurf& s = b->surfs[q.surface];
         b->offsets.push_back(b->offsets.back() + 3 + (int64_t)s.I * s.J);
@@ -334,6 +410,9 @@ lv_status lv_book_create(const lv_surface_t* surfaces, int32_t n_surfaces, const
         b->total_paths += q.n_paths;
     }
     const size_t n_out = (size_t)b->offsets.back();
+    b->risk_offsets.assign(1, 0);
+    for (const lv::BookSurf& bs : b->surfs) b->risk_offsets.push_back(bs.risk_off + 3 + (int64_t)bs.I * bs.J);
+    const size_t n_risk = (size_t)b->risk_offsets.back();
     if (cudaMalloc(&b->d_surfs, sizeof(lv::BookSurf) * b->surfs.size()) != cudaSuccess ||
         cudaMalloc(&b->d_insts, sizeof(lv::BookInst) * b->insts.size()) != cudaSuccess ||
         cudaMalloc(&b->d_sig2, sizeof(float2) * n_sig) != cudaSuccess ||
@@ -343,8 +422,11 @@ lv_status lv_book_create(const lv_surface_t* surfaces, int32_t n_surfaces, const
         cudaMalloc(&b->d_run, sizeof(lv::BookRun)) != cudaSuccess ||
         cudaMalloc(&b->d_sums, sizeof(double) * n_out) != cudaSuccess ||
         cudaMalloc(&b->d_out, sizeof(double) * n_out) != cudaSuccess ||
+        cudaMalloc(&b->d_risk, sizeof(double) * n_risk) != cudaSuccess ||
+        cudaMalloc(&b->d_rout, sizeof(double) * n_risk) != cudaSuccess ||
         cudaMallocHost(&b->h_run, sizeof(lv::BookRun)) != cudaSuccess ||
-        cudaMallocHost(&b->h_out, sizeof(double) * n_out) != cudaSuccess) {
+        cudaMallocHost(&b->h_out, sizeof(double) * n_out) != cudaSuccess ||
+        cudaMallocHost(&b->h_rout, sizeof(double) * n_risk) != cudaSuccess) {
         cudaGetLastError();
         return bail(set_error(LV_ENOMEM, "book allocation failed"));
     }
@@ -423,41 +505,47 @@ lv_status lv_book_run_device(lv_book_t b, double S0, double r, uint64_t seed, do
 
 lv_status lv_book_run(lv_book_t b, double S0, double r, uint64_t seed, double* out)
 {
-    if (!b || !out) return set_error(LV_EINVAL, "NULL argument");
+    return run_captured(b, S0, r, seed, false, out);
+}
+
+lv_status lv_book_run_risk(lv_book_t b, double S0, double r, uint64_t seed, double* out)
+{
+    return run_captured(b, S0, r, seed, true, out);
+}
+
+lv_status lv_book_run_risk_device(lv_book_t b, double S0, double r, uint64_t seed, double* d_out)
+{
+    if (!b || !d_out) return set_error(LV_EINVAL, "NULL argument");
     lv_status st = check_run(S0, r);
     if (st != LV_OK) return st;
     BookDevice guard(b->device);
     LV_BCUDA(cudaStreamSynchronize(b->stream));
     set_run(b, S0, r, seed);
-    const size_t n_out = (size_t)b->offsets.back();
-    if (!b->exec) {
-        LV_BCUDA(lv::book_prepare(b->k));
-        cudaGraph_t graph = nullptr;
-        LV_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        lv_status cst = LV_OK;
-        cudaError_t e = cudaMemcpyAsync(b->d_run, b->h_run, sizeof(lv::BookRun), cudaMemcpyHostToDevice, b->stream);
-        if (e != cudaSuccess) cst = set_error(LV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-        if (cst == LV_OK) cst = enqueue_run(b, b->d_out);
-        if (cst == LV_OK) {
-            e = cudaMemcpyAsync(b->h_out, b->d_out, sizeof(double) * n_out, cudaMemcpyDeviceToHost, b->stream);
-            if (e != cudaSuccess) cst = set_error(LV_ECUDA, std::string("capture: ") + cudaGetErrorString(e));
-        }
-        const cudaError_t ee = cudaStreamEndCapture(b->stream, &graph);
-        if (cst != LV_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return cst;
-        }
-        if (ee != cudaSuccess) return set_error(LV_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ee));
-        const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ie != cudaSuccess) {
-            b->exec = nullptr;
-            return set_error(LV_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
-        }
-    }
-    LV_BCUDA(cudaGraphLaunch(b->exec, b->stream));
+    LV_BCUDA(cudaMemcpyAsync(b->d_run, b->h_run, sizeof(lv::BookRun), cudaMemcpyHostToDevice, b->stream));
+    return enqueue_risk(b, d_out);
+}
+
+lv_status lv_book_set_weights(lv_book_t b, const double* weights)
+{
+    if (!b || !weights) return set_error(LV_EINVAL, "NULL argument");
+    for (size_t o = 0; o < b->insts.size(); ++o)
+        if (!std::isfinite(weights[o])) return set_error(LV_EINVAL, "weights must be finite");
+    BookDevice guard(b->device);
+    // an enqueued run may still read the table
     LV_BCUDA(cudaStreamSynchronize(b->stream));
-    std::memcpy(out, b->h_out, sizeof(double) * n_out);
+    for (size_t o = 0; o < b->insts.size(); ++o) {
+        b->insts[o].w = weights[o];
+        b->insts[o].scale = weights[o] / (double)b->insts[o].n_paths;
+    }
+    LV_BCUDA(cudaMemcpy(b->d_insts, b->insts.data(), sizeof(lv::BookInst) * b->insts.size(),
+                        cudaMemcpyHostToDevice));
+    return LV_OK;
+}
+
+lv_status lv_book_risk_offsets(lv_book_t b, int64_t* offsets)
+{
+    if (!b || !offsets) return set_error(LV_EINVAL, "NULL argument");
+    std::memcpy(offsets, b->risk_offsets.data(), sizeof(int64_t) * b->risk_offsets.size());
     return LV_OK;
 }
 

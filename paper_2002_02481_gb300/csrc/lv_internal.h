@@ -134,6 +134,7 @@ struct BookSurf {
     int I, J, Je, log_uniform;
     float cell_scale, cell_shift, s_lo, s_hi;
     long long off_sig2, off_node, off_ab, off_tau;   // offsets into the book's grid arrays
+    long long risk_off;                              // first double of this surface's aggregated risk
 };
 
 struct BookInst {
@@ -141,6 +142,8 @@ struct BookInst {
     double K, T;
     long long n_paths;
     long long out_off;                               // first double of this option's sums / outputs
+    double w;                                        // position weight (aggregated risk)
+    double scale;                                    // w / n_paths
 };
 
 struct BookItem {
@@ -164,6 +167,8 @@ struct BookParams {
     const BookRun* run;
     unsigned int* item_counter;
     double* sums;          // per option [3 + I J] binary64 sums (zeroed before a run)
+    double* risk;          // aggregated runs: per surface [3 + I J], the vega part summed with
+                           // weights w / n_paths (zeroed before a run); null: per-option vegas
     float* l1;             // [gridDim.x][max_IJe] binary32 buckets per block
     float* ckpt;           // [ceil(max_N / k)][gridDim.x * warps * ring slots]
     int max_I, max_Je, max_N, max_IJe;
@@ -175,6 +180,8 @@ cudaError_t book_prepare(int k);
 cudaError_t book_occupancy(int block, int k, size_t smem, int* blocks_per_sm);
 cudaError_t launch_book(const BookParams& b, int grid, int block, int k, size_t smem, cudaStream_t s);
 cudaError_t launch_book_finalize(const BookParams& b, int n_inst, int max_IJ, double* out, cudaStream_t s);
+cudaError_t launch_book_risk_finalize(const BookParams& b, int n_surf, int n_inst, int max_IJ, double* out,
+                                      cudaStream_t s);
 
 }  // namespace lv
 

@@ -264,6 +264,10 @@ def _declare_book(lib):
         "lv_book_run": [vp, d, d, u64, c.POINTER(d)],
         "lv_book_run_device": [vp, d, d, u64, vp],
         "lv_book_tune": [vp, d, d, u64, c.POINTER(i32), c.POINTER(i32), c.POINTER(i32), c.POINTER(d)],
+        "lv_book_set_weights": [vp, c.POINTER(d)],
+        "lv_book_risk_offsets": [vp, c.POINTER(i64)],
+        "lv_book_run_risk": [vp, d, d, u64, c.POINTER(d)],
+        "lv_book_run_risk_device": [vp, d, d, u64, vp],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -287,6 +291,10 @@ class Book:
         off = (ctypes.c_int64 * (self.n + 1))()
         _check(self.lib, self.lib.lv_book_output_offsets(self.h, off), "lv_book_output_offsets")
         self.offsets = list(off)
+        self.n_surfaces = len(surfaces)
+        roff = (ctypes.c_int64 * (self.n_surfaces + 1))()
+        _check(self.lib, self.lib.lv_book_risk_offsets(self.h, roff), "lv_book_risk_offsets")
+        self.risk_offsets = list(roff)
 
     def close(self) -> None:
         if self.h:
@@ -317,6 +325,28 @@ class Book:
         _check(self.lib, self.lib.lv_book_tune(self.h, S0, r, int(seed), ctypes.byref(b), ctypes.byref(k),
                                                ctypes.byref(p), ctypes.byref(ms)), "lv_book_tune")
         return b.value, k.value, p.value, ms.value
+
+    def set_weights(self, weights) -> None:
+        """Position weight per option for the aggregated risk."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        if w.shape != (self.n,):
+            raise ValueError(f"need {self.n} weights")
+        _check(self.lib, self.lib.lv_book_set_weights(self.h, _dp(w)), "lv_book_set_weights")
+
+    def run_risk(self, S0, r, seed) -> np.ndarray:
+        """Aggregated risk per surface: [sum w price, sum w delta, stderr, sum w vega...] blocks."""
+        out = np.zeros(self.risk_offsets[-1], dtype=np.float64)
+        _check(self.lib, self.lib.lv_book_run_risk(self.h, S0, r, int(seed), _dp(out)), "lv_book_run_risk")
+        return out
+
+    def run_risk_device(self, S0, r, seed, d_out_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_book_run_risk_device(self.h, S0, r, int(seed), ctypes.c_void_p(d_out_ptr)),
+               "lv_book_run_risk_device")
+
+    def risk(self, out: np.ndarray, s: int):
+        """(price, delta, stderr, vega flat) of surface s from a risk run's output."""
+        r = out[self.risk_offsets[s]:self.risk_offsets[s + 1]]
+        return r[0], r[1], r[2], r[3:]
 
     def result(self, out: np.ndarray, o: int):
         """(price, delta, stderr, vega flat) of option o from a run's output."""

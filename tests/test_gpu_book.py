@@ -107,3 +107,69 @@ def test_book_options_against_oracle(lib):
         vm = np.max(np.abs(ref["vega"]))
         assert np.max(np.abs(v - ref["vega"].reshape(-1))) <= 1e-4 * max(vm, 1e-12), o
     book.close()
+
+
+def test_aggregated_risk_is_the_weighted_sum_of_the_options(lib):
+    """Per surface: the weighted sums of the options' prices, deltas and vega
+    buckets (and the independent-stream standard error), accumulated inside
+    the persistent kernel; graph replay and the device entry point agree."""
+    import torch
+    surfs, items = _book_inputs()
+    handles = [lv.Surface.from_workload(s, lib) for s in surfs]
+    book = lv.Book(handles, items, lib)
+    S0, r, seed = 100.0, 0.02, 9
+    per_option = book.run(S0, r, seed)
+    for weights in (np.ones(len(items)), np.random.Generator(np.random.PCG64(3)).normal(size=len(items))):
+        book.set_weights(weights)
+        risk = book.run_risk(S0, r, seed)
+        for s in range(len(surfs)):
+            mine = [o for o, it in enumerate(items) if it.surface == s]
+            p = sum(weights[o] * book.result(per_option, o)[0] for o in mine)
+            d = sum(weights[o] * book.result(per_option, o)[1] for o in mine)
+            e = np.sqrt(sum((weights[o] * book.result(per_option, o)[2]) ** 2 for o in mine))
+            v = sum(weights[o] * book.result(per_option, o)[3] for o in mine) if mine else 0.0
+            rp, rd, re, rv = book.risk(risk, s)
+            scale = max(sum(abs(weights[o] * book.result(per_option, o)[0]) for o in mine), 1e-12)
+            assert abs(rp - p) <= 1e-12 * scale, (s, rp, p)
+            dscale = max(sum(abs(weights[o] * book.result(per_option, o)[1]) for o in mine), 1e-12)
+            assert abs(rd - d) <= 1e-9 * dscale, (s, rd, d)
+            assert abs(re - e) <= 1e-9 * max(e, 1e-12), (s, re, e)
+            vscale = max(sum(np.max(np.abs(weights[o] * book.result(per_option, o)[3])) for o in mine), 1e-12)
+            assert np.max(np.abs(rv - v)) <= 1e-5 * vscale, s
+        dev = torch.zeros(book.risk_offsets[-1], dtype=torch.float64, device="cuda")
+        book.run_risk_device(S0, r, seed, dev.data_ptr())
+        torch.cuda.synchronize()
+        dd = dev.cpu().numpy()
+        for s in range(len(surfs)):
+            a, b = book.risk(dd, s), book.risk(risk, s)
+            assert abs(a[0] - b[0]) <= 1e-12 * max(abs(b[0]), 1e-12)
+            assert np.max(np.abs(a[3] - b[3])) <= 1e-5 * max(np.max(np.abs(b[3])), 1e-12)
+    with pytest.raises(lv.LVError):
+        book.set_weights(np.full(len(items), np.nan))
+    book.close()
+
+
+def test_aggregated_risk_against_the_oracle(lib):
+    """One surface's aggregated vega buckets against the weighted sum of the
+    FP64 oracle's per-option buckets."""
+    surfs, items = _book_inputs()
+    handles = [lv.Surface.from_workload(s, lib) for s in surfs]
+    book = lv.Book(handles, items, lib)
+    S0, r, seed = 100.0, 0.02, 9
+    weights = np.linspace(-1.0, 2.0, len(items))
+    book.set_weights(weights)
+    risk = book.run_risk(S0, r, seed)
+    s = items[4].surface
+    ref_p, ref_v = 0.0, 0.0
+    for o, it in enumerate(items):
+        if it.surface != s:
+            continue
+        opt = W.Option(S0=S0, r=r, K=it.K, T=it.T, n_steps=it.n_steps, n_paths=it.n_paths, seed=seed,
+                       phi=it.phi, stream_id=it.stream_id)
+        ref = oracle.price_greeks(surfs[s], opt)
+        ref_p = ref_p + weights[o] * ref["price"]
+        ref_v = ref_v + weights[o] * ref["vega"].reshape(-1)
+    p, _, _, v = book.risk(risk, s)
+    assert abs(p - ref_p) <= 1e-5 * max(abs(ref_p), 1e-12)
+    assert np.max(np.abs(v - ref_v)) <= 1e-4 * max(np.max(np.abs(ref_v)), 1e-12)
+    book.close()
