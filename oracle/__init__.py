@@ -31,17 +31,22 @@ _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
 
 
+INTERP_S, INTERP_LOGS = 0, 1      # spot weight linear in S / in ln S
+SCHEME_LOG, SCHEME_X = 0, 1       # Euler on ln X / on X
+
+
 class _Surface(ctypes.Structure):
     _fields_ = [("n_spot", ctypes.c_int32), ("n_time", ctypes.c_int32),
                 ("spot", ctypes.POINTER(ctypes.c_double)),
                 ("time", ctypes.POINTER(ctypes.c_double)),
-                ("sigma", ctypes.POINTER(ctypes.c_double))]
+                ("sigma", ctypes.POINTER(ctypes.c_double)),
+                ("interp", ctypes.c_int32)]
 
 
 class _Option(ctypes.Structure):
     _fields_ = [("S0", ctypes.c_double), ("r", ctypes.c_double), ("K", ctypes.c_double),
                 ("T", ctypes.c_double), ("n_steps", ctypes.c_int32), ("phi", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint64), ("stream_id", ctypes.c_uint32), ("scheme", ctypes.c_int32)]
 
 
 class _Decisions(ctypes.Structure):
@@ -155,16 +160,23 @@ def _ptr(a: np.ndarray):
 class _Args:
     """Keeps the numpy buffers alive while C sees their pointers."""
 
-    def __init__(self, spot, time, sigma, S0, r, K, T, n_steps, seed, phi=1, stream_id=0):
+    def __init__(self, spot, time, sigma, S0, r, K, T, n_steps, seed, phi=1, stream_id=0, interp=0, scheme=0):
         self.spot, self.time = _f64(spot), _f64(time)
         self.sigma = _f64(sigma).reshape(-1)
         I, J = self.spot.shape[0], self.time.shape[0]
         if self.sigma.shape[0] != I * J:
             raise ValueError("sigma must hold n_spot * n_time values")
         self.IJ = I * J
-        self.surf = _Surface(I, J, _ptr(self.spot), _ptr(self.time), _ptr(self.sigma))
+        self.surf = _Surface(I, J, _ptr(self.spot), _ptr(self.time), _ptr(self.sigma), int(interp))
         self.opt = _Option(float(S0), float(r), float(K), float(T), int(n_steps), int(phi),
-                           int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id))
+                           int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id), int(scheme))
+
+
+def _args(surface, opt) -> _Args:
+    """C views of a workloads.Surface and workloads.Option (their interp and
+    scheme fields select the reading; both default to the main one)."""
+    return _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T, opt.n_steps,
+                 opt.seed, opt.phi, opt.stream_id, getattr(surface, "interp", 0), getattr(opt, "scheme", 0))
 
 
 def _check(st: int, what: str) -> None:
@@ -200,7 +212,8 @@ def normals(seed: int, path: int, n_steps: int, stream_id: int = 0, lib=None) ->
 def sigma_eval(surface, S: float, t: float, lib=None) -> dict:
     """Bilinear sigma, d sigma / d S, cell and node weights at (S, t)."""
     lib = lib or load_library()
-    a = _Args(surface.spot, surface.time, surface.sigma, 1.0, 0.0, 1.0, 1.0, 1, 0)
+    a = _Args(surface.spot, surface.time, surface.sigma, 1.0, 0.0, 1.0, 1.0, 1, 0,
+              interp=getattr(surface, "interp", 0))
     p = _Point()
     lib.orc_sigma_eval(ctypes.byref(a.surf), float(S), float(t), ctypes.byref(p))
     return dict(i=p.i, j=p.j, u=p.u, v=p.v, w=list(p.w), sigma=p.sigma, dsigma_dS=p.dsigma_dS)
@@ -213,8 +226,7 @@ def run_sums(surface, opt, path_begin: int = 0, path_end: Optional[int] = None,
     kink_vega[IJ] (see lv_oracle.h for the layout). ``decisions`` imposes
     payoff-indicator and spot-cell decisions on listed paths / steps."""
     lib = lib or load_library()
-    a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
-              opt.n_steps, opt.seed, opt.phi, opt.stream_id)
+    a = _args(surface, opt)
     if path_end is None:
         path_end = opt.n_paths
     out = np.zeros(NSCAL + 2 * a.IJ, dtype=np.float64)
@@ -248,8 +260,7 @@ def paths(surface, opt, path_begin: int, m: int, n_threads: Optional[int] = None
           decisions: Optional[Decisions] = None):
     """Per-path x_N, discounted payoff and d V / d x_0 for m paths."""
     lib = lib or load_library()
-    a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
-              opt.n_steps, opt.seed, opt.phi, opt.stream_id)
+    a = _args(surface, opt)
     xN, V, xb = (np.zeros(m) for _ in range(3))
     _check(lib.orc_paths_ex(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(m),
                             ctypes.byref(decisions.c) if decisions is not None else None,
@@ -262,8 +273,7 @@ def bump(surface, opt, eps_sigma: float, eps_S0: float, n_paths: Optional[int] =
     """Central bump-and-reprice with common random numbers (Sec. III):
     (vega grid [I, J], delta)."""
     lib = lib or load_library()
-    a = _Args(surface.spot, surface.time, surface.sigma, opt.S0, opt.r, opt.K, opt.T,
-              opt.n_steps, opt.seed, opt.phi, opt.stream_id)
+    a = _args(surface, opt)
     vega = np.zeros(a.IJ)
     delta = ctypes.c_double(0.0)
     _check(lib.orc_bump(ctypes.byref(a.surf), ctypes.byref(a.opt), int(n_paths or opt.n_paths),

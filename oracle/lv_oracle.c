@@ -35,6 +35,13 @@
  *     s_i <= S (0 below the grid), u = (S - s_i)/(s_{i+1} - s_i) clamped to
  *     [0, 1]; the same in time. Outside the grid sigma is flat and
  *     d sigma/d S = 0. With one time node sigma does not depend on t.
+ *   - Two further readings, selected by flags: the spot weight linear in
+ *     ln S, u = (ln S - ln s_i)/(ln s_{i+1} - ln s_i) (surface flag
+ *     ORC_INTERP_LOGS; Sec. IV-A's grid is uniform in price, the workloads'
+ *     nodes are log-spaced), and the Euler scheme on X itself,
+ *     X_{n+1} = X_n + r X_n dt + sigma_n X_n sqrt(dt) Z_n (option flag
+ *     ORC_SCHEME_X; Sec. IV-A states "tomorrow's price" as today's plus its
+ *     increment). Under ORC_SCHEME_X a spot at or below 0 is below the grid.
  *   - Payoff kink: the indicator 1{phi (S_N - K) > 0}, so a tie gives 0.
  *   - Vega is d price / d sigma_ij per unit of sigma.
  *
@@ -150,8 +157,16 @@ static void orc_sigma_in_cell(const orc_surface* sf, double S, double t, int32_t
                               orc_point* p)
 {
     const int32_t J = sf->n_time;
-    double width = sf->spot[i + 1] - sf->spot[i];
-    double u = orc_clamp01((S - sf->spot[i]) / width);
+    const double lo_s = sf->spot[i], hi_s = sf->spot[i + 1];
+    const int logs = sf->interp == ORC_INTERP_LOGS;
+    /* spot weight, clamped to [0, 1] (decided by comparison first, so that a
+     * spot at or below 0 never reaches the logarithm) */
+    double u;
+    if (S <= lo_s) u = 0.0;
+    else if (S >= hi_s) u = 1.0;
+    else u = logs ? (log(S) - log(lo_s)) / (log(hi_s) - log(lo_s)) : (S - lo_s) / (hi_s - lo_s);
+    /* d u / d S inside the cell */
+    double du_dS = logs ? 1.0 / (S * (log(hi_s) - log(lo_s))) : 1.0 / (hi_s - lo_s);
 
     int32_t j = 0;
     double v = 0.0;
@@ -175,7 +190,7 @@ static void orc_sigma_in_cell(const orc_surface* sf, double S, double t, int32_t
     p->w[3] = u * v;                   /* node (i+1, j+1) */
     p->sigma = p->w[0] * s00 + p->w[1] * s10 + p->w[2] * s01 + p->w[3] * s11;
     if (inside)
-        p->dsigma_dS = ((1.0 - v) * (s10 - s00) + v * (s11 - s01)) / width;
+        p->dsigma_dS = ((1.0 - v) * (s10 - s00) + v * (s11 - s01)) * du_dS;
     else
         p->dsigma_dS = 0.0;
 }
@@ -273,17 +288,23 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     int64_t c_first, c_last;
     orc_cell_range(dec, path, &c_first, &c_last);
 
-    /* forward: Euler on the log-spot (Sec. IV-A) */
-    x[0] = log(op->S0);
+    /* forward: Euler on the log-spot, or on the spot itself (Sec. IV-A);
+     * x holds ln S, or S under ORC_SCHEME_X */
+    const int on_x = op->scheme == ORC_SCHEME_X;
+    x[0] = on_x ? op->S0 : log(op->S0);
     for (int32_t n = 0; n < N; ++n) {
         double t = (double)n * dt;
-        orc_sigma_decided(sf, exp(x[n]), t, orc_forced_cell(dec, c_first, c_last, n), &pt);
-        x[n + 1] = x[n] + (op->r - 0.5 * pt.sigma * pt.sigma) * dt + pt.sigma * sqdt * z[n];
+        double S = on_x ? x[n] : exp(x[n]);
+        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);
+        if (on_x)
+            x[n + 1] = x[n] + op->r * x[n] * dt + pt.sigma * x[n] * sqdt * z[n];
+        else
+            x[n + 1] = x[n] + (op->r - 0.5 * pt.sigma * pt.sigma) * dt + pt.sigma * sqdt * z[n];
     }
 
     /* payoff (Sec. IV-B) */
     const double disc = exp(-op->r * op->T);
-    const double SN = exp(x[N]);
+    const double SN = on_x ? x[N] : exp(x[N]);
     const double itm = (double)op->phi * (SN - op->K);
     res->V = disc * (itm > 0.0 ? itm : 0.0);
     res->SN = SN;
@@ -295,13 +316,15 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     /* reverse sweep over the stored trajectory (back-propagation, Sec. IV-C) */
     const int forced = orc_forced_itm(dec, path);
     const int in_money = forced >= 0 ? forced : (itm > 0.0);
-    double xbar = in_money ? disc * (double)op->phi * SN : 0.0;
+    /* xbar = d V / d x_n: x = ln S, or S under ORC_SCHEME_X */
+    double xbar = in_money ? disc * (double)op->phi * (on_x ? 1.0 : SN) : 0.0;
     double vtot = 0.0;
     for (int32_t n = N - 1; n >= 0; --n) {
         double t = (double)n * dt;
-        double S = exp(x[n]);
+        double S = on_x ? x[n] : exp(x[n]);
         orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);
-        double h = sqdt * z[n] - pt.sigma * dt;     /* d x_{n+1} / d sigma_n */
+        /* d x_{n+1} / d sigma_n */
+        double h = on_x ? x[n] * sqdt * z[n] : sqdt * z[n] - pt.sigma * dt;
         double sbar = xbar * h;                     /* adjoint of sigma_n */
         int32_t nodes[4] = { pt.i * J + pt.j, (pt.i + 1) * J + pt.j,
                              pt.i * J + pt.j + 1, (pt.i + 1) * J + pt.j + 1 };
@@ -312,10 +335,15 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
             if (res->kink) kink_vega[nodes[c]] += fabs(contrib);
             vtot += contrib;
         }
-        /* d x_{n+1} / d x_n = 1 + h * d sigma / d x, and d sigma/d x = S d sigma/d S */
-        xbar = xbar * (1.0 + h * S * pt.dsigma_dS);
+        /* d x_{n+1} / d x_n: 1 + h S d sigma/d S on ln S (d sigma/d x = S d sigma/d S);
+         * 1 + r dt + sigma sqrt(dt) Z + h d sigma/d S on S */
+        if (on_x)
+            xbar = xbar * (1.0 + op->r * dt + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS);
+        else
+            xbar = xbar * (1.0 + h * S * pt.dsigma_dS);
     }
-    res->xbar0 = xbar;
+    /* d V / d ln S0 in both cases (= S0 d V / d S0) */
+    res->xbar0 = on_x ? xbar * op->S0 : xbar;
     res->vtot = vtot;
 }
 
@@ -375,6 +403,9 @@ static int orc_check(const orc_surface* sf, const orc_option* op)
     if (sf->n_spot < 2 || sf->n_time < 1 || op->n_steps < 1 || !(op->T > 0.0) || !(op->S0 > 0.0))
         return ORC_EINVAL;
     if (op->phi != 1 && op->phi != -1) return ORC_EINVAL;
+    if (sf->interp != ORC_INTERP_S && sf->interp != ORC_INTERP_LOGS) return ORC_EINVAL;
+    if (op->scheme != ORC_SCHEME_LOG && op->scheme != ORC_SCHEME_X) return ORC_EINVAL;
+    if (sf->interp == ORC_INTERP_LOGS && !(sf->spot[0] > 0.0)) return ORC_EINVAL;
     return ORC_OK;
 }
 
@@ -488,7 +519,9 @@ static void* orc_path_job_run(void* arg)
         orc_path_result res;
         orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, 1, 0.0, jb->dec, vega, vega + IJ, &res);
         const int64_t q = p - jb->first;
-        if (jb->xN) jb->xN[q] = ws.x[jb->op->n_steps];
+        /* ln S_N under either scheme */
+        if (jb->xN)
+            jb->xN[q] = jb->op->scheme == ORC_SCHEME_X ? log(ws.x[jb->op->n_steps]) : ws.x[jb->op->n_steps];
         if (jb->V) jb->V[q] = res.V;
         if (jb->xbar0) jb->xbar0[q] = res.xbar0;
     }

@@ -19,7 +19,7 @@ enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EINTERNAL = 4 };
 enum {
     ORC_SUM_V = 0,        /* sum of discounted payoffs */
     ORC_SUM_V2 = 1,       /* sum of squared payoffs */
-    ORC_SUM_XBAR0 = 2,    /* sum of d V / d x_0 */
+    ORC_SUM_XBAR0 = 2,    /* sum of d V / d x_0, x_0 = ln S0 (= S0 d V / d S0 under either scheme) */
     ORC_SUM_XBAR0_2 = 3,  /* sum of squares of the above */
     ORC_SUM_VTOT = 4,     /* sum over paths of (sum over nodes of the path's vega) */
     ORC_SUM_VTOT_2 = 5,   /* sum of squares of the above */
@@ -29,12 +29,20 @@ enum {
     ORC_NSCAL = 9
 };
 
+/* Interpolation in spot between the nodes of a cell (Sec. IV-D reads as
+ * bilinear; the coordinate is open): linear in S or linear in ln S. */
+enum { ORC_INTERP_S = 0, ORC_INTERP_LOGS = 1 };
+/* Euler scheme (Sec. IV-A): on x = ln X (drift r - sigma^2/2) or on X
+ * itself (X_{n+1} = X_n + r X_n dt + sigma_n X_n sqrt(dt) Z_n). */
+enum { ORC_SCHEME_LOG = 0, ORC_SCHEME_X = 1 };
+
 typedef struct {
     int32_t n_spot;       /* I >= 2 */
     int32_t n_time;       /* J >= 1 */
-    const double* spot;   /* [I], strictly increasing */
+    const double* spot;   /* [I], strictly increasing, > 0 */
     const double* time;   /* [J], strictly increasing */
     const double* sigma;  /* [I*J], sigma_ij at i*J + j */
+    int32_t interp;       /* ORC_INTERP_* */
 } orc_surface;
 
 typedef struct {
@@ -43,6 +51,7 @@ typedef struct {
     int32_t phi;          /* +1 call, -1 put */
     uint64_t seed;
     uint32_t stream_id;
+    int32_t scheme;       /* ORC_SCHEME_* */
 } orc_option;
 
 typedef struct {

@@ -299,6 +299,125 @@ def pin_bilinear(lib):
         assert abs(ref - e["sigma"]) < 1e-13
 
 
+# ------------------------------------------- the other readings of Sec. IV
+
+def pin_flat_closed_form_paths_euler_x(lib):
+    """Euler on X, flat sigma, per path: X_N = S0 prod_n (1 + r dt + sigma
+    sqrt(dt) Z_n); d V / d ln S0 = e^{-rT} phi X_N on in-the-money paths
+    (X_N is linear in S0); the bucket total is d V / d sigma =
+    e^{-rT} phi X_N sum_n sqrt(dt) Z_n / (1 + r dt + sigma sqrt(dt) Z_n)."""
+    sig, r, T, N, K = 0.3, 0.03, 1.5, 18, 100.0
+    surf = W.flat_surface(sig, n_spot=4, n_time=3, s_lo=40.0, s_hi=250.0, t_hi=1.5)
+    dt = T / N
+    for phi in (1, -1):
+        opt = W.Option(S0=100.0, r=r, K=K, T=T, n_steps=N, n_paths=48, seed=13, phi=phi, scheme=oracle.SCHEME_X)
+        xN, V, xb = oracle.paths(surf, opt, 0, 48, lib=lib)
+        for p in range(48):
+            z = oracle.normals(13, p, N, lib=lib)
+            f = 1.0 + r * dt + sig * math.sqrt(dt) * z
+            XN = 100.0 * np.prod(f)
+            assert abs(math.exp(xN[p]) - XN) < 1e-12 * XN
+            itm = phi * (XN - K) > 0
+            disc = math.exp(-r * T)
+            assert abs(V[p] - (disc * phi * (XN - K) if itm else 0.0)) < 1e-11 * XN
+            assert abs(xb[p] - (disc * phi * XN if itm else 0.0)) < 1e-11 * XN
+            s = oracle.run_sums(surf, opt, p, p + 1, lib=lib, n_threads=1)
+            vpath = disc * phi * XN * np.sum(math.sqrt(dt) * z / f) if itm else 0.0
+            assert abs(s[oracle.SUM_VTOT] - vpath) <= 1e-11 * max(1.0, abs(vpath)), (p, s[oracle.SUM_VTOT], vpath)
+
+
+def pin_martingale_euler_x(lib):
+    """Euler on X on any grid: E[X_N] = S0 (1 + r dt)^N, so a call struck at
+    0 prices e^{-rT} S0 (1 + r dt)^N with delta e^{-rT} (1 + r dt)^N, within
+    3.5 standard errors."""
+    surf, _ = W.config_small()
+    for r in (0.0, 0.05):
+        opt = W.Option(S0=100.0, r=r, K=0.0, T=1.0, n_steps=26, n_paths=1 << 15, seed=6, scheme=oracle.SCHEME_X)
+        s = oracle.run_sums(surf, opt, lib=lib)
+        P, dt = opt.n_paths, opt.T / opt.n_steps
+        grow = math.exp(-r * opt.T) * (1.0 + r * dt) ** opt.n_steps
+        assert abs(s[oracle.SUM_V] / P - 100.0 * grow) < 3.5 * se_of(s[oracle.SUM_V], s[oracle.SUM_V2], P)
+        se_d = se_of(s[oracle.SUM_XBAR0], s[oracle.SUM_XBAR0_2], P) / 100.0
+        assert abs(s[oracle.SUM_XBAR0] / (P * 100.0) - grow) < 3.5 * se_d
+
+
+def pin_log_interpolation(lib):
+    """Spot weight linear in ln S: a grid with sigma_ij = a_j + b_j ln s_i is
+    reproduced exactly inside the grid, (1-v)(a_j + b_j ln S) + v(a_{j+1} +
+    b_{j+1} ln S), with d sigma / d S = ((1-v) b_j + v b_{j+1}) / S; values
+    equal scipy's linear interpolator on (ln s, t); flat and slope 0 outside."""
+    from scipy.interpolate import RegularGridInterpolator
+    s = np.array([60.0, 75.0, 97.0, 120.0, 155.0])
+    t = np.array([0.0, 0.4, 1.1])
+    a, b = np.array([0.9, 1.1, 0.7]), np.array([-0.12, -0.16, -0.09])
+    g = a[None, :] + b[None, :] * np.log(s)[:, None]
+    surf = W.Surface(s, t, g, interp=oracle.INTERP_LOGS)
+    rng = np.random.Generator(np.random.PCG64(8))
+    ref = RegularGridInterpolator((np.log(s), t), g, method="linear")
+    for _ in range(60):
+        S = rng.uniform(s[0], s[-1])
+        tt = rng.uniform(0.0, t[-1])
+        e = oracle.sigma_eval(surf, S, tt, lib=lib)
+        j = min(int(np.searchsorted(t, tt, side="right")) - 1, 1)
+        v = (tt - t[j]) / (t[j + 1] - t[j])
+        exact = (1 - v) * (a[j] + b[j] * math.log(S)) + v * (a[j + 1] + b[j + 1] * math.log(S))
+        assert abs(e["sigma"] - exact) < 1e-13
+        assert abs(e["dsigma_dS"] - ((1 - v) * b[j] + v * b[j + 1]) / S) < 1e-13
+        assert abs(e["sigma"] - ref([[math.log(S), tt]])[0]) < 1e-13
+        assert abs(sum(e["w"]) - 1.0) < 1e-14
+    for S in (10.0, 1000.0):
+        e = oracle.sigma_eval(surf, S, 0.5, lib=lib)
+        edge = oracle.sigma_eval(surf, s[0] if S < s[0] else s[-1], 0.5, lib=lib)
+        assert e["dsigma_dS"] == 0.0 and abs(e["sigma"] - edge["sigma"]) < 1e-15
+
+
+def _model_cases():
+    out = []
+    for interp, scheme, tag in ((oracle.INTERP_LOGS, oracle.SCHEME_LOG, "ln-S weight"),
+                                (oracle.INTERP_S, oracle.SCHEME_X, "Euler on X"),
+                                (oracle.INTERP_LOGS, oracle.SCHEME_X, "both")):
+        for c in ADJOINT_CASES[:4]:
+            name, surf, opt = _case(c)
+            surf = W.Surface(surf.spot, surf.time, surf.sigma, interp=interp)
+            out.append((f"{tag}: {name}", surf, W.Option(**{**opt.__dict__, "scheme": scheme})))
+    return out
+
+
+def pin_adjoint_vs_autograd_readings(lib):
+    """The reverse sweep against torch.autograd of the independent
+    restatement, under the ln-S spot weight, the Euler scheme on X and both,
+    on the same tiny grids as pin_adjoint_vs_autograd."""
+    for name, surf, opt in _model_cases():
+        Z = np.stack([oracle.normals(opt.seed, p, opt.n_steps, lib=lib) for p in range(opt.n_paths)])
+        price, delta, vega, _ = torch_lv.autograd_greeks(
+            surf.spot, surf.time, surf.sigma, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.phi, Z,
+            interp=surf.interp, scheme=opt.scheme)
+        res = oracle.finalize(oracle.run_sums(surf, opt, lib=lib), opt.n_paths, opt.S0,
+                              surf.n_spot * surf.n_time, lib=lib)
+        scale = max(1e-3, np.max(np.abs(vega)))
+        assert abs(res[0] - price) <= 1e-11 * max(1.0, abs(price)), name
+        assert abs(res[1] - delta) <= 1e-11 * max(1.0, abs(delta)), (name, res[1], delta)
+        np.testing.assert_allclose(res[3:].reshape(vega.shape), vega, rtol=0, atol=1e-11 * scale, err_msg=name)
+
+
+def pin_adjoint_vs_bump_readings(lib):
+    """Central bump-and-reprice (Sec. III) against the adjoint under the
+    other readings, as in pin_adjoint_vs_bump."""
+    for interp, scheme in ((oracle.INTERP_LOGS, oracle.SCHEME_LOG), (oracle.INTERP_S, oracle.SCHEME_X)):
+        base = W.random_surface(8, 3, 2, s_lo=85, s_hi=118, t_hi=0.6)
+        surf = W.Surface(base.spot, base.time, base.sigma, interp=interp)
+        opt = W.Option(S0=100.0, r=0.01, K=101.0, T=0.6, n_steps=4, n_paths=64, seed=12, phi=1, scheme=scheme)
+        xN, _, _ = oracle.paths(surf, opt, 0, opt.n_paths, lib=lib)
+        assert np.min(np.abs(np.exp(xN) - opt.K)) > 1e-3
+        res = oracle.finalize(oracle.run_sums(surf, opt, lib=lib), opt.n_paths, opt.S0, 6, lib=lib)
+        vfd, dfd = oracle.bump(surf, opt, 1e-6, 1e-6 * opt.S0, lib=lib)
+        scale = np.max(np.abs(vfd))
+        np.testing.assert_allclose(res[3:].reshape(3, 2), vfd, rtol=0, atol=2e-6 * scale)
+        assert abs(res[1] - dfd) < 2e-6 * max(1.0, abs(dfd))
+
+
 ALL_PINS = [pin_philox_curand, pin_normals_from_curand_words, pin_uniform_exact, pin_normal_law,
             pin_black_scholes, pin_flat_closed_form_paths, pin_martingale, pin_put_call_parity,
-            pin_adjoint_vs_autograd, pin_adjoint_vs_bump, pin_bilinear]
+            pin_adjoint_vs_autograd, pin_adjoint_vs_bump, pin_bilinear,
+            pin_flat_closed_form_paths_euler_x, pin_martingale_euler_x, pin_log_interpolation,
+            pin_adjoint_vs_autograd_readings, pin_adjoint_vs_bump_readings]

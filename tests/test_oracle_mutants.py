@@ -18,8 +18,7 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "lv_oracle.c")
 MUTANTS = {
     "drift sign": ("(op->r - 0.5 * pt.sigma * pt.sigma) * dt",
                    "(op->r + 0.5 * pt.sigma * pt.sigma) * dt"),
-    "dx/dsigma sign": ("double h = sqdt * z[n] - pt.sigma * dt;",
-                       "double h = sqdt * z[n] + pt.sigma * dt;"),
+    "dx/dsigma sign": ("sqdt * z[n] - pt.sigma * dt;", "sqdt * z[n] + pt.sigma * dt;"),
     "dsigma/dx drops S": ("xbar * (1.0 + h * S * pt.dsigma_dS)",
                           "xbar * (1.0 + h * pt.dsigma_dS)"),
     "node weights transposed": ("p->w[1] = u * (1.0 - v);", "p->w[1] = (1.0 - u) * v;"),
@@ -28,17 +27,29 @@ MUTANTS = {
     "box-muller cos/sin swapped": ("z[2 * pair] = radius * cos(angle);",
                                    "z[2 * pair] = radius * sin(angle);"),
     "uniform offset dropped": ("((double)(w >> 9) + 0.5)", "((double)(w >> 9) + 0.0)"),
-    "discount missing in adjoint": ("disc * (double)op->phi * SN : 0.0", "(double)op->phi * SN : 0.0"),
+    "discount missing in adjoint": ("disc * (double)op->phi * (on_x ? 1.0 : SN) : 0.0",
+                                    "(double)op->phi * (on_x ? 1.0 : SN) : 0.0"),
     "time-neighbour index": ("double s01 = (J > 1) ? sf->sigma[i * J + j + 1] : 0.0;",
                              "double s01 = (J > 1) ? sf->sigma[i * J + j] : 0.0;"),
     "cell rule strict": ("if (nodes[mid] <= x) lo = mid;", "if (nodes[mid] < x) lo = mid;"),
     "slope kept outside grid": ("if (inside)\n", "if (1)\n"),
-    "sigma at right point": ("        double t = (double)n * dt;\n        orc_sigma_decided(sf, exp(x[n]),",
-                             "        double t = (double)(n + 1) * dt;\n        orc_sigma_decided(sf, exp(x[n]),"),
+    "sigma at right point": ("double t = (double)n * dt;\n        double S = on_x ? x[n] : exp(x[n]);\n"
+                             "        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);\n"
+                             "        if (on_x)",
+                             "double t = (double)(n + 1) * dt;\n        double S = on_x ? x[n] : exp(x[n]);\n"
+                             "        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);\n"
+                             "        if (on_x)"),
     "inside test drops the upper edge": ("int inside = (S >= sf->spot[0] && S <= sf->spot[I - 1]);",
                                          "int inside = (S >= sf->spot[0]);"),
     "payoff sign": ("const double itm = (double)op->phi * (SN - op->K);",
                     "const double itm = (SN - op->K);"),
+    "log-weight slope drops 1/S": ("double du_dS = logs ? 1.0 / (S * (log(hi_s) - log(lo_s)))",
+                                   "double du_dS = logs ? 1.0 / (log(hi_s) - log(lo_s))"),
+    "log weight taken in S": ("u = logs ? (log(S) - log(lo_s)) / (log(hi_s) - log(lo_s))",
+                              "u = logs ? (S - lo_s) / (log(hi_s) - log(lo_s))"),
+    "Euler on X: adjoint drops r dt": ("xbar * (1.0 + op->r * dt + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS)",
+                                       "xbar * (1.0 + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS)"),
+    "Euler on X: dx/dsigma drops the spot": ("double h = on_x ? x[n] * sqdt * z[n]", "double h = on_x ? sqdt * z[n]"),
 }
 
 

@@ -11,9 +11,11 @@ import math
 import torch
 
 
-def forward_price(spot, time, sigma, S0, r, K, T, n_steps, phi, Z):
-    """Mean discounted payoff of log-Euler paths driven by Z [P, N] under
-    the bilinear local-vol grid (spot [I], time [J], sigma [I, J]).
+def forward_price(spot, time, sigma, S0, r, K, T, n_steps, phi, Z, interp=0, scheme=0):
+    """Mean discounted payoff of Euler paths driven by Z [P, N] under the
+    bilinear local-vol grid (spot [I], time [J], sigma [I, J]): on ln S
+    (scheme 0) or on S (scheme 1), with the spot weight linear in S
+    (interp 0) or in ln S (interp 1).
 
     The cell convention is the largest node index at or below the point,
     clamped so that the cell has a right neighbour; weights are clamped to
@@ -21,12 +23,16 @@ def forward_price(spot, time, sigma, S0, r, K, T, n_steps, phi, Z):
     I, J = spot.shape[0], time.shape[0]
     P = Z.shape[0]
     dt = T / n_steps
-    x = torch.log(S0) * torch.ones(P, dtype=torch.float64)
+    state = (torch.log(S0) if scheme == 0 else S0) * torch.ones(P, dtype=torch.float64)
     for n in range(n_steps):
         t = n * dt
-        S = torch.exp(x)
+        S = torch.exp(state) if scheme == 0 else state
         i = torch.clamp(torch.searchsorted(spot, S.detach(), right=True) - 1, 0, I - 2)
-        u = torch.clamp((S - spot[i]) / (spot[i + 1] - spot[i]), 0.0, 1.0)
+        if interp == 0:
+            u = torch.clamp((S - spot[i]) / (spot[i + 1] - spot[i]), 0.0, 1.0)
+        else:
+            u = torch.clamp((torch.log(S) - torch.log(spot[i])) / (torch.log(spot[i + 1]) - torch.log(spot[i])),
+                            0.0, 1.0)
         if J > 1:
             tt = torch.tensor([t], dtype=torch.float64)
             j = int(torch.clamp(torch.searchsorted(time, tt, right=True) - 1, 0, J - 2).item())
@@ -36,19 +42,22 @@ def forward_price(spot, time, sigma, S0, r, K, T, n_steps, phi, Z):
             sig = lo * (1 - v) + hi * v
         else:
             sig = sigma[i, 0] * (1 - u) + sigma[i + 1, 0] * u
-        x = x + (r - 0.5 * sig * sig) * dt + sig * math.sqrt(dt) * Z[:, n]
-    SN = torch.exp(x)
+        if scheme == 0:
+            state = state + (r - 0.5 * sig * sig) * dt + sig * math.sqrt(dt) * Z[:, n]
+        else:
+            state = state + r * state * dt + sig * state * math.sqrt(dt) * Z[:, n]
+    SN = torch.exp(state) if scheme == 0 else state
     V = math.exp(-r * T) * torch.relu(phi * (SN - K))
     return V.mean(), SN
 
 
-def autograd_greeks(spot, time, sigma, S0, r, K, T, n_steps, phi, Z):
+def autograd_greeks(spot, time, sigma, S0, r, K, T, n_steps, phi, Z, interp=0, scheme=0):
     """(price, delta, vega [I, J], S_N [P]) by torch.autograd, all FP64."""
     sp = torch.tensor(spot, dtype=torch.float64)
     tm = torch.tensor(time, dtype=torch.float64)
     sg = torch.tensor(sigma, dtype=torch.float64, requires_grad=True)
     s0 = torch.tensor(float(S0), dtype=torch.float64, requires_grad=True)
     z = torch.tensor(Z, dtype=torch.float64)
-    price, SN = forward_price(sp, tm, sg, s0, r, K, T, n_steps, phi, z)
+    price, SN = forward_price(sp, tm, sg, s0, r, K, T, n_steps, phi, z, interp, scheme)
     d_s0, d_sig = torch.autograd.grad(price, [s0, sg])
     return float(price.detach()), float(d_s0), d_sig.numpy(), SN.detach().numpy()

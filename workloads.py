@@ -24,6 +24,7 @@ class Surface:
     spot: np.ndarray   # [I] strictly increasing, > 0
     time: np.ndarray   # [J] strictly increasing, >= 0
     sigma: np.ndarray  # [I, J] float64, spot-major
+    interp: int = 0    # spot weight linear in S (0) or in ln S (1)
 
     @property
     def n_spot(self) -> int:
@@ -45,6 +46,7 @@ class Option:
     seed: int = 1
     phi: int = 1          # +1 call, -1 put
     stream_id: int = 0
+    scheme: int = 0       # Euler on ln S (0) or on S (1)
 
 
 def log_spaced(lo: float, hi: float, n: int) -> np.ndarray:
