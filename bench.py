@@ -206,11 +206,13 @@ def other_workloads(lib, dev, ev0, ev1):
     res = {}
     stream = torch.cuda.current_stream(dev)
 
-    def single(name, surf, opt, launch=None, acc=0, method=lv.LV_ADJ_REVERSE):
+    def single(name, surf, opt, launch=None, acc=0, method=lv.LV_ADJ_REVERSE, interp=0, scheme=0):
         S = lv.Surface.from_workload(surf, lib)
         S.set_stream(stream.cuda_stream)
         S.set_accumulation(acc)
         S.set_adjoint_method(method)
+        S.set_interpolation(interp)
+        S.set_scheme(scheme)
         if launch:
             S.set_launch(*launch)
         S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
@@ -222,6 +224,12 @@ def other_workloads(lib, dev, ev0, ev1):
         S.close()
 
     single("small 20x10, 52 steps, 2^14 paths", *W.config_small())
+    # the other readings of the scheme, on the bench workload
+    for interp, scheme, tag in ((lv.LV_INTERP_LOGS, lv.LV_SCHEME_LOG, "spot weight linear in ln S"),
+                                (lv.LV_INTERP_S, lv.LV_SCHEME_S, "Euler on S"),
+                                (lv.LV_INTERP_LOGS, lv.LV_SCHEME_S, "Euler on S, weight in ln S")):
+        single(f"reading: {tag}, 30x60, 156 steps, 2^20 paths", *W.config_paper_shape(), interp=interp,
+               scheme=scheme)
     # the tangent-ratio form of the adjoint (two forward passes, no checkpoints)
     single("tangent-ratio adjoint, 30x60, 156 steps, 2^20 paths", *W.config_paper_shape(),
            method=lv.LV_ADJ_TANGENT)

@@ -83,6 +83,19 @@ enum { LV_ACC_FP64 = 0, LV_ACC_KAHAN = 1 };
  * g_n = h_n S_n d sigma / d S and h_n = sqrt(dt) Z_n - sigma_n dt. */
 enum { LV_ADJ_REVERSE = 0, LV_ADJ_TANGENT = 1 };
 
+/* The two readings of the scheme besides the main one (Sec. IV-A, IV-D):
+ *  - spot weight of the bilinear interpolation linear in S (LV_INTERP_S,
+ *    default) or in ln S (LV_INTERP_LOGS: u = (ln S - ln s_i) /
+ *    (ln s_{i+1} - ln s_i), clamped);
+ *  - Euler scheme on x = ln S (LV_SCHEME_LOG, default: drift r - sigma^2/2)
+ *    or on S itself (LV_SCHEME_S: S_{n+1} = S_n (1 + r dt + sigma_n sqrt(dt)
+ *    Z_n); a spot at or below 0 is below the grid).
+ * The delta is d price / d S0 and the vegas d price / d sigma_ij under every
+ * reading. The other readings run checkpoint intervals k = 4 and 8 (larger k
+ * are capped at 8); the book and the bump baseline run the main reading. */
+enum { LV_INTERP_S = 0, LV_INTERP_LOGS = 1 };
+enum { LV_SCHEME_LOG = 0, LV_SCHEME_S = 1 };
+
 /* Layout of the [3 + n_spot * n_time] result of lv_price_greeks_device. */
 enum { LV_OUT_PRICE = 0, LV_OUT_DELTA = 1, LV_OUT_STDERR = 2, LV_OUT_VEGA = 3 };
 
@@ -131,6 +144,12 @@ lv_status lv_set_accumulation(lv_surface_t h, int32_t mode);
 /* LV_ADJ_REVERSE (default) or LV_ADJ_TANGENT, for every greeks entry point
  * of the handle except lv_debug_paths (always the reverse sweep). */
 lv_status lv_set_adjoint_method(lv_surface_t h, int32_t method);
+
+/* LV_INTERP_S (default) or LV_INTERP_LOGS for later calls on the handle. */
+lv_status lv_surface_set_interpolation(lv_surface_t h, int32_t interp);
+
+/* LV_SCHEME_LOG (default) or LV_SCHEME_S for later calls on the handle. */
+lv_status lv_set_scheme(lv_surface_t h, int32_t scheme);
 
 /* Launch shape: threads per block (32..128, multiple of 32), checkpoint
  * interval k of the reverse sweep (4, 8, 16 or 32 steps) and resident

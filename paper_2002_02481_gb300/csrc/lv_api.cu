@@ -141,6 +141,7 @@ void free_surface(lv_surface_s* h)
     cudaFree(h->d_sig);
     cudaFree(h->d_node);
     cudaFree(h->d_ab);
+    cudaFree(h->d_abl);
     cudaFree(h->d_tau);
     cudaFree(h->d_scratch);
     cudaFree(h->d_res);
@@ -198,14 +199,16 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
         }
     }
     if (dbg) *k = 4;
+    const int model = (h->interp == LV_INTERP_LOGS ? 1 : 0) | (h->scheme == LV_SCHEME_S ? 2 : 0);
+    if (model != 0 && *k > lv::kModelMaxK) *k = lv::kModelMaxK;
     const bool gs = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, true) <= kGridSmemLimit;
     if (grid_smem) *grid_smem = gs;
     const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, gs);
     if (smem > 200 * 1024)
         return fail(LV_EINVAL, "time table does not fit in shared memory (" + std::to_string(smem) + " bytes)");
     int occ = 0;
-    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, gs, dbg ? 0 : h->adj_method, smem,
-                             &occ));
+    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, gs, dbg ? 0 : h->adj_method, model,
+                             smem, &occ));
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
     *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
     return LV_OK;
@@ -287,7 +290,8 @@ lv::McParams base_params(const lv_surface_s* h, const McCall& c)
     lv::McParams P{};
     P.sig2 = h->d_sig;
     P.node = h->d_node;
-    P.ab = h->d_ab;
+    P.ab = h->interp == LV_INTERP_LOGS ? h->d_abl : h->d_ab;
+    P.model = (h->interp == LV_INTERP_LOGS ? 1 : 0) | (h->scheme == LV_SCHEME_S ? 2 : 0);
     P.tau = h->d_tau;
     P.I = h->I;
     P.J = h->J;
@@ -299,8 +303,11 @@ lv::McParams base_params(const lv_surface_s* h, const McCall& c)
     P.s_hi = h->s_hi;
     const double dt = c.T / (double)c.n_steps;
     const double log2e = 1.4426950408889634;
-    P.x0 = (float)std::log2(c.S0);
-    P.rdt = (float)(log2e * c.r * dt);
+    const bool on_s = h->scheme == LV_SCHEME_S;
+    P.x0 = (float)(on_s ? c.S0 : std::log2(c.S0));
+    P.rdt = (float)(on_s ? c.r * dt : log2e * c.r * dt);
+    P.S0f = (float)c.S0;
+    P.inv_S0 = (float)(1.0 / c.S0);
     P.hdt = (float)(log2e * 0.5 * dt);
     P.sqdt2 = (float)(log2e * std::sqrt(dt));
     P.dt = (float)dt;
@@ -449,6 +456,7 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
     if (cudaMalloc(&h->d_sig, sizeof(float2) * nsig) != cudaSuccess ||
         cudaMalloc(&h->d_node, sizeof(float) * n_spot) != cudaSuccess ||
         cudaMalloc(&h->d_ab, sizeof(float2) * n_spot) != cudaSuccess ||
+        cudaMalloc(&h->d_abl, sizeof(float2) * n_spot) != cudaSuccess ||
         cudaMalloc(&h->d_tau, sizeof(double) * n_time) != cudaSuccess ||
         cudaMalloc(&h->d_res, sizeof(double) * nres) != cudaSuccess ||
         cudaMallocHost(&h->h_sig_stage, sizeof(float2) * nsig) != cudaSuccess ||
@@ -457,20 +465,24 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
         return bail(LV_ENOMEM, "device or pinned allocation failed");
     }
     std::vector<float> node(n_spot);
-    std::vector<float2> ab(n_spot);
+    std::vector<float2> ab(n_spot), abl(n_spot);
     for (int i = 0; i < n_spot; ++i) {
         node[i] = (float)spot_nodes[i];
         if (i + 1 < n_spot) {
             const double w = spot_nodes[i + 1] - spot_nodes[i];
             ab[i] = make_float2((float)(1.0 / w), (float)(-spot_nodes[i] / w));
+            // the ln-S weight from y = log2 S: u = (y - y_i) / (y_{i+1} - y_i)
+            const double y0 = std::log2(spot_nodes[i]), wl = std::log2(spot_nodes[i + 1]) - y0;
+            abl[i] = make_float2((float)(1.0 / wl), (float)(-y0 / wl));
         } else {
-            ab[i] = make_float2(0.0f, 0.0f);
+            ab[i] = abl[i] = make_float2(0.0f, 0.0f);
         }
     }
     pack_sigma(h, sigma, h->h_sig_stage);
     if (cudaMemcpy(h->d_sig, h->h_sig_stage, sizeof(float2) * nsig, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_node, node.data(), sizeof(float) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_ab, ab.data(), sizeof(float2) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_abl, abl.data(), sizeof(float2) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_tau, time_nodes, sizeof(double) * n_time, cudaMemcpyHostToDevice) != cudaSuccess) {
         e = cudaGetLastError();
         return bail(LV_ECUDA, std::string("upload of the grid failed: ") + cudaGetErrorString(e));
@@ -524,6 +536,24 @@ lv_status lv_set_accumulation(lv_surface_t h, int32_t mode)
     if (mode != LV_ACC_FP64 && mode != LV_ACC_KAHAN)
         return fail(LV_EINVAL, "mode must be LV_ACC_FP64 or LV_ACC_KAHAN");
     h->acc_mode = mode;
+    return LV_OK;
+}
+
+lv_status lv_surface_set_interpolation(lv_surface_t h, int32_t interp)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (interp != LV_INTERP_S && interp != LV_INTERP_LOGS)
+        return fail(LV_EINVAL, "interp must be LV_INTERP_S or LV_INTERP_LOGS");
+    h->interp = interp;
+    return LV_OK;
+}
+
+lv_status lv_set_scheme(lv_surface_t h, int32_t scheme)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (scheme != LV_SCHEME_LOG && scheme != LV_SCHEME_S)
+        return fail(LV_EINVAL, "scheme must be LV_SCHEME_LOG or LV_SCHEME_S");
+    h->scheme = scheme;
     return LV_OK;
 }
 
@@ -712,6 +742,8 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
     lv_status st = check_option(S0, r, K, T, n_steps);
     if (st != LV_OK) return st;
     if (!is_finite(eps) || !(eps > 0.0)) return fail(LV_EINVAL, "eps must be finite and > 0");
+    if (h->interp != LV_INTERP_S || h->scheme != LV_SCHEME_LOG)
+        return fail(LV_EINVAL, "the bump baseline runs the main reading (LV_INTERP_S, LV_SCHEME_LOG) only");
     if (n_paths < 1 || n_paths > LV_MAX_PATH_INDEX) return fail(LV_EINVAL, "n_paths out of range");
     DeviceGuard g(h->device);
     if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");

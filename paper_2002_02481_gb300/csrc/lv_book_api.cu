@@ -336,6 +336,8 @@ lv_status lv_book_create(const lv_surface_t* surfaces, int32_t n_surfaces, const
     int device = -1;
     for (int s = 0; s < n_surfaces; ++s) {
         if (!surfaces[s]) return set_error(LV_EINVAL, "NULL surface");
+        if (surfaces[s]->interp != LV_INTERP_S || surfaces[s]->scheme != LV_SCHEME_LOG)
+            return set_error(LV_EINVAL, "a book runs the main reading (LV_INTERP_S, LV_SCHEME_LOG) only");
         if (s == 0) device = surfaces[s]->device;
         else if (surfaces[s]->device != device) return set_error(LV_EINVAL, "surfaces on different devices");
     }

@@ -136,24 +136,43 @@ __device__ __forceinline__ int spot_cell(const McParams& P, const SmemGrid& g, f
     return lo;
 }
 
+// The model a kernel is instantiated for: bit 0 makes the spot weight
+// linear in ln S instead of S (the other reading of Sec. IV-D's bilinear
+// interpolation on a log-spaced grid); bit 1 runs the Euler scheme on S
+// itself instead of ln S (the other reading of Sec. IV-A). The path state x
+// is y = log2 S, or S under bit 1. Model 0 is the main reading.
+constexpr int kModelLogWeight = 1;
+constexpr int kModelEulerS = 2;
+constexpr float kLog2e = 1.4426950408889634f;
+
 struct StepEval {
-    float S;       // S_n = 2^{y_n}
+    float S;       // S_n
     float sigma;   // sigma(S_n, t_n)
     float u;       // clamped spot weight
     int i;         // spot cell
-    float slope;   // d sigma / d S (0 outside the grid)
+    float sslope;  // S d sigma / d S = d sigma / d ln S (0 outside the grid)
 };
 
-// Bilinear sigma at (S_n, t_n), Sec. IV-D; slope only when WANT_SLOPE.
-template <bool WANT_SLOPE>
-__device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid& g, float y,
+// Bilinear sigma at (S_n, t_n), Sec. IV-D, from the path state x; the
+// slope only when WANT_SLOPE. With the ln-S weight the cell coefficients ab
+// are (1 / (y_{i+1} - y_i), -y_i / (y_{i+1} - y_i)) in y = log2 s, so that
+// d u / d ln S = ab.x log2(e); otherwise they are in S.
+template <bool WANT_SLOPE, int MODEL = 0>
+__device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid& g, float x,
                                                const int4& tb)
 {
     StepEval e;
-    e.S = ex2_approx(y);
+    float y;
+    if (MODEL & kModelEulerS) {
+        e.S = x;
+        y = lg2_approx(fmaxf(x, 1e-30f));       // a spot at or below 0 is below the grid
+    } else {
+        e.S = ex2_approx(x);
+        y = x;
+    }
     e.i = spot_cell(P, g, y, e.S);
     const float2 ab = g.ab[e.i];
-    e.u = __saturatef(fmaf(e.S, ab.x, ab.y));
+    e.u = __saturatef(fmaf((MODEL & kModelLogWeight) ? y : e.S, ab.x, ab.y));
     const float2 lo = g.sig2[tb.x + e.i];      // time row j:     sigma_{i,j},   its spot step
     const float2 hi = g.sig2[tb.y + e.i];      // time row j + 1
     const float v = __int_as_float(tb.w);
@@ -162,9 +181,10 @@ __device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid
     e.sigma = fmaf(v, bot - top, top);
     if (WANT_SLOPE) {
         const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
-        e.slope = inside ? fmaf(v, hi.y - lo.y, lo.y) * ab.x : 0.0f;
+        const float d = fmaf(v, hi.y - lo.y, lo.y) * ab.x;     // d sigma / d (S or y)
+        e.sslope = inside ? ((MODEL & kModelLogWeight) ? d * kLog2e : e.S * d) : 0.0f;
     } else {
-        e.slope = 0.0f;
+        e.sslope = 0.0f;
     }
     return e;
 }
@@ -175,6 +195,60 @@ __device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid
 __device__ __forceinline__ float euler_step(const McParams& P, float y, float sigma, float z)
 {
     return y + fmaf(sigma, P.sqdt2 * z, fmaf(-P.hdt * sigma, sigma, P.rdt));
+}
+
+// One step of the model's scheme: the log-Euler step, or on S
+//   S_{n+1} = S_n (1 + r dt + sigma_n sqrt(dt) Z_n)   (rdt = r dt there).
+template <int MODEL>
+__device__ __forceinline__ float step_state(const McParams& P, float x, float sigma, float z)
+{
+    if (MODEL & kModelEulerS) return fmaf(x, fmaf(sigma, P.sqdt * z, P.rdt), x);
+    return euler_step(P, x, sigma, z);
+}
+
+// Adjoint factors of step n: h = d x_{n+1} / d sigma_n and g with
+// d x_{n+1} / d x_n = 1 + g. On ln S: h = sqrt(dt) Z - sigma dt,
+// g = h S d sigma / d S. On S the adjoint runs scaled by S0 (xbar_N =
+// e^{-rT} phi S0 on paths in the money, so that xbar_0 = d V / d ln S0 as on
+// ln S): h = S_n sqrt(dt) Z / S0, g = r dt + sqrt(dt) Z (sigma + S d sigma / d S).
+template <int MODEL>
+__device__ __forceinline__ void adjoint_factors(const McParams& P, const StepEval& e, float z, float& h, float& g)
+{
+    if (MODEL & kModelEulerS) {
+        const float w = P.sqdt * z;
+        h = e.S * P.inv_S0 * w;
+        g = fmaf(w, e.sigma + e.sslope, P.rdt);
+    } else {
+        h = fmaf(P.sqdt, z, -e.sigma * P.dt);
+        g = h * e.sslope;
+    }
+}
+
+// 1 + g_n for the tangent-ratio form (one rounding on ln S).
+template <int MODEL>
+__device__ __forceinline__ float tangent_factor(const McParams& P, const StepEval& e, float z, float h)
+{
+    if (MODEL & kModelEulerS) return fmaf(P.sqdt * z, e.sigma + e.sslope, 1.0f + P.rdt);
+    return fmaf(h, e.sslope, 1.0f);
+}
+
+// Discounted payoff V and terminal adjoint xbar_N from the final state
+// (Sec. IV-B): xbar_N = e^{-rT} 1{phi (S_N - K) > 0} phi S_N on ln S, with
+// S0 in place of S_N on S (the scaled adjoint of adjoint_factors).
+template <int MODEL>
+__device__ __forceinline__ void payoff(const McParams& P, float x, float& V, float& xbarN)
+{
+    const float SN = (MODEL & kModelEulerS) ? x : exp2f(x);
+    const float itm = P.phi * (SN - P.K);
+    V = itm > 0.0f ? P.disc * itm : 0.0f;
+    xbarN = itm > 0.0f ? P.disc * P.phi * ((MODEL & kModelEulerS) ? P.S0f : SN) : 0.0f;
+}
+
+// ln S of a path state (per-path diagnostics).
+template <int MODEL>
+__device__ __forceinline__ float ln_spot(float x)
+{
+    return (MODEL & kModelEulerS) ? logf(x) : x * 0.6931471805599453f;
 }
 
 // Near-node decision log of the DBG instantiation: (path, step, 2 i + inside).
@@ -194,7 +268,7 @@ __device__ __forceinline__ void log_cell_decision(const McParams& P, const SmemG
 }
 
 // Forward pass of one path from x0; checkpoints every KCK steps when STORE.
-template <int KCK, bool STORE, bool DBG>
+template <int KCK, bool STORE, bool DBG, int MODEL = 0>
 __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
                                               float* ck, size_t cks, long long rel)
 {
@@ -209,9 +283,9 @@ __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid&
             if (n < P.N) {
                 if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
                 const int4 tb = g.tab[n];
-                const StepEval e = eval_sigma<false>(P, g, x, tb);
+                const StepEval e = eval_sigma<false, MODEL>(P, g, x, tb);
                 if (DBG) log_cell_decision(P, g, e, rel, n);
-                x = euler_step(P, x, e.sigma, z[q & 3]);
+                x = step_state<MODEL>(P, x, e.sigma, z[q & 3]);
             }
         }
     }
@@ -223,7 +297,7 @@ __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid&
 // forward_path (its checkpoints and terminal state are bit-identical), and
 // the per-step time data is loaded once for both. Path b is logged only
 // when log_b (it may lie past the end of the call's range).
-template <int KCK, bool STORE, bool DBG>
+template <int KCK, bool STORE, bool DBG, int MODEL = 0>
 __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid& g, uint32_t c1a, uint32_t c2a,
                                               uint32_t c1b, uint32_t c2b, float* cka, float* ckb, size_t cks,
                                               long long rel_a, long long rel_b, bool log_b, float& ya_out,
@@ -246,14 +320,14 @@ __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid&
                     normals4((uint32_t)(n >> 2), c1b, c2b, P.k0, P.k1, zb);
                 }
                 const int4 tb = g.tab[n];
-                const StepEval ea = eval_sigma<false>(P, g, ya, tb);
-                const StepEval eb = eval_sigma<false>(P, g, yb, tb);
+                const StepEval ea = eval_sigma<false, MODEL>(P, g, ya, tb);
+                const StepEval eb = eval_sigma<false, MODEL>(P, g, yb, tb);
                 if (DBG) {
                     log_cell_decision(P, g, ea, rel_a, n);
                     if (log_b) log_cell_decision(P, g, eb, rel_b, n);
                 }
-                ya = euler_step(P, ya, ea.sigma, za[q & 3]);
-                yb = euler_step(P, yb, eb.sigma, zb[q & 3]);
+                ya = step_state<MODEL>(P, ya, ea.sigma, za[q & 3]);
+                yb = step_state<MODEL>(P, yb, eb.sigma, zb[q & 3]);
             }
         }
     }
@@ -280,7 +354,7 @@ __device__ __forceinline__ void path_counter(const McParams& P, long long rel, u
 // (i+1, j+1) with the bilinear weights. Corner sums are kept in registers
 // while the cell is unchanged and then added to the block's binary32 buckets
 // `l1` (time-major, row j * I) with red.global.add.f32. Returns d V / d x_0.
-template <int KCK>
+template <int KCK, int MODEL = 0>
 __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
                                               const float* ck, size_t cks, float xbar, float* l1)
 {
@@ -300,13 +374,11 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
             if (n < P.N) {
                 if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
                 const int4 tb = g.tab[n];
-                const StepEval ev = eval_sigma<true>(P, g, x, tb);
-                const float h = fmaf(P.sqdt, z[q & 3], -ev.sigma * P.dt);
-                hq[q] = h;
-                gq[q] = h * (ev.S * ev.slope);
+                const StepEval ev = eval_sigma<true, MODEL>(P, g, x, tb);
+                adjoint_factors<MODEL>(P, ev, z[q & 3], hq[q], gq[q]);
                 uq[q] = ev.u;
                 iq[q] = ev.i;
-                x = euler_step(P, x, ev.sigma, z[q & 3]);
+                x = step_state<MODEL>(P, x, ev.sigma, z[q & 3]);
             }
         }
 #pragma unroll
@@ -359,6 +431,7 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
 // D_N; `tiny` is set when some |1 + g_n| < 2^-20, where dividing by D loses
 // what the reverse sweep keeps. The path's arithmetic is that of
 // forward_path (same sigma, same Euler step), so y_N is the same.
+template <int MODEL = 0>
 __device__ __forceinline__ float tangent_forward(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
                                                  float& D, bool& tiny)
 {
@@ -372,12 +445,13 @@ __device__ __forceinline__ float tangent_forward(const McParams& P, const SmemGr
             const int n = n0 + q;
             if (n < P.N) {
                 const int4 tb = g.tab[n];
-                const StepEval e = eval_sigma<true>(P, g, y, tb);
-                const float h = fmaf(P.sqdt, z[q], -e.sigma * P.dt);
-                const float f = fmaf(h, e.S * e.slope, 1.0f);      // 1 + g_n
+                const StepEval e = eval_sigma<true, MODEL>(P, g, y, tb);
+                float h, gn;
+                adjoint_factors<MODEL>(P, e, z[q], h, gn);
+                const float f = tangent_factor<MODEL>(P, e, z[q], h);   // 1 + g_n
                 fmin = fminf(fmin, fabsf(f));
                 d *= f;
-                y = euler_step(P, y, e.sigma, z[q]);
+                y = step_state<MODEL>(P, y, e.sigma, z[q]);
             }
         }
     }
@@ -390,6 +464,7 @@ __device__ __forceinline__ float tangent_forward(const McParams& P, const SmemGr
 // sigma_bar_n = c h_n / D_{n+1}, c = xbar_N D_N, over the corner buckets of
 // its cell with the bilinear weights, through the same run-length register
 // sums and binary32 reductions into `l1` as reverse_path, in time order.
+template <int MODEL = 0>
 __device__ __forceinline__ void tangent_scatter(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
                                                 float c, float* l1)
 {
@@ -404,9 +479,10 @@ __device__ __forceinline__ void tangent_scatter(const McParams& P, const SmemGri
             const int n = n0 + q;
             if (n < P.N) {
                 const int4 tb = g.tab[n];
-                const StepEval e = eval_sigma<true>(P, g, y, tb);
-                const float h = fmaf(P.sqdt, z[q], -e.sigma * P.dt);
-                d *= fmaf(h, e.S * e.slope, 1.0f);                // D_{n+1}
+                const StepEval e = eval_sigma<true, MODEL>(P, g, y, tb);
+                float h, gn;
+                adjoint_factors<MODEL>(P, e, z[q], h, gn);
+                d *= tangent_factor<MODEL>(P, e, z[q], h);          // D_{n+1}
                 const float sbar = __fdividef(c * h, d);
                 const int key = tb.z + e.i;
                 if (key != cur) {
@@ -427,7 +503,7 @@ __device__ __forceinline__ void tangent_scatter(const McParams& P, const SmemGri
                 AU = fmaf(a, e.u, AU);
                 Bs += b;
                 BU = fmaf(b, e.u, BU);
-                y = euler_step(P, y, e.sigma, z[q]);
+                y = step_state<MODEL>(P, y, e.sigma, z[q]);
             }
         }
     }

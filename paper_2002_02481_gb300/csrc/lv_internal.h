@@ -29,15 +29,18 @@ struct McParams {
     float cell_shift;      // -ln(s_0) / d(ln s)
     float s_lo, s_hi;      // s_0, s_{I-1}
 
-    // option and scheme; the path state is y = log2 S
-    float x0;              // log2 S0
-    float rdt;             // log2(e) r dt
+    // option and scheme; the path state is y = log2 S (or S when the model
+    // runs the Euler scheme on S)
+    int model;             // bit 0: spot weight linear in ln S; bit 1: Euler scheme on S
+    float x0;              // log2 S0 (S0 on S)
+    float rdt;             // log2(e) r dt (r dt on S)
     float hdt;             // log2(e) dt / 2
     float sqdt2;           // log2(e) sqrt(dt)
     float dt;
     float sqdt;            // sqrt(dt) (natural units, for d x_{n+1} / d sigma_n)
     float K;
     float disc;            // e^{-rT}
+    float S0f, inv_S0;     // S0, 1 / S0 (the scaled adjoint of the scheme on S)
     float phi;             // +1 call, -1 put
     double dt_d;           // dt in binary64 for the time table
     int N;                 // steps
@@ -120,8 +123,22 @@ size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_sme
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method,
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, int model,
                          size_t smem, int* blocks_per_sm);
+
+// The kernels of the other models (lv_model1.cu .. lv_model3.cu, one
+// translation unit each so that they compile in parallel); they exist for
+// checkpoint intervals k = 4 and 8.
+#define LV_DECLARE_MODEL(N)                                                                                \
+    cudaError_t launch_mc_model##N(const McParams& p, int grid, int block, int k, bool greeks, size_t smem, \
+                                   cudaStream_t s);                                                        \
+    cudaError_t mc_occupancy_model##N(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem,    \
+                                      int method, size_t smem, int* blocks_per_sm);
+LV_DECLARE_MODEL(1)
+LV_DECLARE_MODEL(2)
+LV_DECLARE_MODEL(3)
+#undef LV_DECLARE_MODEL
+constexpr int kModelMaxK = 8;
 int ring_slots_per_warp();
 int paths_per_tile(bool greeks);   // paths a warp claims at a time (adjoint / price kernel)
 
@@ -205,11 +222,14 @@ struct lv_surface_s {
     int device = 0;
     int num_sms = 0;
     int adj_method = 0;              // LV_ADJ_REVERSE or LV_ADJ_TANGENT
+    int interp = 0;                  // LV_INTERP_S or LV_INTERP_LOGS
+    int scheme = 0;                  // LV_SCHEME_LOG or LV_SCHEME_S
     int I = 0, J = 0, Je = 0;
     std::vector<double> spot, time;
     float2* d_sig = nullptr;         // [Je][I-1] pairs (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j})
     float* d_node = nullptr;
     float2* d_ab = nullptr;
+    float2* d_abl = nullptr;         // [I] cell coefficients of the ln-S weight, in y = log2 S
     double* d_tau = nullptr;
     float2* h_sig_stage = nullptr;   // pinned staging for sigma uploads
     int log_uniform = 0;

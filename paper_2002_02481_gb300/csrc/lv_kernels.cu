@@ -1,441 +1,11 @@
-// lv_kernels.cu -- the Monte Carlo price / pathwise-adjoint kernels and the
-// fixed-order finalize (arXiv 2002.02481, Sec. III, IV-A..IV-D).
-//
-// Adjoint kernel: persistent, warp-centric, no block-wide barrier in its
-// main loop. Every warp repeatedly either
-//   (F) claims a tile of 32 consecutive paths from a global counter and runs
-//       their forward passes: normals generated in registers, log-Euler
-//       steps under the bilinear grid staged in shared memory, x stored every
-//       KCK steps (the checkpoints) into one of kRing groups of 32 slots
-//       owned by the warp; payoff and terminal adjoint
-//       xbar_N = e^{-rT} 1{phi(S_N - K) > 0} phi S_N; the paths with a
-//       nonzero xbar_N (all others have a zero adjoint everywhere) are
-//       appended to a per-warp FIFO in shared memory; or
-//   (R) takes up to 32 queued paths and runs their reverse sweeps: per
-//       checkpoint segment, last to first, recompute KCK steps from the
-//       checkpoint with the same Philox counters keeping h_n = d x_{n+1} /
-//       d sigma_n, g_n = h_n S_n d sigma / d S, the cell and the weight in
-//       registers, then walk back: sigma_bar_n = xbar_{n+1} h_n,
-//       xbar_n = xbar_{n+1} (1 + g_n), sigma_bar_n spread over the four
-//       corner buckets with the bilinear weights.
-// A reverse batch runs when 32 paths are queued, when the oldest queued
-// path's checkpoint slots are about to be reused by the next forward tile,
-// and at the end; so the reverse sweeps run on full warps.
-//
-// Bucket accumulation: run-length sums in registers while the cell is
-// unchanged (level 0); binary32 reductions (red.global.add.f32, resolved in
-// L2 without a retry loop) into a per-block bucket array in global memory
-// (level 1); every few batches a warp drains that array (atomicExch) into
-// level 2: the block's binary64 row through binary64 reductions, or in Kahan
-// mode a compensated binary32 row the warp owns; at the end each block folds
-// what is left into its binary64 row, and a separate fixed-order binary64
-// reduction over blocks gives the outputs (level 3).
-//
-// The DBG instantiation additionally writes per-path results and logs
-// every forward step whose spot lies within a relative band of its cell's
-// nodes, with the cell and inside-grid decision taken there, so that a
-// test can hand the same decisions to the binary64 oracle.
-#include <math.h>
-
-#include "lv_device.cuh"
+// lv_kernels.cu -- the main model's Monte Carlo kernels (instantiated from
+// lv_mc.cuh), the launchers that route every model to its translation unit,
+// and the fixed-order binary64 finalize (level 3 of the bucket sums).
+#include "lv_mc.cuh"
 
 namespace lv {
 
 namespace {
-
-constexpr int kTile = 32;      // paths per warp tile of the adjoint kernel (one per lane)
-constexpr int kPriceTile = 64; // paths per warp tile of the price kernel (two per lane)
-constexpr int kRing = 4;       // checkpoint slot groups of kTile per warp
-constexpr int kQueue = 64;     // per-warp FIFO capacity (entries; < 32 + kTile never overflows)
-constexpr int kMaxWarps = 8;   // blockDim.x <= 256 (the adjoint kernel runs at most 128)
-
-__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
-
-// Level-2 accumulator of one value: binary64 or Kahan-compensated binary32.
-// The slots live in shared memory (one per thread and value), which keeps
-// them out of the registers the reverse sweep needs.
-struct AccSlot {
-    double d;
-    float s, c;
-};
-
-struct SmemLayout {
-    size_t tab, sig, node, ab, qslot, qrel, qxb, acc, red, total;
-};
-
-__host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks, bool grid_smem)
-{
-    const int W = block / 32;
-    SmemLayout L;
-    size_t o = 0;
-    L.tab = o;   o += align16(sizeof(int4) * (size_t)N);
-    L.sig = o;   if (grid_smem) o += align16(sizeof(float2) * (size_t)Je * (I - 1));
-    L.node = o;  o += align16(sizeof(float) * (size_t)I);
-    L.ab = o;    o += align16(sizeof(float2) * (size_t)I);
-    L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
-    L.qrel = o;  if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
-    L.qxb = o;   if (greeks) o += align16(sizeof(float) * (size_t)W * kQueue);
-    L.acc = o;   o += align16(sizeof(AccSlot) * 3 * (size_t)block);
-    L.red = o;   o += align16(sizeof(double) * 3 * kMaxWarps);
-    L.total = o;
-    return L;
-}
-
-// Adds x to a level-2 slot.
-template <int ACC>
-__device__ __forceinline__ void acc_add(AccSlot& a, float x)
-{
-    if (ACC == 1) {
-        const float y = x - a.c;
-        const float t = a.s + y;
-        a.c = (t - a.s) - y;
-        a.s = t;
-    } else {
-        a.d += (double)x;
-    }
-}
-
-template <int ACC>
-__device__ __forceinline__ double acc_value(const AccSlot& a)
-{
-    return ACC == 1 ? (double)a.s - (double)a.c : a.d;
-}
-
-// Stages the time table, the spot nodes, the cell coefficients and (when GS)
-// the sigma pairs in shared memory; large grids are read from global memory
-// through L1 instead, which leaves room for more resident blocks.
-template <bool GS>
-__device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* smem, const SmemLayout& L)
-{
-    const int B = blockDim.x, tid = threadIdx.x;
-    int4* s_tab = reinterpret_cast<int4*>(smem + L.tab);
-    float2* s_sig = reinterpret_cast<float2*>(smem + L.sig);
-    float* s_node = reinterpret_cast<float*>(smem + L.node);
-    float2* s_ab = reinterpret_cast<float2*>(smem + L.ab);
-    if (GS)
-        for (int e = tid; e < P.Je * (P.I - 1); e += B) s_sig[e] = P.sig2[e];
-    for (int e = tid; e < P.I; e += B) s_node[e] = P.node[e];
-    for (int e = tid; e < P.I - 1; e += B) s_ab[e] = P.ab[e];
-    for (int n = tid; n < P.N; n += B) s_tab[n] = step_time(P, n);
-}
-
-// Block sum of three per-thread binary64 values into row[0..2] (fixed order).
-__device__ __forceinline__ void block_scalars(double a, double b, double c, double* s_red, double* row)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-        c += __shfl_down_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) {
-        s_red[3 * warp + 0] = a;
-        s_red[3 * warp + 1] = b;
-        s_red[3 * warp + 2] = c;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double sa = 0.0, sb = 0.0, sc = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            sa += s_red[3 * w + 0];
-            sb += s_red[3 * w + 1];
-            sc += s_red[3 * w + 2];
-        }
-        row[0] = sa;
-        row[1] = sb;
-        row[2] = sc;
-    }
-}
-
-__device__ __forceinline__ int claim_tile(unsigned int* counter)
-{
-    int t = 0;
-    if ((threadIdx.x & 31) == 0) t = (int)atomicAdd(counter, 1u);
-    return __shfl_sync(0xffffffffu, t, 0);
-}
-
-template <int ACC>
-__device__ __forceinline__ void drain_buckets(float* l1, int nIJ, double* wrow)
-{
-    const int lane = threadIdx.x & 31;
-    for (int e = lane; e < nIJ; e += 32) {
-        if (l1[e] == 0.0f) continue;            // a skipped bucket is drained later
-        const float v = atomicExch(&l1[e], 0.0f);
-        if (ACC == 1) {
-            float2* k = reinterpret_cast<float2*>(wrow) + e;
-            float2 p = *k;
-            const float y = v - p.y;
-            const float t = p.x + y;
-            p.y = (t - p.x) - y;
-            p.x = t;
-            *k = p;
-        } else {
-            atomicAdd(&wrow[e], (double)v);       // the block's row, shared by its warps
-        }
-    }
-}
-
-template <int KCK, int ACC, bool DBG, bool GS>
-__global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__ McParams P)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int B = blockDim.x, W = B >> 5;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
-    stage_grid<GS>(P, smem, L);
-    float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);    // this block's level-1 buckets
-    int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQueue;
-    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
-    float* q_xb = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
-    double* s_red = reinterpret_cast<double*>(smem + L.red);
-    const int nIJ = P.Je * P.I;
-    for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
-    const int wid = blockIdx.x * W + warp;                    // global warp id
-    // level 2: binary64 mode drains into the block's own row with binary64
-    // reductions; Kahan pairs cannot be updated atomically, so each warp owns one
-    double* const row = P.partials + (size_t)blockIdx.x * P.row_words;
-    double* wrow;
-    if (ACC == 1) {
-        wrow = P.warp_rows + (size_t)wid * nIJ;
-        for (int e = lane; e < nIJ; e += 32) wrow[e] = 0.0;   // zero as a float2 pair too
-    } else {
-        wrow = row + 3;
-        for (int e = tid; e < nIJ; e += B) wrow[e] = 0.0;
-    }
-    __syncthreads();
-
-    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
-                      GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
-                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
-    const size_t cks = (size_t)gridDim.x * W * kRing * kTile;   // checkpoint stride
-    float* const ckw = P.ckpt + (size_t)wid * kRing * kTile;     // this warp's slots
-
-    AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
-    acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
-    int q_head = 0, q_count = 0, batches = 0;
-    unsigned fwd_count = 0;
-    int tile = claim_tile(P.tile_counter);
-
-    while (true) {
-        const int g_next = (int)(fwd_count % kRing);
-        const bool more = tile < P.n_tiles;
-        const bool reuse = more && q_count > 0 && q_slot[q_head] / kTile == g_next;
-        if (q_count >= 32 || (!more && q_count > 0) || reuse) {
-            // ---------------- reverse batch over up to 32 queued paths
-            const int nb = min(32, q_count);
-            if (lane < nb) {
-                const int e = (q_head + lane) & (kQueue - 1);
-                const int slot = q_slot[e];
-                const long long rel = q_rel[e];
-                float xbar = q_xb[e];
-                uint32_t c1, c2;
-                path_counter(P, rel, c1, c2);
-                xbar = reverse_path<KCK>(P, g, c1, c2, ckw + slot, cks, xbar, l1);
-                acc_add<ACC>(acc[2 * B], xbar);
-                if (DBG) P.dbg_xbar0[rel] = xbar;
-            }
-            q_head = (q_head + nb) & (kQueue - 1);
-            q_count -= nb;
-            __syncwarp();
-            if (++batches % P.flush_every == 0) drain_buckets<ACC>(l1, nIJ, wrow);
-            continue;
-        }
-        if (!more) break;
-
-        // ---------------- forward tile of 32 paths into slot group g_next
-        const long long rel = (long long)tile * kTile + lane;
-        const bool active = rel < P.n_paths;
-        const int slot = g_next * kTile + lane;
-        float xbarN = 0.0f;
-        if (active) {
-            uint32_t c1, c2;
-            path_counter(P, rel, c1, c2);
-            const float x = forward_path<KCK, true, DBG>(P, g, c1, c2, ckw + slot, cks, rel);
-            const float SN = exp2f(x);
-            const float itm = P.phi * (SN - P.K);
-            const float V = itm > 0.0f ? P.disc * itm : 0.0f;
-            xbarN = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
-            acc_add<ACC>(acc[0], V);
-            acc_add<ACC>(acc[B], V * V);
-            if (DBG) {
-                P.dbg_xN[rel] = x * 0.6931471805599453f;   // ln S_N
-                P.dbg_V[rel] = V;
-                P.dbg_xbar0[rel] = 0.0f;
-            }
-        }
-        const bool live = xbarN != 0.0f;
-        const unsigned bal = __ballot_sync(0xffffffffu, live);
-        if (live) {
-            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
-            q_slot[e] = slot;
-            q_rel[e] = (int)rel;
-            q_xb[e] = xbarN;
-        }
-        q_count += __popc(bal);
-        ++fwd_count;
-        __syncwarp();
-        tile = claim_tile(P.tile_counter);
-    }
-
-    // fold: remaining level-1 buckets (and, in Kahan mode, every warp row of
-    // this block) into the block's binary64 row (after the barrier nothing adds)
-    __syncthreads();
-    const double* rows0 = P.warp_rows + (size_t)blockIdx.x * W * nIJ;
-    for (int e = tid; e < nIJ; e += B) {
-        if (ACC == 1) {
-            double s = (double)l1[e];
-            for (int w = 0; w < W; ++w) {
-                const float2 k = reinterpret_cast<const float2*>(rows0 + (size_t)w * nIJ)[e];
-                s += (double)k.x - (double)k.y;
-            }
-            row[3 + e] = s;
-        } else {
-            row[3 + e] += (double)l1[e];
-        }
-    }
-    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
-}
-
-// Tangent-ratio adjoint (LV_ADJ_TANGENT): persistent and warp-centric like
-// adjoint_kernel, without checkpoints. A warp claims a tile of 32 paths and
-// runs pass 1 (tangent_forward): payoff, xbar_N, and xbar_0 = xbar_N D_N;
-// the paths with xbar_N != 0 join the warp's queue with c = xbar_N D_N. At
-// 32 queued paths (and at the end) the warp runs pass 2 (tangent_scatter)
-// on them as a full-warp batch. Buckets go through the same levels 0-3.
-template <int ACC, bool GS>
-__global__ void __launch_bounds__(128, 6) tangent_kernel(const __grid_constant__ McParams P)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int B = blockDim.x, W = B >> 5;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
-    stage_grid<GS>(P, smem, L);
-    float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);
-    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
-    float* q_c = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
-    double* s_red = reinterpret_cast<double*>(smem + L.red);
-    const int nIJ = P.Je * P.I;
-    for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
-    const int wid = blockIdx.x * W + warp;
-    double* const row = P.partials + (size_t)blockIdx.x * P.row_words;
-    double* wrow;
-    if (ACC == 1) {
-        wrow = P.warp_rows + (size_t)wid * nIJ;
-        for (int e = lane; e < nIJ; e += 32) wrow[e] = 0.0;
-    } else {
-        wrow = row + 3;
-        for (int e = tid; e < nIJ; e += B) wrow[e] = 0.0;
-    }
-    __syncthreads();
-    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
-                      GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
-                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
-    AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
-    acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
-    int q_head = 0, q_count = 0, batches = 0;
-    int tile = claim_tile(P.tile_counter);
-    while (true) {
-        const bool more = tile < P.n_tiles;
-        if (q_count >= 32 || (!more && q_count > 0)) {
-            const int nb = min(32, q_count);
-            if (lane < nb) {
-                const int e = (q_head + lane) & (kQueue - 1);
-                uint32_t c1, c2;
-                path_counter(P, q_rel[e], c1, c2);
-                tangent_scatter(P, g, c1, c2, q_c[e], l1);
-            }
-            q_head = (q_head + nb) & (kQueue - 1);
-            q_count -= nb;
-            __syncwarp();
-            if (++batches % P.flush_every == 0) drain_buckets<ACC>(l1, nIJ, wrow);
-            continue;
-        }
-        if (!more) break;
-        const long long rel = (long long)tile * kTile + lane;
-        float xbarN = 0.0f, c = 0.0f;
-        if (rel < P.n_paths) {
-            uint32_t c1, c2;
-            path_counter(P, rel, c1, c2);
-            float D;
-            bool tiny;
-            const float y = tangent_forward(P, g, c1, c2, D, tiny);
-            const float SN = exp2f(y);
-            const float itm = P.phi * (SN - P.K);
-            const float V = itm > 0.0f ? P.disc * itm : 0.0f;
-            xbarN = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
-            c = xbarN * D;
-            acc_add<ACC>(acc[0], V);
-            acc_add<ACC>(acc[B], V * V);
-            acc_add<ACC>(acc[2 * B], c);
-            if (tiny && xbarN != 0.0f) atomicAdd(P.flag, 1u);
-        }
-        const bool live = xbarN != 0.0f;
-        const unsigned bal = __ballot_sync(0xffffffffu, live);
-        if (live) {
-            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
-            q_rel[e] = (int)rel;
-            q_c[e] = c;
-        }
-        q_count += __popc(bal);
-        __syncwarp();
-        tile = claim_tile(P.tile_counter);
-    }
-    __syncthreads();
-    const double* rows0 = P.warp_rows + (size_t)blockIdx.x * W * nIJ;
-    for (int e = tid; e < nIJ; e += B) {
-        if (ACC == 1) {
-            double s = (double)l1[e];
-            for (int w = 0; w < W; ++w) {
-                const float2 k = reinterpret_cast<const float2*>(rows0 + (size_t)w * nIJ)[e];
-                s += (double)k.x - (double)k.y;
-            }
-            row[3 + e] = s;
-        } else {
-            row[3 + e] += (double)l1[e];
-        }
-    }
-    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
-}
-
-template <int ACC, bool GS>
-__global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ McParams P)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, blockDim.x, false, GS);
-    stage_grid<GS>(P, smem, L);
-    __syncthreads();
-    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
-                      GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
-                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
-    const int lane = threadIdx.x & 31;
-    AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + threadIdx.x;
-    acc[0] = acc[blockDim.x] = AccSlot{0.0, 0.0f, 0.0f};
-    for (int tile = claim_tile(P.tile_counter); tile < P.n_tiles; tile = claim_tile(P.tile_counter)) {
-        const long long rel_a = (long long)tile * kPriceTile + lane, rel_b = rel_a + 32;
-        if (rel_a < P.n_paths) {
-            uint32_t c1a, c2a, c1b, c2b;
-            path_counter(P, rel_a, c1a, c2a);
-            path_counter(P, rel_b, c1b, c2b);
-            float ya, yb;
-            forward_path2<4, false, false>(P, g, c1a, c2a, c1b, c2b, nullptr, nullptr, 0, rel_a, rel_b, false, ya,
-                                           yb);
-            float itm = P.phi * (exp2f(ya) - P.K);
-            float V = itm > 0.0f ? P.disc * itm : 0.0f;
-            acc_add<ACC>(acc[0], V);
-            acc_add<ACC>(acc[blockDim.x], V * V);
-            if (rel_b < P.n_paths) {
-                itm = P.phi * (exp2f(yb) - P.K);
-                V = itm > 0.0f ? P.disc * itm : 0.0f;
-                acc_add<ACC>(acc[0], V);
-                acc_add<ACC>(acc[blockDim.x], V * V);
-            }
-        }
-    }
-    double* s_red = reinterpret_cast<double*>(smem + L.red);
-    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[blockDim.x]), 0.0, s_red,
-                  P.partials + (size_t)blockIdx.x * P.row_words);
-}
 
 // Level 3, stage 1: rows [chunk * RCH, (chunk + 1) * RCH) summed in order,
 // column by column, into one binary64 row per chunk.
@@ -490,71 +60,6 @@ __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks,
     out[3 + i * J + j] = want_sums ? s : s / P;
 }
 
-template <typename K>
-cudaError_t set_smem_attr(K kernel)
-{
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-}
-
-template <typename K>
-cudaError_t launch_configured(K kernel, bool& configured, const McParams& p, int grid, int block, size_t smem,
-                              cudaStream_t s)
-{
-    if (!configured) {
-        cudaError_t e = set_smem_attr(kernel);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    kernel<<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <typename K>
-cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
-{
-    cudaError_t e = set_smem_attr(kernel);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kernel, block, smem);
-}
-
-// Calls f(kernel, flag) with the instantiation for (greeks, k, acc, dbg, gs).
-template <bool GS, typename F>
-cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, F&& f)
-{
-    if (!greeks) {
-        static bool c0 = false, c1 = false;
-        return acc ? f(price_kernel<1, GS>, c1) : f(price_kernel<0, GS>, c0);
-    }
-    if (method == LV_ADJ_TANGENT && !dbg) {
-        static bool t0 = false, t1 = false;
-        return acc ? f(tangent_kernel<1, GS>, t1) : f(tangent_kernel<0, GS>, t0);
-    }
-    if (dbg) {
-        static bool cd = false;
-        if (k != 4) return cudaErrorInvalidValue;       // scratch must be planned with k = 4
-        return f(adjoint_kernel<4, 0, true, GS>, cd);
-    }
-    static bool c[8] = {};
-    switch (k * 2 + acc) {
-    case 8: return f(adjoint_kernel<4, 0, false, GS>, c[0]);
-    case 9: return f(adjoint_kernel<4, 1, false, GS>, c[1]);
-    case 16: return f(adjoint_kernel<8, 0, false, GS>, c[2]);
-    case 17: return f(adjoint_kernel<8, 1, false, GS>, c[3]);
-    case 32: return f(adjoint_kernel<16, 0, false, GS>, c[4]);
-    case 33: return f(adjoint_kernel<16, 1, false, GS>, c[5]);
-    case 64: return f(adjoint_kernel<32, 0, false, GS>, c[6]);
-    case 65: return f(adjoint_kernel<32, 1, false, GS>, c[7]);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename F>
-cudaError_t with_kernel(bool greeks, int k, int acc, bool dbg, bool gs, int method, F&& f)
-{
-    return gs ? with_kernel_gs<true>(greeks, k, acc, dbg, method, f)
-              : with_kernel_gs<false>(greeks, k, acc, dbg, method, f);
-}
-
 }  // namespace
 
 size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem)
@@ -568,17 +73,25 @@ int paths_per_tile(bool greeks) { return greeks ? kTile : kPriceTile; }
 cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
                       cudaStream_t s)
 {
-    return with_kernel(greeks, k, p.acc_mode, p.dbg_xN != nullptr, p.grid_smem != 0, p.method,
-                       [&](auto kernel, bool& configured) {
-                           return launch_configured(kernel, configured, p, grid, block, smem, s);
-                       });
+    switch (p.model) {
+    case 0: return launch_model_impl<0>(p, grid, block, k, greeks, smem, s);
+    case 1: return launch_mc_model1(p, grid, block, k, greeks, smem, s);
+    case 2: return launch_mc_model2(p, grid, block, k, greeks, smem, s);
+    case 3: return launch_mc_model3(p, grid, block, k, greeks, smem, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, size_t smem,
-                         int* bps)
+cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, int model,
+                         size_t smem, int* bps)
 {
-    return with_kernel(greeks, k, acc, dbg, grid_smem, method,
-                       [&](auto kernel, bool&) { return occupancy(kernel, block, smem, bps); });
+    switch (model) {
+    case 0: return occupancy_model_impl<0>(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
+    case 1: return mc_occupancy_model1(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
+    case 2: return mc_occupancy_model2(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
+    case 3: return mc_occupancy_model3(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s)

@@ -1,0 +1,20 @@
+// lv_model3.cu -- the kernels of model 3 (both: Euler on S, weight linear in ln S), from lv_mc.cuh,
+// in a translation unit of their own so that the build compiles the models
+// in parallel.
+#include "lv_mc.cuh"
+
+namespace lv {
+
+cudaError_t launch_mc_model3(const McParams& p, int grid, int block, int k, bool greeks, size_t smem,
+                              cudaStream_t s)
+{
+    return launch_model_impl<3>(p, grid, block, k, greeks, smem, s);
+}
+
+cudaError_t mc_occupancy_model3(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method,
+                                 size_t smem, int* bps)
+{
+    return occupancy_model_impl<3>(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
+}
+
+}  // namespace lv

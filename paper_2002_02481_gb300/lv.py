@@ -22,6 +22,8 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "lv.h")
 LV_OK, LV_EINVAL, LV_ENOMEM, LV_ECUDA, LV_EINTERNAL, LV_ENUMERIC = range(6)
 LV_ACC_FP64, LV_ACC_KAHAN = 0, 1
 LV_ADJ_REVERSE, LV_ADJ_TANGENT = 0, 1
+LV_INTERP_S, LV_INTERP_LOGS = 0, 1
+LV_SCHEME_LOG, LV_SCHEME_S = 0, 1
 LV_OUT_PRICE, LV_OUT_DELTA, LV_OUT_STDERR, LV_OUT_VEGA = 0, 1, 2, 3
 LV_SUM_V, LV_SUM_V2, LV_SUM_XBAR0, LV_SUM_VEGA = 0, 1, 2, 3
 
@@ -69,6 +71,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_set_stream": [vp, vp],
         "lv_set_accumulation": [vp, i32],
         "lv_set_adjoint_method": [vp, i32],
+        "lv_surface_set_interpolation": [vp, i32],
+        "lv_set_scheme": [vp, i32],
         "lv_set_launch": [vp, i32, i32, i32],
         "lv_set_kernel_events": [vp, vp, vp],
         "lv_tune": [vp, d, d, d, d, i32, i64, u64, c.POINTER(i32), c.POINTER(i32), c.POINTER(d)],
@@ -170,6 +174,14 @@ class Surface:
     def set_adjoint_method(self, method: int) -> None:
         """LV_ADJ_REVERSE (checkpointed reverse sweep) or LV_ADJ_TANGENT (tangent ratio)."""
         _check(self.lib, self.lib.lv_set_adjoint_method(self.h, int(method)), "lv_set_adjoint_method")
+
+    def set_interpolation(self, interp: int) -> None:
+        """LV_INTERP_S (spot weight linear in S) or LV_INTERP_LOGS (in ln S)."""
+        _check(self.lib, self.lib.lv_surface_set_interpolation(self.h, int(interp)), "lv_surface_set_interpolation")
+
+    def set_scheme(self, scheme: int) -> None:
+        """LV_SCHEME_LOG (Euler on ln S) or LV_SCHEME_S (Euler on S)."""
+        _check(self.lib, self.lib.lv_set_scheme(self.h, int(scheme)), "lv_set_scheme")
 
     def set_launch(self, block: int = 0, k: int = 0, blocks_per_sm: int = 0) -> None:
         _check(self.lib, self.lib.lv_set_launch(self.h, int(block), int(k), int(blocks_per_sm)), "lv_set_launch")

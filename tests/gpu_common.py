@@ -34,6 +34,8 @@ def make_surface(w_surf, opt, lib, launch=None, accumulation=0, method=lv.LV_ADJ
     s.set_option_type(opt.phi)
     s.set_accumulation(accumulation)
     s.set_adjoint_method(method)
+    s.set_interpolation(getattr(w_surf, "interp", 0))
+    s.set_scheme(getattr(opt, "scheme", 0))
     if launch:
         s.set_launch(*launch)
     return s
