@@ -161,7 +161,8 @@ def kernel_source_hash() -> str:
     them invalidates a recorded traffic figure)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2002_02481_gb300", "csrc")
-    text = "".join(open(os.path.join(csrc, f)).read() for f in ("lv_device.cuh", "lv_kernels.cu", "lv_internal.h"))
+    text = "".join(open(os.path.join(csrc, f)).read()
+                   for f in ("lv_device.cuh", "lv_mc.cuh", "lv_kernels.cu", "lv_internal.h"))
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
