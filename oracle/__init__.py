@@ -24,8 +24,9 @@ _SRC = os.path.join(_HERE, "lv_oracle.c")
 _HDR = os.path.join(_HERE, "lv_oracle.h")
 _LIB = os.path.join(_HERE, "_build", "liblv_oracle.so")
 
-NSCAL = 9
-SUM_V, SUM_V2, SUM_XBAR0, SUM_XBAR0_2, SUM_VTOT, SUM_VTOT_2, SUM_SN, KINK_COUNT, KINK_XBAR0 = range(9)
+NSCAL = 13
+(SUM_V, SUM_V2, SUM_XBAR0, SUM_XBAR0_2, SUM_VTOT, SUM_VTOT_2, SUM_SN, KINK_COUNT, KINK_XBAR0,
+ SUM_RHO, SUM_RHO_2, SUM_DVDT, SUM_DVDT_2) = range(13)
 
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
@@ -83,7 +84,7 @@ class Decisions:
 class _Point(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("u", ctypes.c_double),
                 ("v", ctypes.c_double), ("w", ctypes.c_double * 4),
-                ("sigma", ctypes.c_double), ("dsigma_dS", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("dsigma_dS", ctypes.c_double), ("dsigma_dt", ctypes.c_double)]
 
 
 def build(src: str = _SRC, out: str = _LIB, extra: tuple = ()) -> str:
@@ -216,7 +217,8 @@ def sigma_eval(surface, S: float, t: float, lib=None) -> dict:
               interp=getattr(surface, "interp", 0))
     p = _Point()
     lib.orc_sigma_eval(ctypes.byref(a.surf), float(S), float(t), ctypes.byref(p))
-    return dict(i=p.i, j=p.j, u=p.u, v=p.v, w=list(p.w), sigma=p.sigma, dsigma_dS=p.dsigma_dS)
+    return dict(i=p.i, j=p.j, u=p.u, v=p.v, w=list(p.w), sigma=p.sigma, dsigma_dS=p.dsigma_dS,
+                dsigma_dt=p.dsigma_dt)
 
 
 def run_sums(surface, opt, path_begin: int = 0, path_end: Optional[int] = None,
@@ -253,7 +255,8 @@ def price_greeks(surface, opt, n_threads: Optional[int] = None, lib=None) -> dic
     IJ = surface.n_spot * surface.n_time
     res = finalize(s, opt.n_paths, opt.S0, IJ, lib)
     return dict(price=res[0], delta=res[1], stderr=res[2],
-                vega=res[3:].reshape(surface.n_spot, surface.n_time), sums=s)
+                vega=res[3:].reshape(surface.n_spot, surface.n_time), sums=s,
+                rho=s[SUM_RHO] / opt.n_paths, dVdT=s[SUM_DVDT] / opt.n_paths)
 
 
 def paths(surface, opt, path_begin: int, m: int, n_threads: Optional[int] = None, lib=None,

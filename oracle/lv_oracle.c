@@ -44,6 +44,11 @@
  *     increment). Under ORC_SCHEME_X a spot at or below 0 is below the grid.
  *   - Payoff kink: the indicator 1{phi (S_N - K) > 0}, so a tie gives 0.
  *   - Vega is d price / d sigma_ij per unit of sigma.
+ *   - Rho is d price / d r; d price / d T is the maturity sensitivity with
+ *     the number of steps fixed (dt = T / N, t_n = n T / N) and the grid
+ *     fixed in time, so sigma_n moves with t_n through d sigma / d t. Both
+ *     come from the same reverse sweep: the derivative of the discount plus
+ *     the sum over steps of xbar_{n+1} times d x_{n+1} / d r (or d T).
  *
  * Parity pins (tests/test_oracle_*.py): Philox against cuRAND's host
  * generator; normal moments and a KS test; Black-Scholes price, delta and
@@ -170,9 +175,11 @@ static void orc_sigma_in_cell(const orc_surface* sf, double S, double t, int32_t
 
     int32_t j = 0;
     double v = 0.0;
+    int t_inside = 0;
     if (J > 1) {
         j = orc_cell(sf->time, J, t);
         v = orc_clamp01((t - sf->time[j]) / (sf->time[j + 1] - sf->time[j]));
+        t_inside = t >= sf->time[0] && t < sf->time[J - 1];
     }
     /* sigma_ij lives at sig[i * J + j] */
     double s00 = sf->sigma[i * J + j];
@@ -193,6 +200,12 @@ static void orc_sigma_in_cell(const orc_surface* sf, double S, double t, int32_t
         p->dsigma_dS = ((1.0 - v) * (s10 - s00) + v * (s11 - s01)) * du_dS;
     else
         p->dsigma_dS = 0.0;
+    /* d sigma / d t at fixed S: the time slope of the cell (right derivative at
+     * a time node; the grid is flat in t outside [t_0, t_{J-1})) */
+    if (t_inside)
+        p->dsigma_dt = ((1.0 - u) * (s01 - s00) + u * (s11 - s10)) / (sf->time[j + 1] - sf->time[j]);
+    else
+        p->dsigma_dt = 0.0;
 }
 
 void orc_sigma_eval(const orc_surface* sf, double S, double t, orc_point* p)
@@ -215,6 +228,8 @@ typedef struct {
     double xbar0;   /* d V / d x_0 */
     double SN;      /* terminal spot */
     double vtot;    /* sum over buckets of this path's sigma adjoints */
+    double rho;     /* d V / d r */
+    double dvdt;    /* d V / d T */
     int kink;       /* |S_N - K| within the kink band */
 } orc_path_result;
 
@@ -311,6 +326,8 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     res->kink = (kink_tol > 0.0) && (fabs(SN - op->K) <= kink_tol * SN);
     res->xbar0 = 0.0;
     res->vtot = 0.0;
+    res->rho = 0.0;
+    res->dvdt = 0.0;
     if (!want_greeks) return;
 
     /* reverse sweep over the stored trajectory (back-propagation, Sec. IV-C) */
@@ -319,6 +336,9 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     /* xbar = d V / d x_n: x = ln S, or S under ORC_SCHEME_X */
     double xbar = in_money ? disc * (double)op->phi * (on_x ? 1.0 : SN) : 0.0;
     double vtot = 0.0;
+    /* the discount's share: d e^{-rT} / d r = -T e^{-rT}, d e^{-rT} / d T = -r e^{-rT} */
+    double rho = -op->T * res->V;
+    double dvdt = -op->r * res->V;
     for (int32_t n = N - 1; n >= 0; --n) {
         double t = (double)n * dt;
         double S = on_x ? x[n] : exp(x[n]);
@@ -335,6 +355,18 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
             if (res->kink) kink_vega[nodes[c]] += fabs(contrib);
             vtot += contrib;
         }
+        /* explicit dependence of x_{n+1} on r and on T (through dt = T / N and
+         * t_n = n T / N); xbar is still xbar_{n+1} here */
+        double dx_dr, dx_ddt;
+        if (on_x) {
+            dx_dr = x[n] * dt;
+            dx_ddt = op->r * x[n] + pt.sigma * x[n] * z[n] / (2.0 * sqdt);
+        } else {
+            dx_dr = dt;
+            dx_ddt = (op->r - 0.5 * pt.sigma * pt.sigma) + pt.sigma * z[n] / (2.0 * sqdt);
+        }
+        rho += xbar * dx_dr;
+        dvdt += xbar * (dx_ddt / (double)N + h * pt.dsigma_dt * (double)n / (double)N);
         /* d x_{n+1} / d x_n: 1 + h S d sigma/d S on ln S (d sigma/d x = S d sigma/d S);
          * 1 + r dt + sigma sqrt(dt) Z + h d sigma/d S on S */
         if (on_x)
@@ -345,6 +377,8 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     /* d V / d ln S0 in both cases (= S0 d V / d S0) */
     res->xbar0 = on_x ? xbar * op->S0 : xbar;
     res->vtot = vtot;
+    res->rho = rho;
+    res->dvdt = dvdt;
 }
 
 /* ----------------------------------------------------------- path ranges */
@@ -386,6 +420,10 @@ static void* orc_job_run(void* arg)
         out[ORC_SUM_VTOT] += res.vtot;
         out[ORC_SUM_VTOT_2] += res.vtot * res.vtot;
         out[ORC_SUM_SN] += res.SN;
+        out[ORC_SUM_RHO] += res.rho;
+        out[ORC_SUM_RHO_2] += res.rho * res.rho;
+        out[ORC_SUM_DVDT] += res.dvdt;
+        out[ORC_SUM_DVDT_2] += res.dvdt * res.dvdt;
         if (res.kink) {
             out[ORC_KINK_COUNT] += 1.0;
             out[ORC_KINK_XBAR0] += fabs(res.xbar0);

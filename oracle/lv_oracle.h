@@ -26,7 +26,11 @@ enum {
     ORC_SUM_SN = 6,       /* sum of terminal spots */
     ORC_KINK_COUNT = 7,   /* paths with |S_N - K| <= kink_tol * S_N */
     ORC_KINK_XBAR0 = 8,   /* sum of |d V / d x_0| over those paths */
-    ORC_NSCAL = 9
+    ORC_SUM_RHO = 9,      /* sum of d V / d r (pathwise, discount included) */
+    ORC_SUM_RHO_2 = 10,
+    ORC_SUM_DVDT = 11,    /* sum of d V / d T (maturity, n_steps fixed, surface fixed in time) */
+    ORC_SUM_DVDT_2 = 12,
+    ORC_NSCAL = 13
 };
 
 /* Interpolation in spot between the nodes of a cell (Sec. IV-D reads as
@@ -60,6 +64,7 @@ typedef struct {
     double w[4];          /* node weights (i,j), (i+1,j), (i,j+1), (i+1,j+1) */
     double sigma;
     double dsigma_dS;
+    double dsigma_dt;     /* 0 outside [t_0, t_{J-1}) and for one time node */
 } orc_point;
 
 /* Decisions taken from outside for listed paths / steps (see lv_oracle.c):

@@ -416,8 +416,71 @@ def pin_adjoint_vs_bump_readings(lib):
         assert abs(res[1] - dfd) < 2e-6 * max(1.0, abs(dfd))
 
 
+# ------------------------------------------------------ rho and d V / d T
+
+def pin_black_scholes_rho_dvdt(lib):
+    """Flat sigma (log-Euler is exact in law): the pathwise rho and d V / d T
+    equal Black-Scholes' rho and -theta (d V / d T at fixed S0) within 3.5
+    standard errors, for a call and a put."""
+    from scipy.stats import norm
+    sig, r, T, S0, K = 0.22, 0.04, 1.3, 100.0, 104.0
+    surf = W.flat_surface(sig, n_spot=3, n_time=4, s_lo=30.0, s_hi=400.0, t_hi=2.0)
+    d1 = (math.log(S0 / K) + (r + 0.5 * sig * sig) * T) / (sig * math.sqrt(T))
+    d2 = d1 - sig * math.sqrt(T)
+    for phi in (1, -1):
+        opt = W.Option(S0=S0, r=r, K=K, T=T, n_steps=16, n_paths=1 << 16, seed=31, phi=phi)
+        s = oracle.run_sums(surf, opt, lib=lib)
+        P = opt.n_paths
+        rho = phi * K * T * math.exp(-r * T) * norm.cdf(phi * d2)
+        dvdt = S0 * norm.pdf(d1) * sig / (2 * math.sqrt(T)) + phi * r * K * math.exp(-r * T) * norm.cdf(phi * d2)
+        assert abs(s[oracle.SUM_RHO] / P - rho) < 3.5 * se_of(s[oracle.SUM_RHO], s[oracle.SUM_RHO_2], P), phi
+        assert abs(s[oracle.SUM_DVDT] / P - dvdt) < 3.5 * se_of(s[oracle.SUM_DVDT], s[oracle.SUM_DVDT_2], P), phi
+
+
+def pin_rho_dvdt_vs_bump(lib):
+    """Pathwise rho and d V / d T equal central differences of the oracle's
+    own price in r and in T (same normals, n_steps fixed) to O(eps^2), on a
+    grid that varies in time, where no path and no step time sits within the
+    bump of a payoff, cell or time-node kink."""
+    surf = W.random_surface(9, 4, 3, s_lo=86, s_hi=116, t_hi=0.9)
+    for scheme in (oracle.SCHEME_LOG, oracle.SCHEME_X):
+        opt = W.Option(S0=100.0, r=0.02, K=101.0, T=0.7, n_steps=5, n_paths=64, seed=14, phi=1, scheme=scheme)
+        xN, _, _ = oracle.paths(surf, opt, 0, opt.n_paths, lib=lib)
+        assert np.min(np.abs(np.exp(xN) - opt.K)) > 1e-3
+        tn = np.arange(opt.n_steps) * opt.T / opt.n_steps
+        assert np.min(np.abs(tn[:, None] - surf.time[None, :])[1:]) > 1e-4   # t_0 = 0 sits on a node in both bumps
+        s = oracle.run_sums(surf, opt, lib=lib)
+        P = opt.n_paths
+
+        def price(**kw):
+            o = W.Option(**{**opt.__dict__, **kw})
+            return oracle.run_sums(surf, o, greeks=False, lib=lib)[oracle.SUM_V] / P
+
+        e = 1e-6
+        rho_fd = (price(r=opt.r + e / 2) - price(r=opt.r - e / 2)) / e
+        dvdt_fd = (price(T=opt.T + e / 2) - price(T=opt.T - e / 2)) / e
+        assert abs(s[oracle.SUM_RHO] / P - rho_fd) < 2e-6 * max(1.0, abs(rho_fd)), (scheme, s[oracle.SUM_RHO] / P, rho_fd)
+        assert abs(s[oracle.SUM_DVDT] / P - dvdt_fd) < 2e-6 * max(1.0, abs(dvdt_fd)), (scheme, s[oracle.SUM_DVDT] / P, dvdt_fd)
+
+
+def pin_rho_dvdt_vs_autograd(lib):
+    """Pathwise rho and d V / d T against torch.autograd of the independent
+    restatement with r and T as inputs, on the tiny grids of the adjoint pins
+    under every reading."""
+    cases = [_case(c) for c in ADJOINT_CASES] + [(n, s, o) for n, s, o in _model_cases()]
+    for name, surf, opt in cases:
+        Z = np.stack([oracle.normals(opt.seed, p, opt.n_steps, lib=lib) for p in range(opt.n_paths)])
+        ref = torch_lv.autograd_all(surf.spot, surf.time, surf.sigma, opt.S0, opt.r, opt.K, opt.T, opt.n_steps,
+                                    opt.phi, Z, interp=getattr(surf, "interp", 0), scheme=opt.scheme)
+        s = oracle.run_sums(surf, opt, lib=lib)
+        P = opt.n_paths
+        assert abs(s[oracle.SUM_RHO] / P - ref["rho"]) <= 1e-10 * max(1.0, abs(ref["rho"])), (name, ref["rho"])
+        assert abs(s[oracle.SUM_DVDT] / P - ref["dVdT"]) <= 1e-10 * max(1.0, abs(ref["dVdT"])), (name, ref["dVdT"])
+
+
 ALL_PINS = [pin_philox_curand, pin_normals_from_curand_words, pin_uniform_exact, pin_normal_law,
             pin_black_scholes, pin_flat_closed_form_paths, pin_martingale, pin_put_call_parity,
             pin_adjoint_vs_autograd, pin_adjoint_vs_bump, pin_bilinear,
             pin_flat_closed_form_paths_euler_x, pin_martingale_euler_x, pin_log_interpolation,
-            pin_adjoint_vs_autograd_readings, pin_adjoint_vs_bump_readings]
+            pin_adjoint_vs_autograd_readings, pin_adjoint_vs_bump_readings,
+            pin_black_scholes_rho_dvdt, pin_rho_dvdt_vs_bump, pin_rho_dvdt_vs_autograd]

@@ -50,6 +50,10 @@ MUTANTS = {
     "Euler on X: adjoint drops r dt": ("xbar * (1.0 + op->r * dt + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS)",
                                        "xbar * (1.0 + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS)"),
     "Euler on X: dx/dsigma drops the spot": ("double h = on_x ? x[n] * sqdt * z[n]", "double h = on_x ? sqdt * z[n]"),
+    "rho drops the discount's share": ("double rho = -op->T * res->V;", "double rho = 0.0;"),
+    "d V / d T: step time factor off by one": ("h * pt.dsigma_dt * (double)n / (double)N",
+                                               "h * pt.dsigma_dt * (double)(n + 1) / (double)N"),
+    "d V / d T: drift term sign": ("dx_ddt = (op->r - 0.5 * pt.sigma * pt.sigma)", "dx_ddt = (op->r + 0.5 * pt.sigma * pt.sigma)"),
 }
 
 

@@ -6,8 +6,6 @@ oracle's hand-written reverse sweep (back-propagation, Sec. IV-C of arXiv
 It shares no code with the oracle; the only thing it takes from the oracle
 is the array of normals (pinned on its own against cuRAND).
 """
-import math
-
 import torch
 
 
@@ -22,7 +20,10 @@ def forward_price(spot, time, sigma, S0, r, K, T, n_steps, phi, Z, interp=0, sch
     [0, 1] (flat outside the grid)."""
     I, J = spot.shape[0], time.shape[0]
     P = Z.shape[0]
+    r = torch.as_tensor(r, dtype=torch.float64)
+    T = torch.as_tensor(T, dtype=torch.float64)
     dt = T / n_steps
+    sqdt = torch.sqrt(dt)
     state = (torch.log(S0) if scheme == 0 else S0) * torch.ones(P, dtype=torch.float64)
     for n in range(n_steps):
         t = n * dt
@@ -34,20 +35,23 @@ def forward_price(spot, time, sigma, S0, r, K, T, n_steps, phi, Z, interp=0, sch
             u = torch.clamp((torch.log(S) - torch.log(spot[i])) / (torch.log(spot[i + 1]) - torch.log(spot[i])),
                             0.0, 1.0)
         if J > 1:
-            tt = torch.tensor([t], dtype=torch.float64)
+            tt = t.detach().reshape(1)
             j = int(torch.clamp(torch.searchsorted(time, tt, right=True) - 1, 0, J - 2).item())
-            v = min(max((t - float(time[j])) / float(time[j + 1] - time[j]), 0.0), 1.0)
+            if float(tt) >= float(time[J - 1]):
+                v = torch.tensor(1.0, dtype=torch.float64)      # flat in t beyond the last node
+            else:
+                v = torch.clamp((t - time[j]) / (time[j + 1] - time[j]), 0.0, 1.0)
             lo = sigma[i, j] * (1 - u) + sigma[i + 1, j] * u
             hi = sigma[i, j + 1] * (1 - u) + sigma[i + 1, j + 1] * u
             sig = lo * (1 - v) + hi * v
         else:
             sig = sigma[i, 0] * (1 - u) + sigma[i + 1, 0] * u
         if scheme == 0:
-            state = state + (r - 0.5 * sig * sig) * dt + sig * math.sqrt(dt) * Z[:, n]
+            state = state + (r - 0.5 * sig * sig) * dt + sig * sqdt * Z[:, n]
         else:
-            state = state + r * state * dt + sig * state * math.sqrt(dt) * Z[:, n]
+            state = state + r * state * dt + sig * state * sqdt * Z[:, n]
     SN = torch.exp(state) if scheme == 0 else state
-    V = math.exp(-r * T) * torch.relu(phi * (SN - K))
+    V = torch.exp(-r * T) * torch.relu(phi * (SN - K))
     return V.mean(), SN
 
 
@@ -61,3 +65,20 @@ def autograd_greeks(spot, time, sigma, S0, r, K, T, n_steps, phi, Z, interp=0, s
     price, SN = forward_price(sp, tm, sg, s0, r, K, T, n_steps, phi, z, interp, scheme)
     d_s0, d_sig = torch.autograd.grad(price, [s0, sg])
     return float(price.detach()), float(d_s0), d_sig.numpy(), SN.detach().numpy()
+
+
+def autograd_all(spot, time, sigma, S0, r, K, T, n_steps, phi, Z, interp=0, scheme=0):
+    """Price and its derivatives in S0, every sigma_ij, r and T (n_steps
+    fixed) by torch.autograd, all FP64, as a dict."""
+    sp = torch.tensor(spot, dtype=torch.float64)
+    tm = torch.tensor(time, dtype=torch.float64)
+    sg = torch.tensor(sigma, dtype=torch.float64, requires_grad=True)
+    s0 = torch.tensor(float(S0), dtype=torch.float64, requires_grad=True)
+    rt = torch.tensor(float(r), dtype=torch.float64, requires_grad=True)
+    Tt = torch.tensor(float(T), dtype=torch.float64, requires_grad=True)
+    z = torch.tensor(Z, dtype=torch.float64)
+    price, _ = forward_price(sp, tm, sg, s0, rt, K, Tt, n_steps, phi, z, interp, scheme)
+    d_s0, d_sig, d_r, d_T = torch.autograd.grad(price, [s0, sg, rt, Tt])
+    return dict(price=float(price.detach()), delta=float(d_s0), vega=d_sig.numpy(), rho=float(d_r),
+                dVdT=float(d_T))
+
