@@ -231,6 +231,18 @@ def other_workloads(lib, dev, ev0, ev1):
                                 (lv.LV_INTERP_LOGS, lv.LV_SCHEME_S, "Euler on S, weight in ln S")):
         single(f"reading: {tag}, 30x60, 156 steps, 2^20 paths", *W.config_paper_shape(), interp=interp,
                scheme=scheme)
+    # price, delta, vegas, rho and d price / d T in one reverse sweep
+    S = lv.Surface.from_workload(W.config_paper_shape()[0], lib)
+    S.set_stream(stream.cuda_stream)
+    S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+    _, o = W.config_paper_shape()
+    d = torch.zeros(5 + S.IJ, dtype=torch.float64, device=dev)
+    ms = time_call(lambda: S.price_greeks_ext_device(o.S0, 0.01, o.K, o.T, o.n_steps, o.n_paths, o.seed,
+                                                      d.data_ptr()), ev0, ev1)
+    res["with rho and dV/dT (lv_price_greeks_ext), 30x60, 156 steps, 2^20 paths"] = {
+        "adjoint_kernel_ms": ms, "path_steps_per_s": o.n_paths * o.n_steps / (ms * 1e-3),
+        "launch": list(S.get_launch(o.n_steps, True))}
+    S.close()
     # the tangent-ratio form of the adjoint (two forward passes, no checkpoints)
     single("tangent-ratio adjoint, 30x60, 156 steps, 2^20 paths", *W.config_paper_shape(),
            method=lv.LV_ADJ_TANGENT)

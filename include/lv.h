@@ -201,6 +201,25 @@ lv_status lv_price_greeks(lv_surface_t h, double S0, double r, double K, double 
 lv_status lv_price_greeks_device(lv_surface_t h, double S0, double r, double K, double T,
                                  int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out);
 
+/* Price, delta and vegas (as lv_price_greeks) plus rho = d price / d r and
+ * d price / d T, the maturity sensitivity with n_steps fixed (dt = T / N,
+ * t_n = n T / N) and the grid fixed in time (Sec. III's pathwise adjoint
+ * applied to the two scalar inputs: the derivative of the discount plus
+ * sum_n xbar_{n+1} d x_{n+1} / d r (or d T), accumulated in the same reverse
+ * sweep). Runs the checkpointed reverse sweep with binary64 level 2 and
+ * k = 4 or 8, whatever the handle's adjoint method, accumulation and k say.
+ * Host outputs like lv_price_greeks, then out_rho and out_dVdT. */
+lv_status lv_price_greeks_ext(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                              int64_t n_paths, uint64_t seed, double* out_price, double* out_delta,
+                              double* out_vega, double* out_rho, double* out_dVdT);
+
+/* Same, to d_out (device, caller-owned) laid out [5 + n_spot * n_time]:
+ * LV_OUT_PRICE, LV_OUT_DELTA, LV_OUT_STDERR, the vegas from LV_OUT_VEGA,
+ * then rho at 3 + n_spot * n_time and d price / d T at 4 + n_spot * n_time;
+ * enqueued on the handle's stream without synchronising. */
+lv_status lv_price_greeks_ext_device(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                                     int64_t n_paths, uint64_t seed, double* d_out);
+
 /* Raw sums over paths [path_begin, path_end) with a given stream_id
  * (< 65536): [3 + n_spot * n_time] doubles, layout LV_SUM_*, written to
  * device memory d_sums owned by the caller, without synchronising. This is

@@ -185,8 +185,10 @@ std::string adjoint_tune_key(const lv_surface_s* h, int32_t n_steps)
 // blocks the register budget allows; larger grids are read through L1.
 constexpr size_t kGridSmemLimit = 44 * 1024;
 
+// extra: the adjoint kernel that also sums d V / d r and d V / d T (reverse
+// sweep, binary64 level 2, k = 4 or 8).
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
-                        bool dbg = false, bool* grid_smem = nullptr)
+                        bool dbg = false, bool* grid_smem = nullptr, bool extra = false)
 {
     *block = h->cfg_block ? h->cfg_block : 128;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
@@ -200,25 +202,27 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
     }
     if (dbg) *k = 4;
     const int model = (h->interp == LV_INTERP_LOGS ? 1 : 0) | (h->scheme == LV_SCHEME_S ? 2 : 0);
-    if (model != 0 && *k > lv::kModelMaxK) *k = lv::kModelMaxK;
-    const bool gs = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, true) <= kGridSmemLimit;
+    if ((model != 0 || extra) && *k > lv::kModelMaxK) *k = lv::kModelMaxK;
+    const bool gs = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, true, extra) <= kGridSmemLimit;
     if (grid_smem) *grid_smem = gs;
-    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, gs);
+    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, gs, extra);
     if (smem > 200 * 1024)
         return fail(LV_EINVAL, "time table does not fit in shared memory (" + std::to_string(smem) + " bytes)");
     int occ = 0;
-    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, dbg ? 0 : h->acc_mode, dbg, gs, dbg ? 0 : h->adj_method, model,
-                             smem, &occ));
+    const int acc = dbg || extra ? 0 : h->acc_mode;
+    const int method = dbg || extra ? LV_ADJ_REVERSE : h->adj_method;
+    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, acc, dbg, gs, method, model, extra, smem, &occ));
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
     *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
     return LV_OK;
 }
 
-lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, bool dbg, Plan* p)
+lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, bool dbg, Plan* p,
+                    bool extra = false)
 {
-    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem);
+    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem, extra);
     if (st != LV_OK) return st;
-    p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem);
+    p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem, extra);
     const int warps = p->block / 32;
     const int64_t tiles = (n_paths + lv::paths_per_tile(greeks) - 1) / lv::paths_per_tile(greeks);   // claimed by warps
     p->n_tiles = (int)tiles;
@@ -227,10 +231,11 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     p->grid = (int)(want_blocks < slots ? want_blocks : slots);
     if (p->grid < 1) p->grid = 1;
     // the tangent-ratio adjoint keeps no checkpoints
-    const bool reverse = dbg || h->adj_method == LV_ADJ_REVERSE;
+    const bool reverse = dbg || extra || h->adj_method == LV_ADJ_REVERSE;
     p->n_ck = greeks && reverse ? (n_steps + p->k - 1) / p->k : 0;
     const size_t nIJ = (size_t)h->Je * h->I;
-    p->row_words = greeks ? 3 + (int)nIJ : 3;             // price-only rows hold the scalars
+    // price-only rows hold the scalars; extra rows end with the sums of d V / d r and d V / d T
+    p->row_words = greeks ? 3 + (int)nIJ + (extra ? 2 : 0) : 3;
     p->n_chunks = lv::finalize_chunks(p->grid);
     const size_t total_warps = (size_t)p->grid * warps;
     size_t o = 0;
@@ -238,7 +243,7 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     p->off_part = o;    o = round_up(o + sizeof(double) * (size_t)p->grid * p->row_words, 256);
     p->off_chunks = o;  o = round_up(o + sizeof(double) * (size_t)p->n_chunks * p->row_words, 256);
     p->off_wrows = o;                   // per-warp rows: Kahan mode only
-    if (greeks && h->acc_mode == LV_ACC_KAHAN) o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
+    if (greeks && !extra && h->acc_mode == LV_ACC_KAHAN) o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
     p->off_l1 = o;      if (greeks) o = round_up(o + sizeof(float) * (size_t)p->grid * nIJ, 256);
     p->off_ckpt = o;
     o = round_up(o + sizeof(float) * (size_t)p->n_ck * total_warps * lv::ring_slots_per_warp(), 256);
@@ -283,6 +288,8 @@ struct McCall {
     unsigned long long* dbg_ev_count = nullptr;
     int64_t dbg_ev_cap = 0;
     double dbg_band = 0.0;
+    // set after brace initialisation, never positionally
+    bool extra = false;      // also d V / d r and d V / d T (after the vegas)
 };
 
 lv::McParams base_params(const lv_surface_s* h, const McCall& c)
@@ -308,6 +315,10 @@ lv::McParams base_params(const lv_surface_s* h, const McCall& c)
     P.rdt = (float)(on_s ? c.r * dt : log2e * c.r * dt);
     P.S0f = (float)c.S0;
     P.inv_S0 = (float)(1.0 / c.S0);
+    P.Tf = (float)c.T;
+    P.r_nat = (float)c.r;
+    P.inv_N = (float)(1.0 / c.n_steps);
+    P.half_inv_sqdt = (float)(0.5 / std::sqrt(dt));
     P.hdt = (float)(log2e * 0.5 * dt);
     P.sqdt2 = (float)(log2e * std::sqrt(dt));
     P.dt = (float)dt;
@@ -329,6 +340,7 @@ lv::McParams base_params(const lv_surface_s* h, const McCall& c)
 
 lv_status run_mc(lv_surface_s* h, const McCall& c)
 {
+    if (!c.d_out) return fail(LV_EINTERNAL, "no output buffer for the call");
     lv_status st = check_option(c.S0, c.r, c.K, c.T, c.n_steps);
     if (st != LV_OK) return st;
     if (c.n_paths < 1) return fail(LV_EINVAL, "the path range is empty");
@@ -337,7 +349,7 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     if (c.stream_id >= 65536u) return fail(LV_EINVAL, "stream_id must be < 65536");
     if (c.n_paths > 0x7fffffffLL) return fail(LV_EINVAL, "one call handles at most 2^31 - 1 paths");
     Plan p;
-    st = make_plan(h, c.n_steps, c.n_paths, c.greeks, c.dbg_xN != nullptr, &p);
+    st = make_plan(h, c.n_steps, c.n_paths, c.greeks, c.dbg_xN != nullptr, &p, c.extra);
     if (st != LV_OK) return st;
     st = ensure_scratch(h, p.total);
     if (st != LV_OK) return st;
@@ -360,7 +372,11 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     P.dbg_ev_count = c.dbg_ev_count;
     P.dbg_ev_cap = c.dbg_ev_cap;
     P.dbg_band = (float)c.dbg_band;
-    if (c.greeks && !c.dbg_xN && h->adj_method == LV_ADJ_TANGENT) {
+    if (c.extra) {                        // reverse sweep, binary64 level 2
+        P.extra = 1;
+        P.acc_mode = 0;
+    }
+    if (c.greeks && !c.dbg_xN && !c.extra && h->adj_method == LV_ADJ_TANGENT) {
         P.method = LV_ADJ_TANGENT;
         P.flag = P.tile_counter + 1;      // in the zeroed counter section; the finalize resets it
     }
@@ -380,13 +396,14 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     F.out = c.d_out;
     F.tile_counter = P.tile_counter;
     F.flag = P.flag;
+    F.extra = c.extra ? 1 : 0;
     LV_CUDA(lv::launch_finalize(F, h->stream));
     return LV_OK;
 }
 
-lv_status fetch_result(lv_surface_s* h)
+lv_status fetch_result(lv_surface_s* h, bool extra = false)
 {
-    const size_t n = 3 + (size_t)h->I * h->J;
+    const size_t n = 3 + (size_t)h->I * h->J + (extra ? 2 : 0);
     LV_CUDA(cudaMemcpyAsync(h->h_res, h->d_res, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     LV_CUDA(cudaStreamSynchronize(h->stream));
     return LV_OK;
@@ -452,7 +469,7 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
     if (e != cudaSuccess) return bail(LV_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
 
     const size_t nsig = (size_t)h->Je * (h->I - 1);
-    const size_t nres = 3 + (size_t)n_spot * n_time;
+    const size_t nres = 5 + (size_t)n_spot * n_time;      // room for the extended layout
     if (cudaMalloc(&h->d_sig, sizeof(float2) * nsig) != cudaSuccess ||
         cudaMalloc(&h->d_node, sizeof(float) * n_spot) != cudaSuccess ||
         cudaMalloc(&h->d_ab, sizeof(float2) * n_spot) != cudaSuccess ||
@@ -649,6 +666,39 @@ lv_status lv_price_greeks(lv_surface_t h, double S0, double r, double K, double 
     if (std::isnan(h->h_res[LV_OUT_PRICE]))
         return fail(LV_ENUMERIC, "a factor 1 + g_n vanished on a live path: use LV_ADJ_REVERSE for this grid");
     return LV_OK;
+}
+
+lv_status lv_price_greeks_ext(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                              int64_t n_paths, uint64_t seed, double* out_price, double* out_delta,
+                              double* out_vega, double* out_rho, double* out_dVdT)
+{
+    if (!h || !out_price || !out_delta || !out_vega || !out_rho || !out_dVdT) return fail(LV_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, h->d_res};
+    c.extra = true;
+    lv_status st = run_mc(h, c);
+    if (st != LV_OK) return st;
+    st = fetch_result(h, true);
+    if (st != LV_OK) return st;
+    const size_t IJ = (size_t)h->I * h->J;
+    *out_price = h->h_res[LV_OUT_PRICE];
+    *out_delta = h->h_res[LV_OUT_DELTA];
+    std::memcpy(out_vega, h->h_res + LV_OUT_VEGA, sizeof(double) * IJ);
+    *out_rho = h->h_res[3 + IJ];
+    *out_dVdT = h->h_res[4 + IJ];
+    return LV_OK;
+}
+
+lv_status lv_price_greeks_ext_device(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                                     int64_t n_paths, uint64_t seed, double* d_out)
+{
+    if (!h || !d_out) return fail(LV_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, d_out};
+    c.extra = true;
+    return run_mc(h, c);
 }
 
 lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, double K, double T,

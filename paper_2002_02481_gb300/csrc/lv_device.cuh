@@ -109,12 +109,29 @@ __device__ __forceinline__ int4 step_time(const McParams& P, int n)
     return make_int4(j * (P.I - 1), (j + 1) * (P.I - 1), j * P.I, __float_as_int((float)v));
 }
 
+// Time slope factor of step n for d price / d T: (n / N) / (tau_{j+1} - tau_j)
+// with the cell of step_time while t_n lies in [tau_0, tau_{J-1}) (the grid is
+// flat in t outside, and with one time node), else 0; decided in binary64.
+__device__ __forceinline__ float step_tdt(const McParams& P, int n)
+{
+    const double t = (double)n * P.dt_d;
+    if (P.J < 2 || t < P.tau[0] || t >= P.tau[P.J - 1]) return 0.0f;
+    int lo = 0, hi = P.J - 2;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.tau[mid] <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return (float)(((double)n / (double)P.N) / (P.tau[lo + 1] - P.tau[lo]));
+}
+
 // Shared-memory view of the grid for one block.
 struct SmemGrid {
     const int4* tab;       // [N] per step: (j (I-1), (j+1) (I-1), j I, bits of v)
     const float2* sig2;    // [Je][I-1]: (sigma_{i,j}, sigma_{i+1,j} - sigma_{i,j})
     const float* node;     // [I]
     const float2* ab;      // [I - 1]
+    const float* tdt;      // [N] step_tdt (kernels that compute d price / d T)
 };
 
 // Spot cell: the largest i <= I-2 with s_i <= S. On log-uniform grids the
@@ -151,6 +168,7 @@ struct StepEval {
     float u;       // clamped spot weight
     int i;         // spot cell
     float sslope;  // S d sigma / d S = d sigma / d ln S (0 outside the grid)
+    float dsig_t;  // sigma(S, tau_{j+1}) - sigma(S, tau_j) at the step's spot
 };
 
 // Bilinear sigma at (S_n, t_n), Sec. IV-D, from the path state x; the
@@ -179,6 +197,7 @@ __device__ __forceinline__ StepEval eval_sigma(const McParams& P, const SmemGrid
     const float top = fmaf(e.u, lo.y, lo.x);
     const float bot = fmaf(e.u, hi.y, hi.x);
     e.sigma = fmaf(v, bot - top, top);
+    e.dsig_t = bot - top;
     if (WANT_SLOPE) {
         const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
         const float d = fmaf(v, hi.y - lo.y, lo.y) * ab.x;     // d sigma / d (S or y)
@@ -221,6 +240,26 @@ __device__ __forceinline__ void adjoint_factors(const McParams& P, const StepEva
     } else {
         h = fmaf(P.sqdt, z, -e.sigma * P.dt);
         g = h * e.sslope;
+    }
+}
+
+// Explicit dependence of x_{n+1} on r and on the maturity T (n_steps fixed:
+// dt = T / N, t_n = n T / N, the grid fixed in time), in the adjoint's units:
+// on ln S, d x / d r = dt and d x / d T = ((r - sigma^2/2) + sigma Z / (2
+// sqrt(dt))) / N + h d sigma / d t (n / N); on S the same with S_n (r dt) and
+// S_n (r + sigma Z / (2 sqrt(dt))), over S0 like h.
+template <int MODEL>
+__device__ __forceinline__ void extra_factors(const McParams& P, const StepEval& e, float z, float h, float tdt,
+                                              float& ar, float& at)
+{
+    const float ttime = h * e.dsig_t * tdt;
+    if (MODEL & kModelEulerS) {
+        const float s = e.S * P.inv_S0;
+        ar = s * P.dt;
+        at = fmaf(s * fmaf(e.sigma * z, P.half_inv_sqdt, P.r_nat), P.inv_N, ttime);
+    } else {
+        ar = P.dt;
+        at = fmaf(fmaf(e.sigma * z, P.half_inv_sqdt, fmaf(-0.5f * e.sigma, e.sigma, P.r_nat)), P.inv_N, ttime);
     }
 }
 
@@ -354,9 +393,10 @@ __device__ __forceinline__ void path_counter(const McParams& P, long long rel, u
 // (i+1, j+1) with the bilinear weights. Corner sums are kept in registers
 // while the cell is unchanged and then added to the block's binary32 buckets
 // `l1` (time-major, row j * I) with red.global.add.f32. Returns d V / d x_0.
-template <int KCK, int MODEL = 0>
+template <int KCK, int MODEL = 0, bool EXTRA = false>
 __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
-                                              const float* ck, size_t cks, float xbar, float* l1)
+                                              const float* ck, size_t cks, float xbar, float* l1,
+                                              float* rho_acc = nullptr, float* t_acc = nullptr)
 {
     const int nseg = (P.N + KCK - 1) / KCK;
     int cur = -1;
@@ -367,6 +407,7 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
         float x = x_next;
         if (m > 0) x_next = ck[(size_t)(m - 1) * cks];    // in flight during this segment
         float hq[KCK], gq[KCK], uq[KCK];
+        float aq[EXTRA ? KCK : 1], tq[EXTRA ? KCK : 1];
         int iq[KCK];
 #pragma unroll
         for (int q = 0; q < KCK; ++q) {
@@ -376,6 +417,7 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
                 const int4 tb = g.tab[n];
                 const StepEval ev = eval_sigma<true, MODEL>(P, g, x, tb);
                 adjoint_factors<MODEL>(P, ev, z[q & 3], hq[q], gq[q]);
+                if (EXTRA) extra_factors<MODEL>(P, ev, z[q & 3], hq[q], g.tdt[n], aq[EXTRA ? q : 0], tq[EXTRA ? q : 0]);
                 uq[q] = ev.u;
                 iq[q] = ev.i;
                 x = step_state<MODEL>(P, x, ev.sigma, z[q & 3]);
@@ -389,6 +431,10 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
                 const int key = tb.z + iq[q];
                 const float v = __int_as_float(tb.w);
                 const float sbar = xbar * hq[q];
+                if (EXTRA) {                             // xbar is still xbar_{n+1}
+                    *rho_acc = fmaf(xbar, aq[EXTRA ? q : 0], *rho_acc);
+                    *t_acc = fmaf(xbar, tq[EXTRA ? q : 0], *t_acc);
+                }
                 xbar = fmaf(xbar, gq[q], xbar);
                 if (key != cur) {
                     if (cur >= 0) {

@@ -32,6 +32,7 @@ struct McParams {
     // option and scheme; the path state is y = log2 S (or S when the model
     // runs the Euler scheme on S)
     int model;             // bit 0: spot weight linear in ln S; bit 1: Euler scheme on S
+    int extra;             // adjoint also sums d V / d r and d V / d T (rows end with them)
     float x0;              // log2 S0 (S0 on S)
     float rdt;             // log2(e) r dt (r dt on S)
     float hdt;             // log2(e) dt / 2
@@ -41,6 +42,8 @@ struct McParams {
     float K;
     float disc;            // e^{-rT}
     float S0f, inv_S0;     // S0, 1 / S0 (the scaled adjoint of the scheme on S)
+    float Tf, r_nat;       // T, r (d price / d r and d price / d T)
+    float inv_N, half_inv_sqdt;   // 1 / N, 1 / (2 sqrt(dt))
     float phi;             // +1 call, -1 put
     double dt_d;           // dt in binary64 for the time table
     int N;                 // steps
@@ -85,6 +88,7 @@ struct FinalizeParams {
     long long n_paths;
     double S0;
     int want_sums;         // 1: raw sums, 0: price / delta / stderr / vega
+    int extra;             // rows end with the sums of d V / d r and d V / d T
     double* chunks;        // [finalize_chunks(G)][row_words] stage-1 sums
     double* out;           // [3 + I * J]
     unsigned int* tile_counter;  // reset to 0
@@ -115,7 +119,7 @@ cudaError_t launch_bump_finalize(const double* partials, int G, int row_words, d
                                  long long n_paths, double eps, double eps_S, double* out,
                                  unsigned int* tile_counter, cudaStream_t s);
 
-size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem);
+size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra = false);
 
 // Launchers; return cudaSuccess or the launch error. An adjoint launch with
 // p.dbg_xN != null runs the logging instantiation with k = 4 and binary64
@@ -124,7 +128,7 @@ cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks
                       cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
 cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, int model,
-                         size_t smem, int* blocks_per_sm);
+                         bool extra, size_t smem, int* blocks_per_sm);
 
 // The kernels of the other models (lv_model1.cu .. lv_model3.cu, one
 // translation unit each so that they compile in parallel); they exist for
@@ -133,7 +137,7 @@ cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool 
     cudaError_t launch_mc_model##N(const McParams& p, int grid, int block, int k, bool greeks, size_t smem, \
                                    cudaStream_t s);                                                        \
     cudaError_t mc_occupancy_model##N(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem,    \
-                                      int method, size_t smem, int* blocks_per_sm);
+                                      int method, bool extra, size_t smem, int* blocks_per_sm);
 LV_DECLARE_MODEL(1)
 LV_DECLARE_MODEL(2)
 LV_DECLARE_MODEL(3)

@@ -28,8 +28,10 @@ __global__ void reduce_rows_kernel(const double* __restrict__ partials, int G, i
 
 // Level 3, stage 2: chunks summed in order; outputs in the ABI layout
 // (vega spot-major), price statistics from the scalar sums.
+// With `extra` the last two columns of the rows are the sums of d V / d r and
+// d V / d T, written after the vegas (out[3 + I J], out[4 + I J]).
 __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks, int row_words,
-                                int I, int J, long long n_paths, double S0, int want_sums,
+                                int I, int J, long long n_paths, double S0, int want_sums, int extra,
                                 double* __restrict__ out, unsigned int* tile_counter, unsigned int* flag)
 {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,6 +56,10 @@ __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks,
         if (col == 0 && flag) *flag = 0u;
         return;
     }
+    if (extra && col >= row_words - 2) {
+        out[3 + I * J + (col - (row_words - 2))] = want_sums ? s : s / P;
+        return;
+    }
     const int e = col - 3;             // time-major bucket j * I + i
     const int j = e / I, i = e - j * I;
     if (j >= J) return;                // padding row of a one-column grid
@@ -62,9 +68,9 @@ __global__ void finalize_kernel(const double* __restrict__ chunks, int n_chunks,
 
 }  // namespace
 
-size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem)
+size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra)
 {
-    return smem_layout(I, Je, N, block, greeks, grid_smem).total;
+    return smem_layout(I, Je, N, block, greeks, grid_smem, extra).total;
 }
 
 int ring_slots_per_warp() { return kRing * kTile; }
@@ -83,13 +89,13 @@ cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks
 }
 
 cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, int model,
-                         size_t smem, int* bps)
+                         bool extra, size_t smem, int* bps)
 {
     switch (model) {
-    case 0: return occupancy_model_impl<0>(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
-    case 1: return mc_occupancy_model1(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
-    case 2: return mc_occupancy_model2(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
-    case 3: return mc_occupancy_model3(block, k, greeks, acc, dbg, grid_smem, method, smem, bps);
+    case 0: return occupancy_model_impl<0>(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
+    case 1: return mc_occupancy_model1(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
+    case 2: return mc_occupancy_model2(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
+    case 3: return mc_occupancy_model3(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -102,7 +108,7 @@ cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     finalize_kernel<<<(f.row_words + 255) / 256, 256, 0, s>>>(f.chunks, n_chunks, f.row_words, f.I, f.J,
-                                                              f.n_paths, f.S0, f.want_sums, f.out,
+                                                              f.n_paths, f.S0, f.want_sums, f.extra, f.out,
                                                               f.tile_counter, f.flag);
     return cudaGetLastError();
 }

@@ -65,10 +65,13 @@ struct AccSlot {
 };
 
 struct SmemLayout {
-    size_t tab, sig, node, ab, qslot, qrel, qxb, acc, red, total;
+    size_t tab, sig, node, ab, tdt, qslot, qrel, qxb, acc, red, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks, bool grid_smem)
+// extra: the adjoint kernel that also sums d V / d r and d V / d T (the time
+// slope table and two more accumulators per thread).
+__host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks, bool grid_smem,
+                                                  bool extra = false)
 {
     const int W = block / 32;
     SmemLayout L;
@@ -77,10 +80,11 @@ __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int bloc
     L.sig = o;   if (grid_smem) o += align16(sizeof(float2) * (size_t)Je * (I - 1));
     L.node = o;  o += align16(sizeof(float) * (size_t)I);
     L.ab = o;    o += align16(sizeof(float2) * (size_t)I);
+    L.tdt = o;   if (extra) o += align16(sizeof(float) * (size_t)N);
     L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
     L.qrel = o;  if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
     L.qxb = o;   if (greeks) o += align16(sizeof(float) * (size_t)W * kQueue);
-    L.acc = o;   o += align16(sizeof(AccSlot) * 3 * (size_t)block);
+    L.acc = o;   o += align16(sizeof(AccSlot) * (extra ? 5 : 3) * (size_t)block);
     L.red = o;   o += align16(sizeof(double) * 3 * kMaxWarps);
     L.total = o;
     return L;
@@ -109,7 +113,7 @@ __device__ __forceinline__ double acc_value(const AccSlot& a)
 // Stages the time table, the spot nodes, the cell coefficients and (when GS)
 // the sigma pairs in shared memory; large grids are read from global memory
 // through L1 instead, which leaves room for more resident blocks.
-template <bool GS>
+template <bool GS, bool EXTRA = false>
 __device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* smem, const SmemLayout& L)
 {
     const int B = blockDim.x, tid = threadIdx.x;
@@ -122,10 +126,14 @@ __device__ __forceinline__ void stage_grid(const McParams& P, unsigned char* sme
     for (int e = tid; e < P.I; e += B) s_node[e] = P.node[e];
     for (int e = tid; e < P.I - 1; e += B) s_ab[e] = P.ab[e];
     for (int n = tid; n < P.N; n += B) s_tab[n] = step_time(P, n);
+    if (EXTRA) {
+        float* s_tdt = reinterpret_cast<float*>(smem + L.tdt);
+        for (int n = tid; n < P.N; n += B) s_tdt[n] = step_tdt(P, n);
+    }
 }
 
 // Block sum of three per-thread binary64 values into row[0..2] (fixed order).
-__device__ __forceinline__ void block_scalars(double a, double b, double c, double* s_red, double* row)
+__device__ __forceinline__ void block_scalars(double a, double b, double c, double* s_red, double* row, int n = 3)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -149,7 +157,7 @@ __device__ __forceinline__ void block_scalars(double a, double b, double c, doub
         }
         row[0] = sa;
         row[1] = sb;
-        row[2] = sc;
+        if (n > 2) row[2] = sc;
     }
 }
 
@@ -181,14 +189,14 @@ __device__ __forceinline__ void drain_buckets(float* l1, int nIJ, double* wrow)
     }
 }
 
-template <int KCK, int ACC, bool DBG, bool GS, int MODEL>
+template <int KCK, int ACC, bool DBG, bool GS, int MODEL, bool EXTRA = false>
 __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__ McParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = blockDim.x, W = B >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
-    stage_grid<GS>(P, smem, L);
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS, EXTRA);
+    stage_grid<GS, EXTRA>(P, smem, L);
     float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);    // this block's level-1 buckets
     int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQueue;
     int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
@@ -212,12 +220,14 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
 
     const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
                       GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
-                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
+                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab),
+                      reinterpret_cast<const float*>(smem + L.tdt) };
     const size_t cks = (size_t)gridDim.x * W * kRing * kTile;   // checkpoint stride
     float* const ckw = P.ckpt + (size_t)wid * kRing * kTile;     // this warp's slots
 
     AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
     acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
+    if (EXTRA) acc[3 * B] = acc[4 * B] = AccSlot{0.0, 0.0f, 0.0f};    // d V / d r, d V / d T
     int q_head = 0, q_count = 0, batches = 0;
     unsigned fwd_count = 0;
     int tile = claim_tile(P.tile_counter);
@@ -236,8 +246,13 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 float xbar = q_xb[e];
                 uint32_t c1, c2;
                 path_counter(P, rel, c1, c2);
-                xbar = reverse_path<KCK, MODEL>(P, g, c1, c2, ckw + slot, cks, xbar, l1);
+                float ra = 0.0f, ta = 0.0f;
+                xbar = reverse_path<KCK, MODEL, EXTRA>(P, g, c1, c2, ckw + slot, cks, xbar, l1, &ra, &ta);
                 acc_add<ACC>(acc[2 * B], xbar);
+                if (EXTRA) {
+                    acc_add<ACC>(acc[3 * B], ra);
+                    acc_add<ACC>(acc[4 * B], ta);
+                }
                 if (DBG) P.dbg_xbar0[rel] = xbar;
             }
             q_head = (q_head + nb) & (kQueue - 1);
@@ -261,6 +276,10 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
             payoff<MODEL>(P, x, V, xbarN);
             acc_add<ACC>(acc[0], V);
             acc_add<ACC>(acc[B], V * V);
+            if (EXTRA) {                       // the discount's share: -T V and -r V
+                acc_add<ACC>(acc[3 * B], -P.Tf * V);
+                acc_add<ACC>(acc[4 * B], -P.r_nat * V);
+            }
             if (DBG) {
                 P.dbg_xN[rel] = ln_spot<MODEL>(x);
                 P.dbg_V[rel] = V;
@@ -298,6 +317,10 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
         }
     }
     block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
+    if (EXTRA) {
+        __syncthreads();                       // s_red is reused
+        block_scalars(acc_value<ACC>(acc[3 * B]), acc_value<ACC>(acc[4 * B]), 0.0, s_red, row + 3 + nIJ, 2);
+    }
 }
 
 // Tangent-ratio adjoint (LV_ADJ_TANGENT): persistent and warp-centric like
@@ -467,8 +490,15 @@ cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
 // Calls f(kernel, flag) with the instantiation for (greeks, k, acc, dbg, gs)
 // of model MODEL: k in {4, 8, 16, 32} for model 0, {4, 8} for the others.
 template <int MODEL, bool GS, typename F>
-cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, F&& f)
+cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, bool extra, F&& f)
 {
+    if (extra) {           // d V / d r and d V / d T: reverse sweep, binary64 level 2, k = 4 or 8
+        static bool ce[2] = {};
+        if (!greeks || dbg || method != LV_ADJ_REVERSE || acc != 0) return cudaErrorInvalidValue;
+        if (k == 4) return f(adjoint_kernel<4, 0, false, GS, MODEL, true>, ce[0]);
+        if (k == 8) return f(adjoint_kernel<8, 0, false, GS, MODEL, true>, ce[1]);
+        return cudaErrorInvalidValue;
+    }
     if (!greeks) {
         static bool c0 = false, c1 = false;
         return acc ? f(price_kernel<1, GS, MODEL>, c1) : f(price_kernel<0, GS, MODEL>, c0);
@@ -510,17 +540,17 @@ cudaError_t launch_model_impl(const McParams& p, int grid, int block, int k, boo
         return launch_configured(kernel, configured, p, grid, block, smem, s);
     };
     const bool dbg = p.dbg_xN != nullptr;
-    return p.grid_smem ? with_kernel_gs<MODEL, true>(greeks, k, p.acc_mode, dbg, p.method, run)
-                       : with_kernel_gs<MODEL, false>(greeks, k, p.acc_mode, dbg, p.method, run);
+    return p.grid_smem ? with_kernel_gs<MODEL, true>(greeks, k, p.acc_mode, dbg, p.method, p.extra != 0, run)
+                       : with_kernel_gs<MODEL, false>(greeks, k, p.acc_mode, dbg, p.method, p.extra != 0, run);
 }
 
 template <int MODEL>
-cudaError_t occupancy_model_impl(int block, int k, bool greeks, int acc, bool dbg, bool gs, int method, size_t smem,
-                                 int* bps)
+cudaError_t occupancy_model_impl(int block, int k, bool greeks, int acc, bool dbg, bool gs, int method, bool extra,
+                                 size_t smem, int* bps)
 {
     auto occ = [&](auto kernel, bool&) { return occupancy(kernel, block, smem, bps); };
-    return gs ? with_kernel_gs<MODEL, true>(greeks, k, acc, dbg, method, occ)
-              : with_kernel_gs<MODEL, false>(greeks, k, acc, dbg, method, occ);
+    return gs ? with_kernel_gs<MODEL, true>(greeks, k, acc, dbg, method, extra, occ)
+              : with_kernel_gs<MODEL, false>(greeks, k, acc, dbg, method, extra, occ);
 }
 
 }  // namespace

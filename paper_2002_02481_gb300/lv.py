@@ -80,6 +80,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_price": [vp, d, d, d, d, i32, i64, u64, dp, dp],
         "lv_price_greeks": [vp, d, d, d, d, i32, i64, u64, dp, dp, dp],
         "lv_price_greeks_device": [vp, d, d, d, d, i32, i64, u64, vp],
+        "lv_price_greeks_ext": [vp, d, d, d, d, i32, i64, u64, dp, dp, dp, dp, dp],
+        "lv_price_greeks_ext_device": [vp, d, d, d, d, i32, i64, u64, vp],
         "lv_price_greeks_sums_device": [vp, d, d, d, d, i32, i64, i64, u64, u32, vp],
         "lv_finalize_sums_device": [vp, vp, i64, d, vp],
         "lv_debug_paths": [vp, d, d, d, d, i32, u64, i64, i64, fp, fp, fp, d, i64,
@@ -215,6 +217,20 @@ class Surface:
         _check(self.lib, self.lib.lv_price_greeks(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
                                                   ctypes.byref(p), ctypes.byref(d), _dp(vega)), "lv_price_greeks")
         return p.value, d.value, vega.reshape(self.n_spot, self.n_time)
+
+    def price_greeks_ext(self, S0, r, K, T, n_steps, n_paths, seed):
+        """(price, delta, vega [I, J], rho, d price / d T)."""
+        p, d, rho, dvdt = (ctypes.c_double() for _ in range(4))
+        vega = np.zeros(self.IJ, dtype=np.float64)
+        _check(self.lib, self.lib.lv_price_greeks_ext(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
+                                                      ctypes.byref(p), ctypes.byref(d), _dp(vega),
+                                                      ctypes.byref(rho), ctypes.byref(dvdt)), "lv_price_greeks_ext")
+        return p.value, d.value, vega.reshape(self.n_spot, self.n_time), rho.value, dvdt.value
+
+    def price_greeks_ext_device(self, S0, r, K, T, n_steps, n_paths, seed, d_out_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_price_greeks_ext_device(self.h, S0, r, K, T, int(n_steps), int(n_paths),
+                                                             int(seed), ctypes.c_void_p(d_out_ptr)),
+               "lv_price_greeks_ext_device")
 
     def price_greeks_device(self, S0, r, K, T, n_steps, n_paths, seed, d_out_ptr: int) -> None:
         _check(self.lib, self.lib.lv_price_greeks_device(self.h, S0, r, K, T, int(n_steps), int(n_paths),
