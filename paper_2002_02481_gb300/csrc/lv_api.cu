@@ -738,7 +738,7 @@ lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32
             McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, h->d_res};
             if (run_mc(h, c) != LV_OK) continue;             // warm-up (and scratch growth)
             float t = 1e30f;
-            for (int rep = 0; rep < 2; ++rep) {
+            for (int rep = 0; rep < 3; ++rep) {          // best of three
                 cudaEventRecord(e0, h->stream);
                 if (run_mc(h, c) != LV_OK) break;
                 cudaEventRecord(e1, h->stream);
