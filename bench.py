@@ -336,8 +336,6 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
 
     step_ms, kern_ms = [], []
-    s0 = torch.cuda.Event(enable_timing=True)
-    s1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(lr) as clk:
         # the sampler reads every 200 ms: keep the GPU loaded for 0.6 s first so that
         # samples land on the same kind of load as the timed region that follows
@@ -345,15 +343,25 @@ def run_ours(args):
         while time.perf_counter() < t_end:
             step()
             torch.cuda.synchronize(dev)
-        for _ in range(args.steps):
-            flush.fill_(1)
-            s0.record(stream)
-            step()
-            s1.record(stream)
-            s1.synchronize()
-            step_ms.append(s0.elapsed_time(s1))
-            kern_ms.append(ev0.elapsed_time(ev1))
+        # the steps are queued without a host wait between them, so the host is
+        # ahead of the device and every s0 -> s1 interval is device work only
+        # (one event pair per step for the step and one for the adjoint kernel)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+        for e in evs:
+            for x in e:
+                x.record(stream)
         torch.cuda.synchronize(dev)
+        for e in evs:
+            flush.fill_(1)
+            e[0].record(stream)
+            S.set_kernel_events(e[2].cuda_event, e[3].cuda_event)
+            step()
+            e[1].record(stream)
+        torch.cuda.synchronize(dev)
+        for e in evs:
+            step_ms.append(e[0].elapsed_time(e[1]))
+            kern_ms.append(e[2].elapsed_time(e[3]))
+        S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
     total_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -435,7 +443,7 @@ def run_ours(args):
                        "launch": {"block": tuned[0], "k": tuned[1], "source": "lv_tune"},
                        "l2": "256 MB buffer rewritten between timed steps (outside the timed region)",
                        "parallelism": f"path-range shards x{ws}"},
-            "clocks": clocks, "gpu_launches": 3 * args.steps, "roofline": roofline,
+            "clocks": clocks, "gpu_launches": 2 * args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e,
             "forward_only": {"kernel_ms": statistics.mean(fwd_ms),
                              "value": P * opt.n_steps / (statistics.mean(fwd_ms) * 1e-3), "unit": "path-steps/s"},

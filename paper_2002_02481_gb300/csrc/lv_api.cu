@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lv.h"
@@ -70,11 +71,18 @@ void lv::tune_cache_append(const std::string& key, const int vals[3], double ms)
 
 std::string lv::gpu_name(int device)
 {
+    // the property query costs tens of microseconds: once per device
+    static std::mutex mu;
+    static std::map<int, std::string> names;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto it = names.find(device);
+    if (it != names.end()) return it->second;
     cudaDeviceProp prop{};
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return "unknown";
     std::string n(prop.name);
     for (char& ch : n)
         if (ch == ' ') ch = '_';
+    names[device] = n;
     return n;
 }
 
@@ -187,12 +195,34 @@ constexpr size_t kGridSmemLimit = 44 * 1024;
 
 // extra: the adjoint kernel that also sums d V / d r and d V / d T (reverse
 // sweep, binary64 level 2, k = 4 or 8).
+// Blocks per SM of one kernel instantiation and launch shape, per device:
+// the runtime's occupancy query costs microseconds, so each answer is kept.
+using OccKey = std::tuple<int, int, int, bool, int, bool, bool, int, int, bool, size_t>;
+std::mutex g_occ_mu;
+std::map<OccKey, int> g_occ;
+
+bool occ_lookup(const OccKey& key, int* occ)
+{
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    const auto it = g_occ.find(key);
+    if (it == g_occ.end()) return false;
+    *occ = it->second;
+    return true;
+}
+
+void occ_store(const OccKey& key, int occ)
+{
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    g_occ[key] = occ;
+}
+
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
                         bool dbg = false, bool* grid_smem = nullptr, bool extra = false)
 {
     *block = h->cfg_block ? h->cfg_block : 128;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
-    if (greeks && !dbg && !h->cfg_block && !h->cfg_k) {
+    const char* cache = std::getenv("LV_TUNE_CACHE");
+    if (greeks && !dbg && !h->cfg_block && !h->cfg_k && cache && *cache) {
         int v[3];
         if (lv::tune_cache_lookup(adjoint_tune_key(h, n_steps), v) && v[0] >= 32 && v[0] <= 128 &&
             v[0] % 32 == 0 && (v[1] == 4 || v[1] == 8 || v[1] == 16 || v[1] == 32)) {
@@ -211,7 +241,11 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
     int occ = 0;
     const int acc = dbg || extra ? 0 : h->acc_mode;
     const int method = dbg || extra ? LV_ADJ_REVERSE : h->adj_method;
-    LV_CUDA(lv::mc_occupancy(*block, *k, greeks, acc, dbg, gs, method, model, extra, smem, &occ));
+    const OccKey key{h->device, *block, *k, greeks, acc, dbg, gs, method, model, extra, smem};
+    if (!occ_lookup(key, &occ)) {
+        LV_CUDA(lv::mc_occupancy(*block, *k, greeks, acc, dbg, gs, method, model, extra, smem, &occ));
+        occ_store(key, occ);
+    }
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
     *bps = h->cfg_bps ? (h->cfg_bps < occ ? h->cfg_bps : occ) : occ;
     return LV_OK;
@@ -543,7 +577,14 @@ lv_status lv_set_option_type(lv_surface_t h, int32_t phi)
 lv_status lv_set_stream(lv_surface_t h, void* cuda_stream)
 {
     if (!h) return fail(LV_EINVAL, "handle is NULL");
-    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (s != h->stream) {
+        // the scratch and the staging buffers may still be in use on the old stream
+        DeviceGuard g(h->device);
+        if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+        LV_CUDA(cudaStreamSynchronize(h->stream));
+        h->stream = s;
+    }
     return LV_OK;
 }
 
