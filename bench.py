@@ -443,7 +443,7 @@ def run_ours(args):
                        "launch": {"block": tuned[0], "k": tuned[1], "source": "lv_tune"},
                        "l2": "256 MB buffer rewritten between timed steps (outside the timed region)",
                        "parallelism": f"path-range shards x{ws}"},
-            "clocks": clocks, "gpu_launches": 2 * args.steps, "roofline": roofline,
+            "clocks": clocks, "gpu_launches": 3 * args.steps, "roofline": roofline,
             "cpu_baseline": cpu, "e2e": e2e,
             "forward_only": {"kernel_ms": statistics.mean(fwd_ms),
                              "value": P * opt.n_steps / (statistics.mean(fwd_ms) * 1e-3), "unit": "path-steps/s"},
