@@ -61,7 +61,8 @@ typedef enum {
     LV_ECUDA = 3,       /* a CUDA runtime call failed (message in lv_last_error) */
     LV_EINTERNAL = 4,   /* a consistency check inside the library failed */
     LV_ENUMERIC = 5     /* the tangent-ratio adjoint met a vanishing factor 1 + g_n (see
-                           lv_set_adjoint_method); the outputs are NaN */
+                           lv_set_adjoint_method); host outputs are left untouched, device
+                           outputs of the call are NaN */
 } lv_status;
 
 /* Level-2 (per-block, across path tiles) accumulation of the payoffs and of
@@ -78,8 +79,9 @@ enum { LV_ACC_FP64 = 0, LV_ACC_KAHAN = 1 };
  *    x_bar_0 = x_bar_N D_N; a second forward pass over the paths with
  *    x_bar_N != 0 spreads sigma_bar_n = x_bar_N D_N h_n / D_{n+1}. No
  *    checkpoints, no reverse order. When some |1 + g_n| falls below 2^-20 the
- *    ratio loses what the reverse sweep keeps: every output of the call is
- *    then NaN and the host-side entry points return LV_ENUMERIC.
+ *    ratio loses what the reverse sweep keeps: every device output of the
+ *    call is then NaN, and the host-output entry points return LV_ENUMERIC
+ *    without writing their outputs.
  * g_n = h_n S_n d sigma / d S and h_n = sqrt(dt) Z_n - sigma_n dt. */
 enum { LV_ADJ_REVERSE = 0, LV_ADJ_TANGENT = 1 };
 

@@ -701,11 +701,11 @@ lv_status lv_price_greeks(lv_surface_t h, double S0, double r, double K, double 
     if (st != LV_OK) return st;
     st = fetch_result(h);
     if (st != LV_OK) return st;
+    if (std::isnan(h->h_res[LV_OUT_PRICE]))    // outputs left untouched, like every failure
+        return fail(LV_ENUMERIC, "a factor 1 + g_n vanished on a live path: use LV_ADJ_REVERSE for this grid");
     *out_price = h->h_res[LV_OUT_PRICE];
     *out_delta = h->h_res[LV_OUT_DELTA];
     std::memcpy(out_vega, h->h_res + LV_OUT_VEGA, sizeof(double) * (size_t)h->I * h->J);
-    if (std::isnan(h->h_res[LV_OUT_PRICE]))
-        return fail(LV_ENUMERIC, "a factor 1 + g_n vanished on a live path: use LV_ADJ_REVERSE for this grid");
     return LV_OK;
 }
 
