@@ -431,10 +431,26 @@ def run_ours(args):
         import oracle
         threads = oracle.default_threads()
         sample = 1 << 13
-        cpu_s = time_oracle(surf, opt, sample, threads)
+        o_s = W.Option(**{**opt.__dict__, "n_paths": sample})
+        t0 = time.perf_counter()
+        ref = oracle.price_greeks(surf, o_s, n_threads=threads)
+        cpu_s = time.perf_counter() - t0
         cpu = {"value": sample * opt.n_steps / cpu_s, "unit": "path-steps/s", "cores": threads,
                "kind": "oracle", "sample": f"first {sample} of the 2^20 paths, 156 steps, "
                                            f"price+delta+1800 vegas ({cpu_model()})"}
+        # accuracy of the adjoint and of the bump baseline against the FP64 oracle's
+        # pathwise estimator on the same paths (same counters)
+        vmax = float(np.max(np.abs(ref["vega"])))
+
+        def errors(p_, d_, v_):
+            return {"price_rel": abs(p_ - ref["price"]) / abs(ref["price"]),
+                    "delta_rel": abs(d_ - ref["delta"]) / abs(ref["delta"]),
+                    "vega_max_abs_of_max": float(np.max(np.abs(v_ - ref["vega"]))) / vmax}
+        accuracy = {"sample": f"first {sample} of the 2^20 paths", "reference": "FP64 oracle, pathwise adjoint",
+                    "adjoint": errors(*S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sample, opt.seed))}
+        if not args.no_bump:
+            accuracy["bump_eps_1e-4"] = errors(*S.bump_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sample,
+                                                              opt.seed, 1e-4))
         line = {
             "metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -444,7 +460,7 @@ def run_ours(args):
                        "l2": "256 MB buffer rewritten between timed steps (outside the timed region)",
                        "parallelism": f"path-range shards x{ws}"},
             "clocks": clocks, "gpu_launches": 3 * args.steps, "roofline": roofline,
-            "cpu_baseline": cpu, "e2e": e2e,
+            "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e,
             "forward_only": {"kernel_ms": statistics.mean(fwd_ms),
                              "value": P * opt.n_steps / (statistics.mean(fwd_ms) * 1e-3), "unit": "path-steps/s"},
             "bump_reprice": bump,
