@@ -137,7 +137,9 @@ lv_status lv_surface_set_sigma(lv_surface_t h, const double* sigma);
 lv_status lv_set_option_type(lv_surface_t h, int32_t phi);
 
 /* CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
- * that later calls enqueue on; NULL selects the legacy default stream. */
+ * that later calls enqueue on; NULL selects the legacy default stream. A
+ * change of stream first waits for the work already enqueued on the old one
+ * (the handle's scratch and staging buffers are shared by its calls). */
 lv_status lv_set_stream(lv_surface_t h, void* cuda_stream);
 
 /* LV_ACC_FP64 (default) or LV_ACC_KAHAN. */
