@@ -105,6 +105,24 @@ def test_launch_shape_invariance(launch, lib):
     assert np.max(np.abs(v1 - v0)) <= 1e-6 * np.max(np.abs(v0))
 
 
+def test_more_than_1024_level2_rows(lib):
+    """One-warp blocks on 2^16 paths give more than 1,024 level-2 rows, so the
+    level-3 finalize sums its chunks in several groups of 32."""
+    import torch
+    surf, opt = W.config_small()
+    opt.n_paths = 1 << 16
+    base = G.make_surface(surf, opt, lib)
+    p0, d0, v0 = base.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    alt = G.make_surface(surf, opt, lib, launch=(32, 4, 0))
+    block, _, bps = alt.get_launch(opt.n_steps, True)
+    rows = min(opt.n_paths // 32, bps * torch.cuda.get_device_properties(0).multi_processor_count)
+    assert block == 32 and rows > 1024, (block, bps, rows)
+    p1, d1, v1 = alt.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert abs(p1 - p0) <= 1e-12 * abs(p0)
+    assert abs(d1 - d0) <= 1e-9 * abs(d0)
+    assert np.max(np.abs(v1 - v0)) <= 1e-6 * np.max(np.abs(v0))
+
+
 def test_path_range_sharding(lib):
     """Sums over [0, P/3), [P/3, P) add up to the sums over [0, P): the
     path-range split a multi-GPU run would use."""
