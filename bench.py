@@ -506,6 +506,44 @@ def precision_study():
     return 0
 
 
+def path_sweep():
+    """Adjoint kernel time and path-steps/s on the 30x60 / 156-step workload
+    for 2^16 ... 2^24 paths at the bench's launch shape: how the end-of-kernel
+    tail amortises. Prints one JSON line."""
+    import torch
+
+    from paper_2002_02481_gb300 import lv
+
+    lib = lv.load()
+    surf, opt = W.config_paper_shape()
+    S = lv.Surface.from_workload(surf, lib)
+    stream = torch.cuda.current_stream()
+    S.set_stream(stream.cuda_stream)
+    S.set_launch(128, 4, 0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+    d = torch.zeros(3 + S.IJ, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    out = {"study": "path sweep", "workload": "30x60 grid, 156 steps", "launch": [128, 4], "points": []}
+    for lg in range(16, 25):
+        P = 1 << lg
+        ts = []
+        for rep in range(6):
+            flush.fill_(1)
+            S.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed, d.data_ptr())
+            ev1.synchronize()
+            if rep:
+                ts.append(ev0.elapsed_time(ev1))
+        ms = statistics.median(ts)
+        out["points"].append({"paths": P, "kernel_ms": ms, "path_steps_per_s": P * opt.n_steps / (ms * 1e-3)})
+    S.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -516,11 +554,15 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--precision-study", action="store_true",
                     help="2^24-path precision workloads: binary64 vs Kahan level 2 against the FP64 oracle")
+    ap.add_argument("--path-sweep", action="store_true",
+                    help="adjoint kernel throughput for 2^16 ... 2^24 paths on the bench workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.precision_study:
         return precision_study()
+    if args.path_sweep:
+        return path_sweep()
     return run_ours(args)
 
 
