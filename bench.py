@@ -254,7 +254,7 @@ def other_workloads(lib, dev, ev0, ev1):
         for acc, nm in ((0, "binary64"), (1, "Kahan")):
             single(f"precision {which} grid, 156 steps, 2^24 paths, level 2 {nm}", surf, opt, acc=acc)
     surf, opt = W.config_large()
-    for k in (8, 32):
+    for k in (4, 32):
         single(f"large 100x100, 1260 steps, 2^26 paths, k={k}", surf, opt, launch=(128, k, 0))
     # the book: 8 grids x 64 options, one persistent launch, graph replay
     handles = [lv.Surface.from_workload(sf, lib) for sf in W.book_surfaces()]

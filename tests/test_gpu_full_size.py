@@ -9,7 +9,7 @@ x_bar_N, so the deltas and the vegas obey
 
 and the prices price_call - price_put = price_(K=0) - e^{-rT} K, up to the
 rounding of the sums. Run at the sizes and launch shapes bench.py times:
-the 100x100 grid with 1,260 steps and 2^26 paths at k = 8, and the 30x60
+the 100x100 grid with 1,260 steps and 2^26 paths at k = 4, and the 30x60
 grid with 156 steps and 2^20 paths at the default shape. The oracle cannot
 run these sizes; the per-path parity tests cover the arithmetic itself."""
 import math
@@ -43,12 +43,12 @@ def _three(lib, surf, opt, launch):
     return out
 
 
-@pytest.mark.parametrize("config", ["large 100x100, 1260 steps, 2^26 paths, k=8",
+@pytest.mark.parametrize("config", ["large 100x100, 1260 steps, 2^26 paths, k=4",
                                     "paper shape 30x60, 156 steps, 2^20 paths"])
 def test_pathwise_put_call_parity_at_full_size(config, lib):
     if config.startswith("large"):
         surf, opt = W.config_large()
-        launch = (128, 8, 0)
+        launch = (128, 4, 0)
     else:
         surf, opt = W.config_paper_shape()
         launch = None
