@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(32) finalize_kernel(const double* __restrict__
             const double mean = s / P;
             const double var = n_paths > 1 ? (sv2 / P - mean * mean) * P / (P - 1.0) : 0.0;
             out[LV_OUT_PRICE_DEV] = mean;
-            out[LV_OUT_STDERR_DEV] = var > 0.0 ? sqrt(var / P) : 0.0;
+            out[LV_OUT_STDERR_DEV] = (var > 0.0 || var != var) ? sqrt(var / P) : 0.0;   // NaN stays NaN
         } else if (col == 2) {
             out[LV_OUT_DELTA_DEV] = s / (P * S0);
         }

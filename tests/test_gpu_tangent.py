@@ -106,3 +106,39 @@ def test_rejects_an_unknown_method(lib):
     with pytest.raises(lv.LVError):
         s.set_adjoint_method(2)
     s.close()
+
+
+def test_vanishing_factor_is_flagged(lib):
+    """On a fine grid with sigma drawn i.i.d. per node, S d sigma / d S reaches
+    ~25, so 1 + g_n = 1 + h_n S d sigma / d S comes within 2^-20 of zero on
+    some live paths among 2^20: the tangent-ratio form must refuse (NaN device
+    outputs, LV_ENUMERIC with the host outputs untouched), the reverse sweep
+    on the same paths must not, and the next tangent call on a benign grid
+    must succeed (the flag is reset)."""
+    import ctypes
+
+    import torch
+    surf = W.random_surface(22, 128, 128, s_lo=40.0, s_hi=250.0, t_hi=1.5)
+    opt = W.Option(S0=100.0, r=0.0, K=95.0, T=1.5, n_steps=64, n_paths=1 << 20, seed=22)
+    gs = G.make_surface(surf, opt, lib, method=T)
+    n = 3 + gs.IJ
+    d = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gs.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, d.data_ptr())
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(d.cpu().numpy()))
+    price, delta = ctypes.c_double(-7.0), ctypes.c_double(-7.0)
+    vega = np.full(gs.IJ, -7.0)
+    st = lib.lv_price_greeks(gs.h, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed,
+                             ctypes.byref(price), ctypes.byref(delta),
+                             vega.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert st == lv.LV_ENUMERIC
+    assert price.value == -7.0 and delta.value == -7.0 and np.all(vega == -7.0)
+    gs.set_adjoint_method(lv.LV_ADJ_REVERSE)
+    p, dl, v = gs.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert np.isfinite(p) and np.isfinite(dl) and np.all(np.isfinite(v))
+    gs.close()
+    s2, o2 = W.config_small()
+    g2 = G.make_surface(s2, o2, lib, method=T)
+    p2, d2, v2 = g2.price_greeks(o2.S0, o2.r, o2.K, o2.T, o2.n_steps, o2.n_paths, o2.seed)
+    assert np.isfinite(p2) and np.all(np.isfinite(v2))
+    g2.close()
