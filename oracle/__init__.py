@@ -54,15 +54,26 @@ class _Decisions(ctypes.Structure):
     _fields_ = [("itm_path", ctypes.POINTER(ctypes.c_int64)), ("itm_val", ctypes.POINTER(ctypes.c_int8)),
                 ("n_itm", ctypes.c_int64),
                 ("cell_path", ctypes.POINTER(ctypes.c_int64)), ("cell_step", ctypes.POINTER(ctypes.c_int32)),
-                ("cell_code", ctypes.POINTER(ctypes.c_int32)), ("n_cell", ctypes.c_int64)]
+                ("cell_code", ctypes.POINTER(ctypes.c_int32)), ("n_cell", ctypes.c_int64),
+                ("band", ctypes.c_double), ("out_overrides", ctypes.POINTER(ctypes.c_int64))]
+
+
+class DecisionRefused(RuntimeError):
+    """An imposed decision that rounding of the path could not have produced
+    (status ORC_EDECISION of lv_oracle.c)."""
 
 
 class Decisions:
     """Decisions taken from another implementation (see lv_oracle.c):
     ``itm`` maps path -> payoff indicator; ``cells`` is (paths, steps,
-    codes) with code = 2 * spot_cell + inside_grid."""
+    codes) with code = 2 * spot_cell + inside_grid. A decision that differs
+    from the oracle's own is applied only when the oracle's own value lies
+    within ``band`` (relative) of the strike, of the node between the two
+    cells, or of the grid's edge node; otherwise the call raises
+    DecisionRefused. After a call, ``overrides`` holds how many cell and
+    payoff decisions differed from the oracle's own and were applied."""
 
-    def __init__(self, itm: Optional[dict] = None, cells=None):
+    def __init__(self, itm: Optional[dict] = None, cells=None, band: float = 0.0):
         keys = sorted((itm or {}).keys())
         self.itm_path = np.array(keys, dtype=np.int64)
         self.itm_val = np.array([1 if itm[k] else 0 for k in keys], dtype=np.int8)
@@ -73,12 +84,19 @@ class Decisions:
         self.cell_path = np.ascontiguousarray(cp[order], dtype=np.int64)
         self.cell_step = np.ascontiguousarray(cs[order], dtype=np.int32)
         self.cell_code = np.ascontiguousarray(cc[order], dtype=np.int32)
+        self.band = float(band)
+        self._ov = np.zeros(2, dtype=np.int64)
         P = ctypes.POINTER
         self.c = _Decisions(self.itm_path.ctypes.data_as(P(ctypes.c_int64)),
                             self.itm_val.ctypes.data_as(P(ctypes.c_int8)), len(keys),
                             self.cell_path.ctypes.data_as(P(ctypes.c_int64)),
                             self.cell_step.ctypes.data_as(P(ctypes.c_int32)),
-                            self.cell_code.ctypes.data_as(P(ctypes.c_int32)), len(self.cell_path))
+                            self.cell_code.ctypes.data_as(P(ctypes.c_int32)), len(self.cell_path),
+                            self.band, self._ov.ctypes.data_as(P(ctypes.c_int64)))
+
+    @property
+    def overrides(self) -> dict:
+        return {"cell": int(self._ov[0]), "payoff": int(self._ov[1])}
 
 
 class _Point(ctypes.Structure):
@@ -142,7 +160,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
                               f64p, f64p, f64p]
     lib.orc_paths.restype = ctypes.c_int
     lib.orc_paths_ex.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, P(_Decisions),
-                                 ctypes.c_int32, f64p, f64p, f64p]
+                                 ctypes.c_int32, f64p, f64p, f64p, f64p]
     lib.orc_paths_ex.restype = ctypes.c_int
     lib.orc_bump.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int32, f64p, f64p]
@@ -180,7 +198,12 @@ def _args(surface, opt) -> _Args:
                  opt.seed, opt.phi, opt.stream_id, getattr(surface, "interp", 0), getattr(opt, "scheme", 0))
 
 
+ORC_EDECISION = 5
+
+
 def _check(st: int, what: str) -> None:
+    if st == ORC_EDECISION:
+        raise DecisionRefused(f"oracle {what}: an imposed decision lies outside its band")
     if st != 0:
         raise RuntimeError(f"oracle {what} failed with status {st}")
 
@@ -260,15 +283,18 @@ def price_greeks(surface, opt, n_threads: Optional[int] = None, lib=None) -> dic
 
 
 def paths(surface, opt, path_begin: int, m: int, n_threads: Optional[int] = None, lib=None,
-          decisions: Optional[Decisions] = None):
-    """Per-path x_N, discounted payoff and d V / d x_0 for m paths."""
+          decisions: Optional[Decisions] = None, amp: bool = False):
+    """Per-path x_N, discounted payoff and d V / d x_0 for m paths (and, with
+    ``amp``, each path's bound on d ln |xbar_0| / d e for a relative error e
+    in every spot of the path)."""
     lib = lib or load_library()
     a = _args(surface, opt)
-    xN, V, xb = (np.zeros(m) for _ in range(3))
+    xN, V, xb, am = (np.zeros(m) for _ in range(4))
     _check(lib.orc_paths_ex(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(m),
                             ctypes.byref(decisions.c) if decisions is not None else None,
-                            int(n_threads or default_threads()), _ptr(xN), _ptr(V), _ptr(xb)), "paths")
-    return xN, V, xb
+                            int(n_threads or default_threads()), _ptr(xN), _ptr(V), _ptr(xb),
+                            _ptr(am) if amp else None), "paths")
+    return (xN, V, xb, am) if amp else (xN, V, xb)
 
 
 def bump(surface, opt, eps_sigma: float, eps_S0: float, n_paths: Optional[int] = None,

@@ -230,6 +230,10 @@ typedef struct {
     double vtot;    /* sum over buckets of this path's sigma adjoints */
     double rho;     /* d V / d r */
     double dvdt;    /* d V / d T */
+    double amp;     /* sum over steps of (|g_n| + k_n^2 dt + 2 sqrt(dt) |Z_n k_n|) / |1 + g_n|,
+                       k_n = S_n d sigma / d S, 1 + g_n = d x_{n+1} / d x_n: a bound on how
+                       much a relative error e in every S_n moves ln |xbar_0| (at most amp e
+                       to first order) */
     int kink;       /* |S_N - K| within the kink band */
 } orc_path_result;
 
@@ -238,9 +242,13 @@ typedef struct {
  * cell of a step (with whether S lies inside the grid, which switches
  * d sigma / d S on). A binary32 implementation may decide them differently
  * for a path whose value lies within rounding of the strike or of a node.
- * Parity tests pass that implementation's decisions for exactly those
- * paths and steps (after checking that they sit at the kink), so both sides
- * take the same decisions. Lists are sorted ascending by path (and step). */
+ * Parity tests pass that implementation's decisions for those paths and
+ * steps, so both sides take the same decisions. The oracle checks each one
+ * against its own path: a decision that differs from its own is applied only
+ * when the oracle's own value lies within the stated band of the value that
+ * separates the two choices (the strike; the node between two adjacent
+ * cells; the edge node for the inside-grid flag); any other is refused.
+ * Lists are sorted ascending by path (and step). */
 static int orc_forced_itm(const orc_decisions* d, uint64_t path)
 {
     if (!d || d->n_itm <= 0) return -1;
@@ -278,19 +286,54 @@ static int32_t orc_forced_cell(const orc_decisions* d, int64_t first, int64_t la
     return -1;
 }
 
-static void orc_sigma_decided(const orc_surface* sf, double S, double t, int32_t code, orc_point* p)
+/* Sigma at (S, t) in the cell of `code` (2 i + inside) when code >= 0, else
+ * in the oracle's own cell. An imposed code that differs from the oracle's
+ * own decision at S must be admissible: an adjacent cell, with S within
+ * band * s of the node s between the two cells (the inside flag then agrees:
+ * that node is interior), or the same cell with the other inside flag, with
+ * S within band * s of the grid's edge node s_0 or s_{I-1} that the flag
+ * switches at. Returns ORC_EDECISION otherwise; *overridden says whether the
+ * imposed code differed from the oracle's own. */
+static int orc_sigma_decided(const orc_surface* sf, double S, double t, int32_t code, double band,
+                             orc_point* p, int* overridden)
 {
-    if (code < 0) orc_sigma_eval(sf, S, t, p);
-    else orc_sigma_in_cell(sf, S, t, code >> 1, code & 1, p);
+    *overridden = 0;
+    if (code < 0) {
+        orc_sigma_eval(sf, S, t, p);
+        return ORC_OK;
+    }
+    const int32_t I = sf->n_spot;
+    const int32_t i_f = code >> 1;
+    const int in_f = code & 1;
+    if (i_f > I - 2) return ORC_EDECISION;
+    const int32_t i_o = orc_cell(sf->spot, I, S);
+    const int in_o = (S >= sf->spot[0] && S <= sf->spot[I - 1]);
+    if (i_f != i_o || in_f != in_o) {
+        int ok;
+        if (i_f != i_o) {
+            const double node = sf->spot[i_f > i_o ? i_f : i_o];
+            ok = in_f == in_o && (i_f - i_o == 1 || i_o - i_f == 1) && fabs(S - node) <= band * node;
+        } else {
+            const int near_lo = i_o == 0 && fabs(S - sf->spot[0]) <= band * sf->spot[0];
+            const int near_hi = i_o == I - 2 && fabs(S - sf->spot[I - 1]) <= band * sf->spot[I - 1];
+            ok = near_lo || near_hi;
+        }
+        if (!ok) return ORC_EDECISION;
+        *overridden = 1;
+    }
+    orc_sigma_in_cell(sf, S, t, i_f, in_f, p);
+    return ORC_OK;
 }
 
-/* Simulates one path, and when vega != NULL runs its reverse sweep and adds
+/* Simulates one path, and when want_greeks runs its reverse sweep and adds
  * every sigma adjoint to vega[i * J + j] (and |.| to kink_vega for paths
- * flagged near the payoff kink). */
-static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t path,
-                         orc_workspace* ws, int want_greeks, double kink_tol,
-                         const orc_decisions* dec, double* vega, double* kink_vega,
-                         orc_path_result* res)
+ * flagged near the payoff kink). Imposed decisions are checked as they are
+ * applied (ORC_EDECISION for an inadmissible one); ov[0], ov[1] count the
+ * applied cell and payoff decisions that differed from the oracle's own. */
+static int orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t path,
+                        orc_workspace* ws, int want_greeks, double kink_tol,
+                        const orc_decisions* dec, double* vega, double* kink_vega,
+                        orc_path_result* res, int64_t ov[2])
 {
     const int32_t N = op->n_steps, J = sf->n_time;
     const double dt = op->T / (double)N;
@@ -302,6 +345,8 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     orc_normals(op->seed, op->stream_id, path, N, z);
     int64_t c_first, c_last;
     orc_cell_range(dec, path, &c_first, &c_last);
+    const double band = dec ? dec->band : 0.0;
+    int overridden, st;
 
     /* forward: Euler on the log-spot, or on the spot itself (Sec. IV-A);
      * x holds ln S, or S under ORC_SCHEME_X */
@@ -310,7 +355,9 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     for (int32_t n = 0; n < N; ++n) {
         double t = (double)n * dt;
         double S = on_x ? x[n] : exp(x[n]);
-        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);
+        st = orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), band, &pt, &overridden);
+        if (st != ORC_OK) return st;
+        ov[0] += overridden;
         if (on_x)
             x[n + 1] = x[n] + op->r * x[n] * dt + pt.sigma * x[n] * sqdt * z[n];
         else
@@ -328,21 +375,30 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
     res->vtot = 0.0;
     res->rho = 0.0;
     res->dvdt = 0.0;
-    if (!want_greeks) return;
+    res->amp = 0.0;
+    /* an imposed payoff decision other than the oracle's own: only at the strike */
+    const int forced = orc_forced_itm(dec, path);
+    const int own_itm = itm > 0.0;
+    if (forced >= 0 && forced != own_itm) {
+        if (!(fabs(SN - op->K) <= band * op->K)) return ORC_EDECISION;
+        ov[1] += 1;
+    }
+    if (!want_greeks) return ORC_OK;
 
     /* reverse sweep over the stored trajectory (back-propagation, Sec. IV-C) */
-    const int forced = orc_forced_itm(dec, path);
-    const int in_money = forced >= 0 ? forced : (itm > 0.0);
+    const int in_money = forced >= 0 ? forced : own_itm;
     /* xbar = d V / d x_n: x = ln S, or S under ORC_SCHEME_X */
     double xbar = in_money ? disc * (double)op->phi * (on_x ? 1.0 : SN) : 0.0;
     double vtot = 0.0;
     /* the discount's share: d e^{-rT} / d r = -T e^{-rT}, d e^{-rT} / d T = -r e^{-rT} */
     double rho = -op->T * res->V;
     double dvdt = -op->r * res->V;
+    double amp = 0.0;
     for (int32_t n = N - 1; n >= 0; --n) {
         double t = (double)n * dt;
         double S = on_x ? x[n] : exp(x[n]);
-        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);
+        st = orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), band, &pt, &overridden);
+        if (st != ORC_OK) return st;
         /* d x_{n+1} / d sigma_n */
         double h = on_x ? x[n] * sqdt * z[n] : sqdt * z[n] - pt.sigma * dt;
         double sbar = xbar * h;                     /* adjoint of sigma_n */
@@ -369,16 +425,25 @@ static void orc_one_path(const orc_surface* sf, const orc_option* op, uint64_t p
         dvdt += xbar * (dx_ddt / (double)N + h * pt.dsigma_dt * (double)n / (double)N);
         /* d x_{n+1} / d x_n: 1 + h S d sigma/d S on ln S (d sigma/d x = S d sigma/d S);
          * 1 + r dt + sigma sqrt(dt) Z + h d sigma/d S on S */
+        double factor;
         if (on_x)
-            xbar = xbar * (1.0 + op->r * dt + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS);
+            factor = 1.0 + op->r * dt + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS;
         else
-            xbar = xbar * (1.0 + h * S * pt.dsigma_dS);
+            factor = 1.0 + h * S * pt.dsigma_dS;
+        xbar = xbar * factor;
+        /* sensitivity of ln |factor| to a relative change e of S_n within the cell
+         * (d sigma / d S is constant there): on ln S, d g = (g - k^2 dt) e, with the
+         * ln-S weight -k^2 dt e; on S, 2 sqrt(dt) Z k e; the sum bounds all three */
+        const double kappa = S * pt.dsigma_dS;
+        amp += (fabs(factor - 1.0) + kappa * kappa * dt + 2.0 * sqdt * fabs(z[n] * kappa)) / fabs(factor);
     }
     /* d V / d ln S0 in both cases (= S0 d V / d S0) */
     res->xbar0 = on_x ? xbar * op->S0 : xbar;
     res->vtot = vtot;
     res->rho = rho;
     res->dvdt = dvdt;
+    res->amp = amp;
+    return ORC_OK;
 }
 
 /* ----------------------------------------------------------- path ranges */
@@ -391,6 +456,7 @@ typedef struct {
     double kink_tol;
     const orc_decisions* dec;
     double* out;     /* ORC_NSCAL + 2 I J */
+    int64_t ov[2];   /* applied decisions that differed from the oracle's own */
     int status;
 } orc_job;
 
@@ -409,10 +475,15 @@ static void* orc_job_run(void* arg)
         jb->status = ORC_ENOMEM;
         return NULL;
     }
+    jb->status = ORC_OK;
     for (int64_t p = jb->begin; p < jb->end; ++p) {
         orc_path_result res;
-        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->want_greeks, jb->kink_tol, jb->dec,
-                     vega, kink_vega, &res);
+        const int st = orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->want_greeks, jb->kink_tol, jb->dec,
+                                    vega, kink_vega, &res, jb->ov);
+        if (st != ORC_OK) {
+            jb->status = st;
+            break;
+        }
         out[ORC_SUM_V] += res.V;
         out[ORC_SUM_V2] += res.V * res.V;
         out[ORC_SUM_XBAR0] += res.xbar0;
@@ -431,7 +502,6 @@ static void* orc_job_run(void* arg)
     }
     free(ws.x);
     free(ws.z);
-    jb->status = ORC_OK;
     return NULL;
 }
 
@@ -456,6 +526,9 @@ int orc_run(const orc_surface* sf, const orc_option* op, int64_t path_begin, int
 static int orc_check_decisions(const orc_decisions* d)
 {
     if (!d) return ORC_OK;
+    if (!(d->band >= 0.0)) return ORC_EINVAL;
+    for (int64_t e = 0; e < d->n_cell; ++e)
+        if (d->cell_code[e] < 0 || d->cell_step[e] < 0) return ORC_EINVAL;
     for (int64_t e = 1; e < d->n_itm; ++e)
         if (d->itm_path[e] <= d->itm_path[e - 1]) return ORC_EINVAL;
     for (int64_t e = 1; e < d->n_cell; ++e)
@@ -509,9 +582,16 @@ int orc_run_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, 
     for (int32_t k = started + 1; k < n_threads; ++k) orc_job_run(&jobs[k]);
 
     st = ORC_OK;
+    int64_t ov[2] = { 0, 0 };
     for (int32_t k = 0; k < n_threads; ++k) {     /* fixed order: range 0 first */
         if (jobs[k].status != ORC_OK) st = jobs[k].status;
         for (int64_t e = 0; e < width; ++e) out[e] += jobs[k].out[e];
+        ov[0] += jobs[k].ov[0];
+        ov[1] += jobs[k].ov[1];
+    }
+    if (dec && dec->out_overrides) {
+        dec->out_overrides[0] = ov[0];
+        dec->out_overrides[1] = ov[1];
     }
     free(jobs); free(parts); free(th);
     return st;
@@ -536,7 +616,8 @@ typedef struct {
     const orc_option* op;
     const orc_decisions* dec;
     int64_t first, begin, end;    /* paths [begin, end) written at index p - first */
-    double *xN, *V, *xbar0;
+    double *xN, *V, *xbar0, *amp;
+    int64_t ov[2];                /* applied decisions that differed from the oracle's own */
     int status;
 } orc_path_job;
 
@@ -553,30 +634,35 @@ static void* orc_path_job_run(void* arg)
         jb->status = ORC_ENOMEM;
         return NULL;
     }
+    jb->status = ORC_OK;
     for (int64_t p = jb->begin; p < jb->end; ++p) {
         orc_path_result res;
-        orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, 1, 0.0, jb->dec, vega, vega + IJ, &res);
+        const int st = orc_one_path(jb->sf, jb->op, (uint64_t)p, &ws, 1, 0.0, jb->dec, vega, vega + IJ, &res, jb->ov);
+        if (st != ORC_OK) {
+            jb->status = st;
+            break;
+        }
         const int64_t q = p - jb->first;
         /* ln S_N under either scheme */
         if (jb->xN)
             jb->xN[q] = jb->op->scheme == ORC_SCHEME_X ? log(ws.x[jb->op->n_steps]) : ws.x[jb->op->n_steps];
         if (jb->V) jb->V[q] = res.V;
         if (jb->xbar0) jb->xbar0[q] = res.xbar0;
+        if (jb->amp) jb->amp[q] = res.amp;
     }
     free(ws.x); free(ws.z); free(vega);
-    jb->status = ORC_OK;
     return NULL;
 }
 
 int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
               int32_t n_threads, double* out_xN, double* out_V, double* out_xbar0)
 {
-    return orc_paths_ex(sf, op, path_begin, m, NULL, n_threads, out_xN, out_V, out_xbar0);
+    return orc_paths_ex(sf, op, path_begin, m, NULL, n_threads, out_xN, out_V, out_xbar0, NULL);
 }
 
 int orc_paths_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
                  const orc_decisions* dec, int32_t n_threads, double* out_xN, double* out_V,
-                 double* out_xbar0)
+                 double* out_xbar0, double* out_amp)
 {
     int st = orc_check(sf, op);
     if (st != ORC_OK) return st;
@@ -601,6 +687,7 @@ int orc_paths_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin
         jobs[k].xN = out_xN;
         jobs[k].V = out_V;
         jobs[k].xbar0 = out_xbar0;
+        jobs[k].amp = out_amp;
         jobs[k].status = ORC_EINTERNAL;
     }
     int started = 0;
@@ -612,8 +699,16 @@ int orc_paths_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin
     for (int32_t k = 1; k <= started; ++k) pthread_join(th[k], NULL);
     for (int32_t k = started + 1; k < n_threads; ++k) orc_path_job_run(&jobs[k]);
     st = ORC_OK;
-    for (int32_t k = 0; k < n_threads; ++k)
+    int64_t ov[2] = { 0, 0 };
+    for (int32_t k = 0; k < n_threads; ++k) {
         if (jobs[k].status != ORC_OK) st = jobs[k].status;
+        ov[0] += jobs[k].ov[0];
+        ov[1] += jobs[k].ov[1];
+    }
+    if (dec && dec->out_overrides) {
+        dec->out_overrides[0] = ov[0];
+        dec->out_overrides[1] = ov[1];
+    }
     free(jobs); free(th);
     return st;
 }

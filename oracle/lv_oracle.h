@@ -11,7 +11,9 @@
 extern "C" {
 #endif
 
-enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EINTERNAL = 4 };
+/* ORC_EDECISION: an imposed decision (see orc_decisions) that rounding of
+ * the path could not have produced. */
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOMEM = 2, ORC_EINTERNAL = 4, ORC_EDECISION = 5 };
 
 /* Layout of the sums array filled by orc_run: ORC_NSCAL scalars, then
  * vega[I*J] (sum of sigma adjoints per node, spot-major), then
@@ -69,7 +71,13 @@ typedef struct {
 
 /* Decisions taken from outside for listed paths / steps (see lv_oracle.c):
  * payoff indicator per path; spot-cell code 2 i + inside per (path, step).
- * Both lists sorted ascending (by path, then step). */
+ * Both lists sorted ascending (by path, then step). A decision that differs
+ * from the oracle's own is accepted only within `band` (relative) of the
+ * value that separates the two choices: the strike, the node between two
+ * adjacent cells, or the grid's edge node; any other is refused with
+ * ORC_EDECISION. out_overrides (nullable, 2 entries) receives how many cell
+ * decisions and how many payoff decisions of the call differed from the
+ * oracle's own and were applied. */
 typedef struct {
     const int64_t* itm_path;
     const int8_t* itm_val;
@@ -78,6 +86,8 @@ typedef struct {
     const int32_t* cell_step;
     const int32_t* cell_code;
     int64_t n_cell;
+    double band;
+    int64_t* out_overrides;
 } orc_decisions;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -95,9 +105,11 @@ int orc_run_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, 
 int orc_finalize(const double* sums, int64_t n_paths, double S0, int64_t IJ, double* res);
 int orc_paths(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
               int32_t n_threads, double* out_xN, double* out_V, double* out_xbar0);
+/* out_amp (nullable): per path, the bound on d ln |xbar_0| / d e for a relative
+ * error e in every spot of the path (see orc_path_result in lv_oracle.c). */
 int orc_paths_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t m,
                  const orc_decisions* dec, int32_t n_threads, double* out_xN, double* out_V,
-                 double* out_xbar0);
+                 double* out_xbar0, double* out_amp);
 int orc_bump(const orc_surface* sf, const orc_option* op, int64_t n_paths, double eps_sigma,
              double eps_S0, int32_t n_threads, double* out_vega, double* out_delta);
 

@@ -19,8 +19,8 @@ MUTANTS = {
     "drift sign": ("(op->r - 0.5 * pt.sigma * pt.sigma) * dt",
                    "(op->r + 0.5 * pt.sigma * pt.sigma) * dt"),
     "dx/dsigma sign": ("sqdt * z[n] - pt.sigma * dt;", "sqdt * z[n] + pt.sigma * dt;"),
-    "dsigma/dx drops S": ("xbar * (1.0 + h * S * pt.dsigma_dS)",
-                          "xbar * (1.0 + h * pt.dsigma_dS)"),
+    "dsigma/dx drops S": ("factor = 1.0 + h * S * pt.dsigma_dS;",
+                          "factor = 1.0 + h * pt.dsigma_dS;"),
     "node weights transposed": ("p->w[1] = u * (1.0 - v);", "p->w[1] = (1.0 - u) * v;"),
     "philox wrong product": ("uint32_t n0 = hi1 ^ c1 ^ k0;", "uint32_t n0 = hi0 ^ c1 ^ k0;"),
     "philox key schedule": ("k1 += ORC_PHILOX_W1;", "k1 += ORC_PHILOX_W0;"),
@@ -34,11 +34,11 @@ MUTANTS = {
     "cell rule strict": ("if (nodes[mid] <= x) lo = mid;", "if (nodes[mid] < x) lo = mid;"),
     "slope kept outside grid": ("if (inside)\n", "if (1)\n"),
     "sigma at right point": ("double t = (double)n * dt;\n        double S = on_x ? x[n] : exp(x[n]);\n"
-                             "        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);\n"
-                             "        if (on_x)",
+                             "        st = orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), band, &pt, "
+                             "&overridden);\n        if (st != ORC_OK) return st;\n        ov[0] += overridden;",
                              "double t = (double)(n + 1) * dt;\n        double S = on_x ? x[n] : exp(x[n]);\n"
-                             "        orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), &pt);\n"
-                             "        if (on_x)"),
+                             "        st = orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), band, &pt, "
+                             "&overridden);\n        if (st != ORC_OK) return st;\n        ov[0] += overridden;"),
     "inside test drops the upper edge": ("int inside = (S >= sf->spot[0] && S <= sf->spot[I - 1]);",
                                          "int inside = (S >= sf->spot[0]);"),
     "payoff sign": ("const double itm = (double)op->phi * (SN - op->K);",
@@ -47,8 +47,8 @@ MUTANTS = {
                                    "double du_dS = logs ? 1.0 / (log(hi_s) - log(lo_s))"),
     "log weight taken in S": ("u = logs ? (log(S) - log(lo_s)) / (log(hi_s) - log(lo_s))",
                               "u = logs ? (S - lo_s) / (log(hi_s) - log(lo_s))"),
-    "Euler on X: adjoint drops r dt": ("xbar * (1.0 + op->r * dt + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS)",
-                                       "xbar * (1.0 + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS)"),
+    "Euler on X: adjoint drops r dt": ("factor = 1.0 + op->r * dt + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS;",
+                                       "factor = 1.0 + pt.sigma * sqdt * z[n] + h * pt.dsigma_dS;"),
     "Euler on X: dx/dsigma drops the spot": ("double h = on_x ? x[n] * sqdt * z[n]", "double h = on_x ? sqdt * z[n]"),
     "rho drops the discount's share": ("double rho = -op->T * res->V;", "double rho = 0.0;"),
     "d V / d T: step time factor off by one": ("h * pt.dsigma_dt * (double)n / (double)N",
