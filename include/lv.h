@@ -252,7 +252,8 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
                          int32_t n_steps, int64_t n_paths, uint64_t seed, double eps,
                          double* out_price, double* out_delta, double* out_vega);
 
-/* Per-path diagnostics for paths [path_begin, path_begin + m), m <= 2^26:
+/* Per-path diagnostics for paths [path_begin, path_begin + m), m <= 2^26,
+ * of RNG stream stream_id (< 65536, as in lv_price_greeks_sums_device):
  * terminal log-spot x_N, discounted payoff V and d V / d x_0, each [m]
  * binary32 in host memory owned by the caller (any may be NULL). The values
  * of a path do not depend on the launch shape. Also logs every forward step
@@ -262,16 +263,35 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
  * (which switches d sigma / d S on); *out_n_ev the number of such steps
  * (entries beyond ev_cap are counted but not stored; order unspecified).
  * These are the integer decisions a binary64 reimplementation may take
- * differently when S sits within rounding of a node. */
+ * differently when S sits within rounding of a node (Sec. IV-D's cell of
+ * the bilinear interpolation). */
 lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T,
-                         int32_t n_steps, uint64_t seed, int64_t path_begin, int64_t m,
+                         int32_t n_steps, uint64_t seed, uint32_t stream_id, int64_t path_begin, int64_t m,
                          float* out_xN, float* out_V, float* out_xbar0,
                          double node_band, int64_t ev_cap, int32_t* out_ev, int64_t* out_n_ev);
 
+/* The kernels' random numbers (Sec. IV-B, read as Philox4x32-10 with the
+ * key, counter and transform given at the top of this file), for tests: for entry e
+ * of n (n in [1, 2^24]), the Philox block blocks[e] of path paths[e]
+ * (< 2^48) of stream stream_id (< 65536) under key seed. out_words [n][4]
+ * receives the four 32-bit words, out_z [n][4] the four binary32 normals
+ * the kernels derive from them (Box-Muller on word pairs (0,1), (2,3)).
+ * Host arrays owned by the caller; synchronous; no handle needed. */
+lv_status lv_debug_normals(uint64_t seed, uint32_t stream_id, const int64_t* paths, const uint32_t* blocks,
+                           int64_t n, uint32_t* out_words, float* out_z);
+
+/* The kernels' time table of a call with maturity T and n_steps steps on
+ * the handle's grid (Sec. IV-A: sigma at the left point t_n = n T / N;
+ * Sec. IV-D: the time cell), for tests: out_j [n_steps] receives the time
+ * cell j_n = the largest j <= J-2 with tau_j <= t_n (0 for one time node),
+ * out_v [n_steps] the clamped weight (t_n - tau_j) / (tau_{j+1} - tau_j)
+ * rounded to binary32 as the kernels use it. Both decided in binary64.
+ * Host arrays owned by the caller; synchronous (on the handle's stream). */
+lv_status lv_debug_time_table(lv_surface_t h, double T, int32_t n_steps, int32_t* out_j, float* out_v);
+
 /* lv_price_greeks_device_noalloc -- lv_price_greeks_device for callers that
- * cannot allocate device memory during the call: code running while someone
- * else captures a CUDA graph, loops with a no-allocation rule, or runtimes
- * that own every device allocation. The paper has no counterpart; it is a
+ * cannot allocate device memory during the call: loops with a no-allocation
+ * rule, or runtimes that own every device allocation. The paper has no counterpart; it is a
  * deployment variant of the same computation with the same results (up to
  * reduction order) and the same output layout (LV_OUT_*), written to d_out
  * (device memory owned by the caller) on the handle's stream, without

@@ -19,7 +19,13 @@ class LVPrice(torch.autograd.Function):
     S0: 0-d tensor; sigma: [n_spot, n_time] tensor (any device, float64 or
     float32); surface: an lv.Surface whose node vectors define the grid (its
     sigma values are replaced by `sigma`). Returns a 0-d float64 tensor on
-    sigma's device."""
+    sigma's device.
+
+    The forward call records the surface's settings (this sigma, the option
+    type, the accumulation, the adjoint method and the readings); backward
+    passes them back to the handle before running the adjoint, so several
+    terms priced on one Surface with different sigma or settings each get
+    their own derivatives, whatever the surface holds when backward runs."""
 
     @staticmethod
     def forward(ctx, S0, sigma, surface, r, K, T, n_steps, n_paths, seed):
@@ -28,6 +34,7 @@ class LVPrice(torch.autograd.Function):
         surface.set_sigma(np.ascontiguousarray(sig))
         price, _ = surface.price(s0, r, K, T, n_steps, n_paths, seed)
         ctx.surface = surface
+        ctx.state = surface.state()
         ctx.args = (s0, r, K, T, n_steps, n_paths, seed)
         ctx.shape = sigma.shape
         ctx.sigma_dtype, ctx.s0_dtype = sigma.dtype, S0.dtype
@@ -42,6 +49,7 @@ class LVPrice(torch.autograd.Function):
         dev = torch.device("cuda", torch.cuda.current_device())
         out = torch.empty(n, dtype=torch.float64, device=dev)
         surface.set_stream(torch.cuda.current_stream(dev).cuda_stream)
+        surface.restore(ctx.state)               # the settings this term was priced with
         surface.price_greeks_device(s0, r, K, T, n_steps, n_paths, seed, out.data_ptr())
         g = grad_out.to(dev, torch.float64)
         d_s0 = (g * out[lv.LV_OUT_DELTA]).to(ctx.device, ctx.s0_dtype)

@@ -890,8 +890,8 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
 }
 
 lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
-                         uint64_t seed, int64_t path_begin, int64_t m, float* out_xN, float* out_V,
-                         float* out_xbar0, double node_band, int64_t ev_cap, int32_t* out_ev,
+                         uint64_t seed, uint32_t stream_id, int64_t path_begin, int64_t m, float* out_xN,
+                         float* out_V, float* out_xbar0, double node_band, int64_t ev_cap, int32_t* out_ev,
                          int64_t* out_n_ev)
 {
     if (!h) return fail(LV_EINVAL, "handle is NULL");
@@ -914,7 +914,7 @@ lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T
     }
     unsigned long long* dcount = reinterpret_cast<unsigned long long*>(d);
     float* df = reinterpret_cast<float*>(d + off_f);
-    McCall c{S0, r, K, T, n_steps, path_begin, m, seed, 0u, true, false, h->d_res};
+    McCall c{S0, r, K, T, n_steps, path_begin, m, seed, stream_id, true, false, h->d_res};
     c.dbg_xN = df;
     c.dbg_V = df + m;
     c.dbg_xbar0 = df + 2 * m;
@@ -949,14 +949,71 @@ lv_status lv_debug_paths(lv_surface_t h, double S0, double r, double K, double T
     return st;
 }
 
+lv_status lv_debug_normals(uint64_t seed, uint32_t stream_id, const int64_t* paths, const uint32_t* blocks,
+                           int64_t n, uint32_t* out_words, float* out_z)
+{
+    if (!paths || !blocks || !out_words || !out_z) return fail(LV_EINVAL, "NULL argument");
+    if (n < 1 || n > ((int64_t)1 << 24)) return fail(LV_EINVAL, "n must be in [1, 2^24]");
+    if (stream_id >= 65536u) return fail(LV_EINVAL, "stream_id must be < 65536");
+    for (int64_t e = 0; e < n; ++e)
+        if (paths[e] < 0 || paths[e] >= LV_MAX_PATH_INDEX) return fail(LV_EINVAL, "path indices must lie in [0, 2^48)");
+    // one allocation: [paths n][blocks n][words 4n][z 4n], each section 256-byte aligned
+    const size_t off_b = round_up(sizeof(long long) * (size_t)n, 256);
+    const size_t off_w = round_up(off_b + sizeof(uint32_t) * (size_t)n, 256);
+    const size_t off_z = round_up(off_w + sizeof(uint32_t) * 4 * (size_t)n, 256);
+    const size_t total = off_z + sizeof(float) * 4 * (size_t)n;
+    char* d = nullptr;
+    if (cudaMalloc(&d, total) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LV_ENOMEM, "cannot allocate the normals buffers");
+    }
+    cudaError_t e = cudaMemcpy(d, paths, sizeof(long long) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + off_b, blocks, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = lv::launch_debug_normals(seed, stream_id, reinterpret_cast<const long long*>(d),
+                                     reinterpret_cast<const uint32_t*>(d + off_b), n,
+                                     reinterpret_cast<uint32_t*>(d + off_w), reinterpret_cast<float*>(d + off_z), 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out_words, d + off_w, sizeof(uint32_t) * 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out_z, d + off_z, sizeof(float) * 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(LV_ECUDA, std::string("lv_debug_normals: ") + cudaGetErrorString(e));
+    return LV_OK;
+}
+
+lv_status lv_debug_time_table(lv_surface_t h, double T, int32_t n_steps, int32_t* out_j, float* out_v)
+{
+    if (!h || !out_j || !out_v) return fail(LV_EINVAL, "NULL argument");
+    lv_status st = check_option(1.0, 0.0, 1.0, T, n_steps);
+    if (st != LV_OK) return st;
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{1.0, 0.0, 1.0, T, n_steps, 0, 1, 1, 0u, true, false, h->d_res};
+    const lv::McParams P = base_params(h, c);
+    const size_t off_v = round_up(sizeof(int) * (size_t)n_steps, 256);
+    char* d = nullptr;
+    if (cudaMalloc(&d, off_v + sizeof(float) * (size_t)n_steps) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(LV_ENOMEM, "cannot allocate the time-table buffers");
+    }
+    cudaError_t e = lv::launch_debug_time_table(P, reinterpret_cast<int*>(d), reinterpret_cast<float*>(d + off_v),
+                                                h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_j, d, sizeof(int) * (size_t)n_steps, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out_v, d + off_v, sizeof(float) * (size_t)n_steps, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(LV_ECUDA, std::string("lv_debug_time_table: ") + cudaGetErrorString(e));
+    return LV_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of lv_price_greeks_device.
 //
-// Some callers cannot call cudaMalloc while they run: code inside a CUDA
-// graph being captured by someone else, a real-time loop with a no-allocation
-// rule, or an embedding runtime that owns every device allocation itself.
+// Some callers cannot call cudaMalloc while they run: a real-time loop with a
+// no-allocation rule, or an embedding runtime that owns every device
+// allocation itself.
 // For them the adjoint can run on scratch memory the library reserves once
 // when its module is loaded: a file-scope __device__ array, kept by every
 // GPU that loads the library until the process exits.

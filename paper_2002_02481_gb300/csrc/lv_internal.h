@@ -121,6 +121,12 @@ cudaError_t launch_bump_finalize(const double* partials, int G, int row_words, d
 
 size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra = false);
 
+// Test-facing kernels (lv_debug.cu): Philox words and normals for listed
+// (path, block) counters; the per-step time table of a call.
+cudaError_t launch_debug_normals(uint64_t seed, uint32_t stream_id, const long long* paths, const uint32_t* blocks,
+                                 long long n, uint32_t* words, float* z, cudaStream_t s);
+cudaError_t launch_debug_time_table(const McParams& P, int* out_j, float* out_v, cudaStream_t s);
+
 // Launchers; return cudaSuccess or the launch error. An adjoint launch with
 // p.dbg_xN != null runs the logging instantiation with k = 4 and binary64
 // level 2 whatever k and p.acc_mode say: plan its scratch with k = 4.

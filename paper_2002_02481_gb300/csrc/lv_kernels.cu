@@ -168,7 +168,7 @@ __global__ void finalize_sums_kernel(const double* __restrict__ sums, int IJ, lo
         const double mean = sums[0] / P;
         const double var = n_paths > 1 ? (sums[1] / P - mean * mean) * P / (P - 1.0) : 0.0;
         out[LV_OUT_PRICE_DEV] = mean;
-        out[LV_OUT_STDERR_DEV] = var > 0.0 ? sqrt(var / P) : 0.0;
+        out[LV_OUT_STDERR_DEV] = (var > 0.0 || var != var) ? sqrt(var / P) : 0.0;   // NaN stays NaN
         out[LV_OUT_DELTA_DEV] = sums[2] / (P * S0);
     }
     if (e < IJ) out[3 + e] = sums[3 + e] / P;

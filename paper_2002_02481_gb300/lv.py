@@ -84,8 +84,10 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_price_greeks_ext_device": [vp, d, d, d, d, i32, i64, u64, vp],
         "lv_price_greeks_sums_device": [vp, d, d, d, d, i32, i64, i64, u64, u32, vp],
         "lv_finalize_sums_device": [vp, vp, i64, d, vp],
-        "lv_debug_paths": [vp, d, d, d, d, i32, u64, i64, i64, fp, fp, fp, d, i64,
+        "lv_debug_paths": [vp, d, d, d, d, i32, u64, u32, i64, i64, fp, fp, fp, d, i64,
                            c.POINTER(i32), c.POINTER(i64)],
+        "lv_debug_normals": [u64, u32, c.POINTER(i64), c.POINTER(u32), i64, c.POINTER(u32), fp],
+        "lv_debug_time_table": [vp, d, i32, c.POINTER(i32), fp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -122,7 +124,11 @@ def _fp(a: Optional[np.ndarray]):
 
 
 class Surface:
-    """A local-vol grid staged on the current CUDA device (lv_surface_t)."""
+    """A local-vol grid staged on the current CUDA device (lv_surface_t).
+
+    The object mirrors the settings it last passed to the handle (sigma,
+    option type, accumulation, adjoint method, interpolation, scheme) in
+    attributes of the same names, so that a caller can restore them."""
 
     def __init__(self, spot, time, sigma, lib: Optional[ctypes.CDLL] = None):
         self.lib = lib or load()
@@ -130,6 +136,10 @@ class Surface:
         self.time = np.ascontiguousarray(time, dtype=np.float64)
         s = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
         self.n_spot, self.n_time = self.spot.shape[0], self.time.shape[0]
+        # the handle's settings as last set through this object (read by autograd)
+        self.sigma = s.copy()
+        self.phi, self.accumulation, self.method = 1, LV_ACC_FP64, LV_ADJ_REVERSE
+        self.interp, self.scheme = LV_INTERP_S, LV_SCHEME_LOG
         self.h = ctypes.c_void_p()
         _check(self.lib, self.lib.lv_surface_create(_dp(self.spot), self.n_spot, _dp(self.time), self.n_time,
                                                     _dp(s), ctypes.byref(self.h)), "lv_surface_create")
@@ -163,27 +173,47 @@ class Surface:
     def set_sigma(self, sigma) -> None:
         s = np.ascontiguousarray(sigma, dtype=np.float64).reshape(-1)
         _check(self.lib, self.lib.lv_surface_set_sigma(self.h, _dp(s)), "lv_surface_set_sigma")
+        self.sigma = s.copy()
 
     def set_option_type(self, phi: int) -> None:
         _check(self.lib, self.lib.lv_set_option_type(self.h, int(phi)), "lv_set_option_type")
+        self.phi = int(phi)
 
     def set_stream(self, stream_ptr: int) -> None:
         _check(self.lib, self.lib.lv_set_stream(self.h, ctypes.c_void_p(stream_ptr or None)), "lv_set_stream")
 
+    def state(self) -> dict:
+        """The settings mirrored by this object (see the class docstring)."""
+        return dict(sigma=self.sigma.copy(), phi=self.phi, accumulation=self.accumulation, method=self.method,
+                    interp=self.interp, scheme=self.scheme)
+
+    def restore(self, st: dict) -> None:
+        """Passes the settings of state() back to the handle."""
+        self.set_sigma(st["sigma"])
+        self.set_option_type(st["phi"])
+        self.set_accumulation(st["accumulation"])
+        self.set_adjoint_method(st["method"])
+        self.set_interpolation(st["interp"])
+        self.set_scheme(st["scheme"])
+
     def set_accumulation(self, mode: int) -> None:
         _check(self.lib, self.lib.lv_set_accumulation(self.h, int(mode)), "lv_set_accumulation")
+        self.accumulation = int(mode)
 
     def set_adjoint_method(self, method: int) -> None:
         """LV_ADJ_REVERSE (checkpointed reverse sweep) or LV_ADJ_TANGENT (tangent ratio)."""
         _check(self.lib, self.lib.lv_set_adjoint_method(self.h, int(method)), "lv_set_adjoint_method")
+        self.method = int(method)
 
     def set_interpolation(self, interp: int) -> None:
         """LV_INTERP_S (spot weight linear in S) or LV_INTERP_LOGS (in ln S)."""
         _check(self.lib, self.lib.lv_surface_set_interpolation(self.h, int(interp)), "lv_surface_set_interpolation")
+        self.interp = int(interp)
 
     def set_scheme(self, scheme: int) -> None:
         """LV_SCHEME_LOG (Euler on ln S) or LV_SCHEME_S (Euler on S)."""
         _check(self.lib, self.lib.lv_set_scheme(self.h, int(scheme)), "lv_set_scheme")
+        self.scheme = int(scheme)
 
     def set_launch(self, block: int = 0, k: int = 0, blocks_per_sm: int = 0) -> None:
         _check(self.lib, self.lib.lv_set_launch(self.h, int(block), int(k), int(blocks_per_sm)), "lv_set_launch")
@@ -248,14 +278,15 @@ class Surface:
                                                           float(S0), ctypes.c_void_p(d_out_ptr)),
                "lv_finalize_sums_device")
 
-    def debug_paths(self, S0, r, K, T, n_steps, seed, path_begin, m, node_band=0.0, ev_cap=0):
+    def debug_paths(self, S0, r, K, T, n_steps, seed, path_begin, m, node_band=0.0, ev_cap=0, stream_id=0):
         """(x_N, V, xbar0) per path, plus the near-node decision log
         (paths, steps, codes) when ev_cap > 0."""
         xN, V, xb = (np.zeros(m, dtype=np.float32) for _ in range(3))
         ev = np.zeros((max(ev_cap, 1), 3), dtype=np.int32)
         n_ev = ctypes.c_int64(0)
         _check(self.lib, self.lib.lv_debug_paths(
-            self.h, S0, r, K, T, int(n_steps), int(seed), int(path_begin), int(m), _fp(xN), _fp(V), _fp(xb),
+            self.h, S0, r, K, T, int(n_steps), int(seed), int(stream_id), int(path_begin), int(m), _fp(xN), _fp(V),
+            _fp(xb),
             float(node_band), int(ev_cap), ev.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
             ctypes.byref(n_ev)), "lv_debug_paths")
         if ev_cap <= 0:
@@ -265,6 +296,15 @@ class Surface:
         e = ev[:n_ev.value]
         return xN, V, xb, (e[:, 0].astype(np.int64) + int(path_begin), e[:, 1].copy(), e[:, 2].copy())
 
+    def time_table(self, T, n_steps):
+        """The kernels' (time cell j_n, binary32 weight v_n) for every step."""
+        j = np.zeros(n_steps, dtype=np.int32)
+        v = np.zeros(n_steps, dtype=np.float32)
+        _check(self.lib, self.lib.lv_debug_time_table(self.h, float(T), int(n_steps),
+                                                      j.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _fp(v)),
+               "lv_debug_time_table")
+        return j, v
+
     def bump_greeks(self, S0, r, K, T, n_steps, n_paths, seed, eps):
         p, d = ctypes.c_double(), ctypes.c_double()
         vega = np.zeros(self.IJ, dtype=np.float64)
@@ -272,6 +312,22 @@ class Surface:
                                                  float(eps), ctypes.byref(p), ctypes.byref(d), _dp(vega)),
                "lv_bump_greeks")
         return p.value, d.value, vega.reshape(self.n_spot, self.n_time)
+
+
+def debug_normals(seed, stream_id, paths, blocks, lib=None):
+    """The kernels' Philox words [n, 4] (uint32) and binary32 normals [n, 4]
+    for the (path, block) counters listed."""
+    lib = lib or load()
+    p = np.ascontiguousarray(paths, dtype=np.int64)
+    b = np.ascontiguousarray(blocks, dtype=np.uint32)
+    n = p.shape[0]
+    w = np.zeros((n, 4), dtype=np.uint32)
+    z = np.zeros((n, 4), dtype=np.float32)
+    _check(lib, lib.lv_debug_normals(int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream_id),
+                                     p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), int(n),
+                                     w.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _fp(z)), "lv_debug_normals")
+    return w, z
 
 
 class Instrument(ctypes.Structure):

@@ -11,10 +11,21 @@ the value sits within rounding of the threshold:
   - the spot cell of a step and whether S lies inside the grid (which picks
     the side of d sigma / d S), for S within rounding of a node.
 The kernel's debug entry point reports its per-path results and logs every
-step whose spot lies within NODE_BAND of a node together with the decision
-it took there; the oracle takes the kernel's decisions for exactly those
-steps and for the paths whose payoff decision differs (checked to lie at the
-kink), and the comparison then runs path for path.
+step whose spot lies within NODE_BAND of a node of its cell, with the
+decision it took there. The harness first measures how far the binary32
+paths drift from the oracle's (max |dx_N| over the paths) and sets the
+decision band to DRIFT_FACTOR times that drift plus the rounding of the
+kernel's cell index. The oracle then takes the kernel's logged cell
+decisions and its payoff decisions where they differ from its own, and
+checks each one: a decision other than its own is accepted only when the
+oracle's own spot lies within the band of the node (or strike) that
+separates the two choices, and the cell is the neighbour across that node;
+anything else is refused (oracle.DecisionRefused). The comparison then runs
+path for path, each path held to the bound its own drift implies:
+  |V - V_o|        <= disc (S_N (dx_N + 2^-20) + K 2^-22)
+  |xbar_0 - xbar_0o| <= |xbar_0o| (dx_N + amp band + N 2^-21 + 2^-20),
+with amp the oracle's per-path bound on how a relative error in every spot
+moves ln |xbar_0| (lv_oracle.c), and N 2^-21 eight binary32 roundings a step.
 """
 import numpy as np
 
@@ -24,9 +35,9 @@ from paper_2002_02481_gb300 import lv
 PRICE_RTOL = 1e-5
 DELTA_RTOL = 1e-5
 VEGA_TOL_OF_MAX = 1e-4
-KINK_REL = 1e-4          # a payoff decision may differ only this close to the strike
-X_ATOL = 1e-4            # per-path |x_N(binary32) - x_N(binary64)|
-NODE_BAND = 2e-4         # logged steps: |S - s| <= NODE_BAND * s for a node s of the cell
+NODE_BAND = 5e-4         # logged steps: |S - s| <= NODE_BAND * s for a node s of the cell
+DRIFT_FACTOR = 4.0       # decision band = DRIFT_FACTOR * max |dx_N| + INDEX_ROUNDING
+INDEX_ROUNDING = 2.0 ** -20   # relative error of the kernel's binary32 cell index, in S
 
 
 def make_surface(w_surf, opt, lib, launch=None, accumulation=0, method=lv.LV_ADJ_REVERSE):
@@ -43,36 +54,47 @@ def make_surface(w_surf, opt, lib, launch=None, accumulation=0, method=lv.LV_ADJ
 
 def per_path(gs, w_surf, opt, m=None, path_begin=0):
     """Per-path comparison on paths [path_begin, path_begin + m); returns the
-    decisions for the oracle (the kernel's, where they can differ)."""
+    decisions for the oracle (the kernel's, checked by the oracle) and the
+    statistics of the comparison."""
     m = opt.n_paths if m is None else m
     cap = min(1 << 27, 64 * m + 65536)
     gx, gV, gxb, cells = gs.debug_paths(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.seed, path_begin, m,
-                                        node_band=NODE_BAND, ev_cap=cap)
-    ox, oV, oxb = oracle.paths(w_surf, opt, path_begin, m, decisions=oracle.Decisions(cells=cells))
+                                        node_band=NODE_BAND, ev_cap=cap, stream_id=opt.stream_id)
+    assert np.all(np.isfinite(gx)), "non-finite binary32 path"
+    # drift of the binary32 paths from the oracle's own, before any decision is taken
+    ox0, oV0, _ = oracle.paths(w_surf, opt, path_begin, m)
+    dx0 = np.abs(gx.astype(np.float64) - ox0)
+    band = DRIFT_FACTOR * float(dx0.max()) + INDEX_ROUNDING
+    # every step where the two sides could decide a cell differently lies within band of
+    # a node for the oracle, so within band + drift < NODE_BAND for the kernel: it was logged
+    assert band <= 0.5 * NODE_BAND, f"drift {dx0.max():.3e} too large for the logged band"
+    flipped = np.nonzero((gV > 0) != (oV0 > 0))[0]
+    itm = {int(path_begin + p): bool(gV[p] > 0) for p in flipped}
+    dec = oracle.Decisions(itm=itm, cells=cells, band=band)
+    ox, oV, oxb, amp = oracle.paths(w_surf, opt, path_begin, m, decisions=dec, amp=True)
+    overrides = dec.overrides
     dx = np.abs(gx.astype(np.float64) - ox)
-    assert np.all(np.isfinite(gx)) and dx.max() <= X_ATOL, f"max |dx_N| = {dx.max():.3e}"
-    assert dx.max() <= 0.25 * NODE_BAND, "the paths drift further apart than the logged band"
-    g_itm, o_itm = gV > 0, oV > 0
-    flipped = np.nonzero(g_itm != o_itm)[0]
-    if flipped.size:
-        SN = np.exp(ox[flipped])
-        assert np.all(np.abs(SN - opt.K) <= KINK_REL * opt.K), "decision differs away from the kink"
-    # payoffs: continuous in S_N, so they differ by about S_N |dx_N|
+    SN = np.exp(ox)
     disc = np.exp(-opt.r * opt.T)
-    np.testing.assert_array_less(np.abs(gV - oV), X_ATOL * disc * np.exp(ox) + 1e-6)
-    both = g_itm & o_itm
+    # payoffs: continuous in S_N (binary32: exp2 and a subtraction)
+    v_bound = disc * (SN * (dx + 2.0 ** -20) + abs(opt.K) * 2.0 ** -22) + 1e-300
+    v_err = np.abs(gV.astype(np.float64) - oV)
+    assert np.all(v_err <= v_bound), f"payoff off its bound by {np.max(v_err / v_bound):.2f}x"
+    both = (gV > 0) & (oV > 0)
     xb_stats = {}
     if both.any():
-        rel = np.abs(gxb[both] - oxb[both]) / np.maximum(np.abs(oxb[both]), 1e-12)
-        assert np.median(rel) < 1e-5, np.median(rel)
-        assert np.quantile(rel, 0.99) < 1e-3, np.quantile(rel, 0.99)
-        assert rel.max() < 1e-2, rel.max()
+        ref = np.abs(oxb[both])
+        err = np.abs(gxb[both].astype(np.float64) - oxb[both])
+        bound = ref * (dx[both] + amp[both] * band + opt.n_steps * 2.0 ** -21 + 2.0 ** -20)
+        ratio = err / np.maximum(bound, 1e-300)
+        assert np.all(ratio <= 1.0), f"xbar_0 off its per-path bound by {ratio.max():.2f}x"
+        rel = err / np.maximum(ref, 1e-300)
         xb_stats = dict(xbar0_rel_median=float(np.median(rel)), xbar0_rel_q99=float(np.quantile(rel, 0.99)),
-                        xbar0_rel_max=float(rel.max()))
-    stats = dict(max_dx=float(dx.max()), n_flipped=int(flipped.size), n_cell_decisions=int(len(cells[0])),
-                 **xb_stats)
-    itm = {int(path_begin + p): bool(g_itm[p]) for p in flipped}
-    return oracle.Decisions(itm=itm, cells=cells), stats
+                        xbar0_rel_max=float(rel.max()), xbar0_err_of_bound_max=float(ratio.max()))
+    stats = dict(path_steps=int(m) * int(opt.n_steps), max_dx=float(dx.max()), band=band,
+                 logged_steps=int(len(cells[0])), cell_overrides=overrides["cell"],
+                 payoff_overrides=overrides["payoff"], **xb_stats)
+    return dec, stats
 
 
 def _rel(a, b):

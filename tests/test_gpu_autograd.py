@@ -42,3 +42,34 @@ def test_backward_is_the_adjoint(lib):
     vfd, dfd = oracle.bump(surf, opt, 1e-5, 1e-5 * opt.S0)
     assert np.max(np.abs(sigma.grad.cpu().numpy() / 3.0 - vfd)) <= 2e-3 * vmax
     s.close()
+
+
+def test_two_terms_on_one_surface(lib):
+    """Two prices on one Surface with different sigma (and option type) in one
+    graph, a single backward: each term gets the derivatives of its own
+    sigma, not of whatever the surface holds when backward runs."""
+    import torch
+    from paper_2002_02481_gb300.autograd import lv_price
+    surf = W.random_surface(8, 4, 3, s_lo=80, s_hi=125, t_hi=1.0)
+    opt = W.Option(S0=100.0, r=0.01, K=100.0, T=0.9, n_steps=12, n_paths=8192, seed=5)
+    s = lv.Surface.from_workload(surf, lib)
+    sig_a = torch.tensor(surf.sigma, dtype=torch.float64, device="cuda", requires_grad=True)
+    sig_b = torch.tensor(surf.sigma * 1.3, dtype=torch.float64, device="cuda", requires_grad=True)
+    S0 = torch.tensor(opt.S0, dtype=torch.float64, requires_grad=True)
+    pa = lv_price(S0, sig_a, s, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    s.set_option_type(-1)
+    pb = lv_price(S0, sig_b, s, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    s.set_option_type(1)
+    s.set_sigma(surf.sigma * 0.5)                  # what the surface holds when backward runs
+    (pa + 2.0 * pb).backward()
+    # each term separately, on fresh handles
+    ra = lv.Surface.from_workload(surf, lib)
+    _, da, va = ra.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    rb = lv.Surface(surf.spot, surf.time, surf.sigma * 1.3, lib)
+    rb.set_option_type(-1)
+    _, db, vb = rb.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert abs(float(S0.grad) - (da + 2.0 * db)) <= 1e-9 * (abs(da) + 2.0 * abs(db))
+    assert np.max(np.abs(sig_a.grad.cpu().numpy() - va)) <= 1e-6 * np.max(np.abs(va))
+    assert np.max(np.abs(sig_b.grad.cpu().numpy() - 2.0 * vb)) <= 1e-6 * np.max(np.abs(2.0 * vb))
+    for h in (s, ra, rb):
+        h.close()

@@ -10,6 +10,8 @@ import oracle
 import workloads as W
 from paper_2002_02481_gb300 import build, lv
 
+from . import gpu_common as G
+
 pytestmark = pytest.mark.gpu
 
 
@@ -172,4 +174,36 @@ def test_aggregated_risk_against_the_oracle(lib):
     p, _, _, v = book.risk(risk, s)
     assert abs(p - ref_p) <= 1e-5 * max(abs(ref_p), 1e-12)
     assert np.max(np.abs(v - ref_v)) <= 1e-4 * max(np.max(np.abs(ref_v)), 1e-12)
+    book.close()
+
+
+def test_benchmark_book_against_oracle(lib):
+    """The benchmark's book (8 seeded 30x60 surfaces x 64 options, uneven
+    maturities and path counts up to 2^20) in the launch shape its autotuner
+    picks: four options of surface 0 at their real path counts against the
+    oracle, path for path with the kernel's near-node decisions checked and
+    imposed (the book runs the single-option kernel's per-path code)."""
+    surfs_w = W.book_surfaces()
+    items = W.book_items()
+    handles = [lv.Surface.from_workload(s, lib) for s in surfs_w]
+    book = lv.Book(handles, items, lib)
+    for h in handles:
+        h.close()
+    book.tune(100.0, 0.0, 1)
+    out = book.run(100.0, 0.0, 1)
+    mine = [o for o, it in enumerate(items) if it.surface == 0]
+    # the longest maturity, the most paths, a put and a short call
+    pick = {max(mine, key=lambda o: items[o].T), max(mine, key=lambda o: items[o].n_paths),
+            next(o for o in mine if items[o].phi < 0), next(o for o in mine if items[o].phi > 0 and items[o].T <= 0.5)}
+    for o in sorted(pick):
+        it = items[o]
+        opt = W.Option(S0=100.0, r=0.0, K=it.K, T=it.T, n_steps=it.n_steps, n_paths=it.n_paths, seed=1,
+                       phi=it.phi, stream_id=it.stream_id)
+        gs = G.make_surface(surfs_w[0], opt, lib)
+        dec, _ = G.per_path(gs, surfs_w[0], opt)
+        gs.close()
+        ref = oracle.finalize(oracle.run_sums(surfs_w[0], opt, decisions=dec), opt.n_paths, opt.S0,
+                              surfs_w[0].n_spot * surfs_w[0].n_time)
+        p, d, _, v = book.result(out, o)
+        G.compare_aggregates(p, d, v, ref, label=f"book option {o} (T={it.T}, P={it.n_paths}, phi={it.phi})")
     book.close()

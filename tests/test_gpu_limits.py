@@ -56,12 +56,16 @@ def test_top_of_the_path_index_space(lib):
     assert abs(s[2] - ref[oracle.SUM_XBAR0]) <= G.DELTA_RTOL * abs(ref[oracle.SUM_XBAR0])
     v_ref = ref[oracle.NSCAL:oracle.NSCAL + gs.IJ]
     assert np.max(np.abs(s[3:] - v_ref)) <= G.VEGA_TOL_OF_MAX * np.max(np.abs(v_ref))
-    # the largest stream id (the top 16 bits of counter word 2) against the oracle
+    # the largest stream id (the top 16 bits of counter word 2) against the oracle,
+    # path for path with the kernel's near-node decisions checked and imposed
     o2 = W.Option(**{**opt.__dict__, "stream_id": 65535})
-    ref2 = oracle.run_sums(surf, o2, pb, pb + m)
+    dec2, _ = G.per_path(gs, surf, o2, m=m, path_begin=pb)
+    ref2 = oracle.run_sums(surf, o2, pb, pb + m, decisions=dec2)
     d2 = torch.zeros_like(d)
     gs.price_greeks_sums_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, pb, pb + m, opt.seed, 65535,
                                 d2.data_ptr())
     s2 = d2.cpu().numpy()
-    assert abs(s2[0] - ref2[oracle.SUM_V]) <= 1e-4 * abs(ref2[oracle.SUM_V])
-    assert abs(s2[2] - ref2[oracle.SUM_XBAR0]) <= 1e-4 * abs(ref2[oracle.SUM_XBAR0])
+    assert abs(s2[0] - ref2[oracle.SUM_V]) <= G.PRICE_RTOL * abs(ref2[oracle.SUM_V])
+    assert abs(s2[2] - ref2[oracle.SUM_XBAR0]) <= G.DELTA_RTOL * abs(ref2[oracle.SUM_XBAR0])
+    v2 = ref2[oracle.NSCAL:oracle.NSCAL + gs.IJ]
+    assert np.max(np.abs(s2[3:] - v2)) <= G.VEGA_TOL_OF_MAX * np.max(np.abs(v2))

@@ -90,6 +90,19 @@ def test_large_grid_sample(lib):
             G.full_parity(surf, opt, lib, launch=(128, 32, 0), label="large"))
 
 
+def test_large_grid_timed_shape(lib):
+    """100x100 grid, 1,260 steps, in the launch shape the benchmark times it
+    at (block 128, checkpoints every 4 steps, the grid read through L1): the
+    first 2^14 paths against the oracle."""
+    surf, opt = W.config_large()
+    opt.n_paths = 1 << 14
+    s = G.make_surface(surf, opt, lib, launch=(128, 4, 0))
+    assert s.get_launch(opt.n_steps, True)[:2] == (128, 4)
+    s.close()
+    _report("100x100 grid, 1260 steps, 2^14 paths, k=4",
+            G.full_parity(surf, opt, lib, launch=(128, 4, 0), label="large k=4"))
+
+
 @pytest.mark.parametrize("launch", [(128, 4, 0), (96, 8, 0), (128, 16, 0), (128, 32, 1), (64, 8, 2), (32, 4, 0)])
 def test_launch_shape_invariance(launch, lib):
     """Per-path arithmetic does not depend on the launch shape; results agree

@@ -133,6 +133,18 @@ def test_vanishing_factor_is_flagged(lib):
                              vega.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     assert st == lv.LV_ENUMERIC
     assert price.value == -7.0 and delta.value == -7.0 and np.all(vega == -7.0)
+    # the raw-sums path (what a path-range shard returns) carries the flag as NaN
+    # sums, and finalizing them keeps every output NaN, the standard error included
+    sums = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gs.set_stream(torch.cuda.current_stream().cuda_stream)
+    gs.price_greeks_sums_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, 0, opt.n_paths, opt.seed, 0,
+                                sums.data_ptr())
+    fin = torch.zeros(n, dtype=torch.float64, device="cuda")
+    gs.finalize_sums_device(sums.data_ptr(), opt.n_paths, opt.S0, fin.data_ptr())
+    torch.cuda.synchronize()
+    assert np.all(np.isnan(sums.cpu().numpy()))
+    assert np.all(np.isnan(fin.cpu().numpy())), fin.cpu().numpy()[:3]
+    gs.set_stream(0)
     gs.set_adjoint_method(lv.LV_ADJ_REVERSE)
     p, dl, v = gs.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
     assert np.isfinite(p) and np.isfinite(dl) and np.all(np.isfinite(v))
