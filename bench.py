@@ -10,8 +10,10 @@ finalize, inputs resident on the device. Prints ONE JSON line (rank 0).
 
 --impl reference times the FP64 CPU oracle on this host's cores on a
 bounded sample of the same workload (the reference arm of the comparison).
-Under torchrun (N > 1) every rank runs its own contiguous range of paths
-(weak scaling; no collective on the data path) and rank 0 reports the
+Under torchrun (N > 1) every rank runs its own contiguous range of 2^20
+paths of one N x 2^20-path estimate (weak scaling): the step is the
+sharded call, the adjoint on the rank's range, one all-reduce of the
+3 + 1,800 raw sums over the ranks and the finalize; rank 0 reports the
 aggregate with the max-over-ranks time.
 """
 from __future__ import annotations
@@ -39,11 +41,17 @@ WORKLOAD = "30x60 local-vol grid, 156 steps, 2^20 paths, European call K=100 T=3
 
 # Algorithmic thread-operations of one path-step of the method: one forward
 # step (Philox share, uniforms, Box-Muller share, exp, cell, bilinear sigma,
-# Euler) plus one reverse step (sigma adjoint, x adjoint, bucket scatter);
-# the checkpoint recompute is overhead and is not counted.
-ALG_OPS_PER_PATH_STEP = 55.0
-# Issue rate of an SM: 4 schedulers x 32 lanes per clock.
+# Euler) for every path, plus one reverse step (sigma adjoint, x adjoint,
+# bucket scatter) for the paths that end in the money (the others have a
+# zero adjoint everywhere and are not swept back); the checkpoint recompute
+# is overhead and is not counted.
+FWD_OPS_PER_PATH_STEP = 36.0
+REV_OPS_PER_PATH_STEP = 19.0
+# Issue rate of an SM: 4 schedulers x 32 lanes per clock (the fallback peak
+# when the pipe probe cannot run).
 LANES_PER_SM_CLOCK = 128
+# ncu pipe of each probed rate: warp instructions issued to that pipe
+PIPE_OF_PROBE = {"fma": "ffma", "fmaheavy": "imad_wide", "alu": "lop3", "xu": "mufu_ex2"}
 
 
 def dist_env():
@@ -166,14 +174,20 @@ def kernel_source_hash() -> str:
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per adjoint launch from the committed ncu capture, or None
-    when the kernel changed since it was taken."""
+def profiled_record():
+    """The committed ncu record of one adjoint launch on the bench workload
+    (DRAM bytes, warp instructions per pipe), or None when the kernel changed
+    since it was taken."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "adjoint_kernel_paper_shape.json")))
     except (OSError, ValueError):
         return None
-    return rec["dram_bytes_per_launch"] if rec.get("source_hash") == kernel_source_hash() else None
+    return rec if rec.get("source_hash") == kernel_source_hash() else None
+
+
+def profiled_traffic():
+    rec = profiled_record()
+    return rec["dram_bytes_per_launch"] if rec else None
 
 
 def load_peaks():
@@ -289,11 +303,158 @@ def other_workloads(lib, dev, ev0, ev1):
     return res
 
 
+def live_fraction(S, opt, m=1 << 16):
+    """Fraction of paths that end in the money (nonzero terminal adjoint), from
+    the kernel's per-path diagnostics on the first m paths."""
+    _, V, _ = S.debug_paths(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.seed, 0, m)
+    return float(np.mean(V > 0))
+
+
+def roofline_block(kern_ms, path_steps, live, peaks, mhz, n_sm, rec):
+    """Counted algorithmic work of the adjoint kernel against the measured
+    issue rate, and, from the committed ncu record, each pipe's busy fraction
+    against its measured rate."""
+    counted = FWD_OPS_PER_PATH_STEP + REV_OPS_PER_PATH_STEP * live
+    t = kern_ms * 1e-3
+    if peaks and peaks.get("ffma", 0) > 0:
+        peak = peaks["ffma"] / 1e9
+        src = "measured: lv_measure_pipe_peaks, fma.rn.f32 rate (one thread-instruction per lane per clock)"
+    else:
+        peak = n_sm * LANES_PER_SM_CLOCK * mhz * 1e6 / 1e9
+        src = f"derived: {n_sm} SMs x {LANES_PER_SM_CLOCK} lanes/clk x {mhz:.0f} MHz (pipe probe unavailable)"
+    achieved = counted * path_steps / t / 1e9
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+           "traffic": rec["dram_bytes_per_launch"] if rec else None, "kernel_ms": kern_ms, "peak_source": src,
+           "ops_per_path_step": {"forward": FWD_OPS_PER_PATH_STEP, "reverse": REV_OPS_PER_PATH_STEP,
+                                 "live_fraction": live, "counted": counted},
+           "frac_if_every_path_were_swept_back":
+               (FWD_OPS_PER_PATH_STEP + REV_OPS_PER_PATH_STEP) * path_steps / t / 1e9 / peak}
+    if rec and peaks and "pipe_warp_inst_per_launch" in rec:
+        wi = rec["pipe_warp_inst_per_launch"]
+        pipes = {}
+        for pipe, probe in PIPE_OF_PROBE.items():
+            if pipe in wi and peaks.get(probe, 0) > 0:
+                rate = wi[pipe] * 32.0 / t
+                pipes[pipe] = {"thread_ops_per_path_step": wi[pipe] * 32.0 / path_steps,
+                               "achieved_gops": rate / 1e9, "peak_gops": peaks[probe] / 1e9,
+                               "frac": rate / peaks[probe], "peak_probe": probe}
+        if "all" in wi:
+            issue = wi["all"] / (4.0 * n_sm * mhz * 1e6 * t)
+            pipes["issue_slots"] = {"warp_inst_per_launch": wi["all"], "frac": issue,
+                                    "thread_ops_per_path_step": wi["all"] * 32.0 / path_steps}
+        if pipes:
+            bind = max((k for k in pipes if k != "issue_slots"), key=lambda k: pipes[k]["frac"])
+            out["pipes"] = pipes
+            out["binding_pipe"] = bind
+    return out
+
+
+def equal_accuracy_bump(S, opt, errors, adjoint_err, kern_ms, bump32_ms, sample):
+    """The bump baseline's variants on the accuracy sample (error against the
+    FP64 oracle's pathwise estimator) with their time on the full workload,
+    and the speed-up of the adjoint over the cheapest variant that is at
+    least as accurate as the adjoint on every output."""
+    import torch
+    variants = []
+    for eps in (1e-4, 1e-3, 1e-2):
+        e = errors(*S.bump_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sample, opt.seed, eps))
+        variants.append({"name": f"binary32 paths, eps={eps:g}", "ms_full": bump32_ms, "timed_paths": opt.n_paths,
+                         **e})
+    eps64 = 1e-6
+    e = errors(*S.bump_greeks_fp64(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sample, opt.seed, eps64))
+    timed = 1 << 16
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+    S.bump_greeks_fp64(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, timed, opt.seed, eps64)
+    ms = ev0.elapsed_time(ev1) * opt.n_paths / timed
+    variants.append({"name": f"binary64 paths, eps={eps64:g} (spot bump eps*S0)", "ms_full": ms,
+                     "timed_paths": timed, "ms_full_is": f"kernel time on {timed} paths x {opt.n_paths // timed} "
+                                                          "(linear in paths)", **e})
+    keys = ("delta_rel", "vega_max_abs_of_max")
+    ok = [v for v in variants if all(v[k] <= adjoint_err[k] for k in keys)]
+    best = min(ok, key=lambda v: v["ms_full"]) if ok else None
+    return {"sample": f"first {sample} paths", "adjoint": {k: adjoint_err[k] for k in keys},
+            "variants": variants, "cheapest_at_adjoint_accuracy": best["name"] if best else None,
+            "speedup_vs_adjoint_kernel": best["ms_full"] / kern_ms if best else None}
+
+
+def large_record(lib, dev, peaks, n_sm, mhz, reps=3):
+    """The 100 x 100 grid, 1,260 steps, 2^26 paths (the largest single-GPU
+    configuration): device time, e2e through the host API, roofline and the
+    oracle on a sample, at the tuned launch shape (k = 4) and, for the
+    configured checkpoint interval, at k = 32."""
+    import torch
+
+    from paper_2002_02481_gb300 import lv
+
+    import oracle
+    surf, opt = W.config_large()
+    S = lv.Surface.from_workload(surf, lib)
+    stream = torch.cuda.current_stream(dev)
+    S.set_stream(stream.cuda_stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for e in ev:
+        e.record(stream)
+    torch.cuda.synchronize(dev)
+    d = torch.zeros(3 + S.IJ, dtype=torch.float64, device=dev)
+    res = {"workload": "100x100 local-vol grid, 1260 steps, 2^26 paths, European call K=100 T=5, "
+                       "price+delta+10000 vegas", "metric": METRIC, "unit": "path-steps/s"}
+    ps = opt.n_paths * opt.n_steps
+    for k in (4, 32):
+        S.set_launch(128, k, 0)
+        S.set_kernel_events(ev[2].cuda_event, ev[3].cuda_event)
+        S.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, d.data_ptr())
+        step_ms, kern_ms = [], []
+        for _ in range(reps):
+            ev[0].record(stream)
+            S.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, d.data_ptr())
+            ev[1].record(stream)
+            ev[1].synchronize()
+            step_ms.append(ev[0].elapsed_time(ev[1]))
+            kern_ms.append(ev[2].elapsed_time(ev[3]))
+        ms = statistics.median(step_ms)
+        res[f"k={k}"] = {"ms_per_step": ms, "value": ps / (ms * 1e-3), "kernel_ms": statistics.median(kern_ms)}
+    S.set_launch(128, 4, 0)
+    res["launch"] = {"block": 128, "k": 4, "source": "tuned (k=4 fastest of 4, 8, 16); k=32 is the configured "
+                                                     "interval, reported beside it"}
+    res["value"] = res["k=4"]["value"]
+    res["ms_per_step"] = res["k=4"]["ms_per_step"]
+    live = live_fraction(S, opt, 1 << 14)
+    res["roofline"] = roofline_block(res["k=4"]["kernel_ms"], ps, live, peaks, mhz, n_sm, None)
+    # end to end through the host API: sigma from pinned host memory, results to host memory
+    sig_host = torch.from_numpy(np.ascontiguousarray(surf.sigma)).pin_memory().numpy()
+    S.set_kernel_events(0, 0)
+    S.set_sigma(sig_host)
+    S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        S.set_sigma(sig_host)
+        S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    e2e_s = (time.perf_counter() - t0) / reps
+    res["e2e"] = {"value": ps / e2e_s, "unit": "path-steps/s", "h2d_bytes_per_step": int(sig_host.nbytes),
+                  "d2h_bytes_per_step": int(8 * (3 + S.IJ)), "ms_per_step": e2e_s * 1e3}
+    threads = oracle.default_threads()
+    sample = 1 << 14
+    t0 = time.perf_counter()
+    oracle.run_sums(surf, W.Option(**{**opt.__dict__, "n_paths": sample}), 0, sample, greeks=True, n_threads=threads)
+    cpu_s = time.perf_counter() - t0
+    res["cpu_baseline"] = {"value": sample * opt.n_steps / cpu_s, "unit": "path-steps/s", "cores": threads,
+                           "kind": "oracle", "sample": f"first {sample} of the 2^26 paths, 1260 steps, price+delta+"
+                           f"10000 vegas; extrapolated linearly in paths ({cpu_model()})"}
+    S.close()
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
 
     from paper_2002_02481_gb300 import lv
+    from paper_2002_02481_gb300.shard import price_greeks_sharded
 
     ws, rk, lr = dist_env()
     if ws > 1:
@@ -303,14 +464,19 @@ def run_ours(args):
     lib = lv.load()
     surf, opt = W.config_paper_shape()
     P = opt.n_paths                       # per rank (weak scaling)
-    first_path = rk * P
     S = lv.Surface.from_workload(surf, lib)
     stream = torch.cuda.current_stream(dev)
     S.set_stream(stream.cuda_stream)
-    # launch shape from the project's autotuner, on this workload
-    tuned = S.tune(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
+    # launch shape from the project's autotuner, on this workload (or fixed by --launch)
+    if args.launch:
+        blk, kk = (int(v) for v in args.launch.split(","))
+        S.set_launch(blk, kk, 0)
+        tuned = (blk, kk, None)
+    else:
+        tuned = S.tune(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
     n_out = 3 + surf.n_spot * surf.n_time
     d_out = torch.zeros(n_out, dtype=torch.float64, device=dev)
+    d_sums = torch.zeros(n_out, dtype=torch.float64, device=dev)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)      # torch creates the underlying CUDA events on first record
@@ -324,8 +490,10 @@ def run_ours(args):
         if ws == 1:
             S.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed, d_out.data_ptr())
         else:
-            S.price_greeks_sums_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, first_path,
-                                       first_path + P, opt.seed, 0, d_out.data_ptr())
+            # this rank's 2^20 paths of one ws x 2^20-path estimate: the adjoint on the
+            # range, one all-reduce of the raw sums, the finalize
+            price_greeks_sharded(S, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, ws * P, opt.seed, device=dev,
+                                 sums=d_sums, out=d_out)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -342,6 +510,8 @@ def run_ours(args):
         while time.perf_counter() < t_end:
             step()
             torch.cuda.synchronize(dev)
+        if ws > 1:
+            dist.barrier()
         # the steps are queued without a host wait between them, so the host is
         # ahead of the device and every s0 -> s1 interval is device work only
         # (one event pair per step for the step and one for the adjoint kernel)
@@ -377,13 +547,14 @@ def run_ours(args):
         S.price(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
         fwd_ms.append(ev0.elapsed_time(ev1))
     bump = None
+    bump32_ms = None
     if rk == 0 and not args.no_bump:
         pa, da, va = S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
         flush.fill_(1)
         pb, db, vb = S.bump_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed, 1e-4)
-        bump_ms = ev0.elapsed_time(ev1)
-        bump = {"ms": bump_ms, "scenarios": 3 + 2 * surf.n_spot * surf.n_time, "eps": 1e-4,
-                "speedup_vs_adjoint_kernel": bump_ms / statistics.mean(kern_ms),
+        bump32_ms = ev0.elapsed_time(ev1)
+        bump = {"ms": bump32_ms, "scenarios": 3 + 2 * surf.n_spot * surf.n_time, "eps": 1e-4,
+                "speedup_vs_adjoint_kernel": bump32_ms / statistics.mean(kern_ms),
                 "max_vega_diff_vs_adjoint_of_max": float(np.max(np.abs(vb - va)) / np.max(np.abs(va))),
                 "delta_diff_vs_adjoint_rel": abs(db - da) / abs(da)}
 
@@ -407,26 +578,27 @@ def run_ours(args):
                "h2d_bytes_per_step": int(sig_np.nbytes), "d2h_bytes_per_step": int(8 * n_out),
                "ms_per_step": e2e_s * 1e3}
 
-    workloads = None
-    if rk == 0 and not args.no_extra:
-        S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
-        workloads = other_workloads(lib, dev, ev0, ev1)
-
     if rk == 0:
-        peaks, src = load_peaks()
+        peaks_file, src = load_peaks()
         clocks = clk.summary()
         kern = statistics.mean(kern_ms)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-        peak_gops = n_sm * LANES_PER_SM_CLOCK * mhz * 1e6 / 1e9
-        achieved = ALG_OPS_PER_PATH_STEP * P * opt.n_steps / (kern * 1e-3) / 1e9
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_gops, "unit": "Gop/s",
-                    "frac": achieved / peak_gops, "traffic": profiled_traffic(),
-                    "kernel": "adjoint_kernel<k=%d,binary64 level 2> (block %d, %d blocks/SM)" % (
-                        S.get_launch(opt.n_steps, True)[1], S.get_launch(opt.n_steps, True)[0],
-                        S.get_launch(opt.n_steps, True)[2]), "kernel_ms": kern,
-                    "peak_source": f"{n_sm} SMs x {LANES_PER_SM_CLOCK} lanes/clk x median SM clock "
-                                   f"{mhz:.0f} MHz under load ({src} clocks)"}
+        mhz = clocks["sm_mhz"] or peaks_file.get("sm_max_mhz", 2070.0)
+        try:
+            pipe_peaks = lv.measure_pipe_peaks(lib)
+        except lv.LVError:
+            pipe_peaks = None
+        live = live_fraction(S, opt)
+        roofline = roofline_block(kern, P * opt.n_steps, live, pipe_peaks, mhz, n_sm, profiled_record())
+        blk, kk, bps = S.get_launch(opt.n_steps, True)
+        roofline["kernel"] = f"adjoint_kernel<k={kk},binary64 level 2> (block {blk}, {bps} blocks/SM)"
+        roofline["clock_mhz"] = mhz
+        workloads = None
+        if not args.no_extra:
+            S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+            workloads = other_workloads(lib, dev, ev0, ev1)
+        large = None if args.no_large else large_record(lib, dev, pipe_peaks, n_sm, mhz)
+        S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
         import oracle
         threads = oracle.default_threads()
         sample = 1 << 13
@@ -445,24 +617,30 @@ def run_ours(args):
             return {"price_rel": abs(p_ - ref["price"]) / abs(ref["price"]),
                     "delta_rel": abs(d_ - ref["delta"]) / abs(ref["delta"]),
                     "vega_max_abs_of_max": float(np.max(np.abs(v_ - ref["vega"]))) / vmax}
+        adj_err = errors(*S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sample, opt.seed))
         accuracy = {"sample": f"first {sample} of the 2^20 paths", "reference": "FP64 oracle, pathwise adjoint",
-                    "adjoint": errors(*S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sample, opt.seed))}
+                    "adjoint": adj_err}
         if not args.no_bump:
             accuracy["bump_eps_1e-4"] = errors(*S.bump_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sample,
                                                               opt.seed, 1e-4))
+            bump["equal_accuracy"] = equal_accuracy_bump(S, opt, errors, adj_err, kern, bump32_ms, sample)
         line = {
             "metric": METRIC, "value": value, "unit": "path-steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "30x60", "n_steps": opt.n_steps, "n_paths_per_gpu": P,
-                       "launch": {"block": tuned[0], "k": tuned[1], "source": "lv_tune"},
+                       "launch": {"block": tuned[0], "k": tuned[1],
+                                  "source": "--launch" if args.launch else "lv_tune"},
                        "l2": "256 MB buffer rewritten between timed steps (outside the timed region)",
-                       "parallelism": f"path-range shards x{ws}"},
-            "clocks": clocks, "gpu_launches": 3 * args.steps, "roofline": roofline,
+                       "parallelism": f"path-range shards x{ws}" + (", one all-reduce of 3+1800 sums per step"
+                                                                     if ws > 1 else "")},
+            "clocks": clocks, "gpu_launches": (3 if ws == 1 else 4) * args.steps, "roofline": roofline,
+            "pipe_peaks_gops": {k: v / 1e9 for k, v in pipe_peaks.items()} if pipe_peaks else None,
             "cpu_baseline": cpu, "accuracy": accuracy, "e2e": e2e,
             "forward_only": {"kernel_ms": statistics.mean(fwd_ms),
                              "value": P * opt.n_steps / (statistics.mean(fwd_ms) * 1e-3), "unit": "path-steps/s"},
             "bump_reprice": bump,
+            "large": large,
             "workloads": workloads,
         }
         print(json.dumps(line), flush=True)
@@ -472,34 +650,58 @@ def run_ours(args):
 
 
 def precision_study():
-    """Config-3 study: FP32 paths with binary64 or Kahan binary32 level-2
-    accumulation, against the FP64 oracle over the same 2^24 paths (seed 1),
-    error stated per output. Prints one JSON line."""
+    """Config-3 study: binary32 paths with binary64 or Kahan binary32 level-2
+    accumulation, each output's error stated against (a) the FP64 oracle on
+    the first 2^18 paths (same counters) and (b) the full-FP64 GPU run
+    (lv_price_greeks_fp64_device) over all 2^24 paths, on both config-3
+    grids (reading C9). Prints one JSON line."""
     import torch
 
     import oracle
     from paper_2002_02481_gb300 import lv
 
     lib = lv.load()
-    out = {"study": "precision", "paths": 1 << 24, "n_steps": 156, "reference": "FP64 CPU oracle, same paths"}
+    sub = 1 << 18
+
+    def errs(p, d, v, rp, rd, rv):
+        vm = float(np.max(np.abs(rv)))
+        return {"price_rel": abs(p - rp) / abs(rp), "delta_rel": abs(d - rd) / abs(rd),
+                "vega_max_abs_err_of_max": float(np.max(np.abs(v - rv))) / vm,
+                "vega_rms_err_of_max": float(np.sqrt(np.mean((v - rv) ** 2))) / vm}
+
+    out = {"study": "precision", "paths": 1 << 24, "oracle_paths": sub, "n_steps": 156,
+           "references": {"oracle": "FP64 CPU oracle on the first 2^18 paths (same counters)",
+                          "fp64_gpu": "lv_price_greeks_fp64_device, every path in binary64, all 2^24 paths"}}
     for which in ("small", "paper"):
         surf, opt = W.config_precision(which)
+        o_sub = W.Option(**{**opt.__dict__, "n_paths": sub})
         t0 = time.perf_counter()
-        ref = oracle.price_greeks(surf, opt)
-        cpu_s = time.perf_counter() - t0
-        row = {"oracle_s": cpu_s, "oracle_threads": oracle.default_threads()}
+        ref = oracle.price_greeks(surf, o_sub)
+        row = {"oracle_s": time.perf_counter() - t0, "oracle_threads": oracle.default_threads()}
+        S = lv.Surface.from_workload(surf, lib)
+        d = torch.zeros(3 + S.IJ, dtype=torch.float64, device="cuda")
+
+        def fp64(n):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            S.price_greeks_fp64_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, n, opt.seed, d.data_ptr())
+            torch.cuda.synchronize()
+            o = d.cpu().numpy()
+            return o[0], o[1], o[3:].reshape(surf.n_spot, surf.n_time), time.perf_counter() - t
+
+        p64s, d64s, v64s, _ = fp64(sub)
+        row["fp64_gpu_vs_oracle_2^18"] = errs(p64s, d64s, v64s, ref["price"], ref["delta"], ref["vega"])
+        p64, d64, v64, t64 = fp64(opt.n_paths)
+        row["fp64_gpu_s"] = t64
         for acc, nm in ((0, "binary64"), (1, "Kahan")):
-            S = lv.Surface.from_workload(surf, lib)
             S.set_accumulation(acc)
-            p, d, v = S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
-            S.close()
-            vm = float(np.max(np.abs(ref["vega"])))
-            row[nm] = {"price_rel": abs(p - ref["price"]) / abs(ref["price"]),
-                       "delta_rel": abs(d - ref["delta"]) / abs(ref["delta"]),
-                       "vega_max_abs_err_of_max": float(np.max(np.abs(v - ref["vega"]))) / vm,
-                       "vega_rms_err_of_max": float(np.sqrt(np.mean((v - ref["vega"]) ** 2))) / vm,
-                       "price": p, "delta": d}
-        row["oracle"] = {"price": ref["price"], "delta": ref["delta"], "stderr": ref["stderr"]}
+            pf, df, vf = S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+            ps, ds, vs = S.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, sub, opt.seed)
+            row[nm] = {"vs_oracle_2^18": errs(ps, ds, vs, ref["price"], ref["delta"], ref["vega"]),
+                       "vs_fp64_gpu_2^24": errs(pf, df, vf, p64, d64, v64), "price": pf, "delta": df}
+        S.close()
+        row["fp64_gpu_2^24"] = {"price": p64, "delta": d64}
+        row["oracle_2^18"] = {"price": ref["price"], "delta": ref["delta"], "stderr": ref["stderr"]}
         out[f"{which} grid {surf.n_spot}x{surf.n_time}"] = row
     print(json.dumps(out), flush=True)
     return 0
@@ -551,6 +753,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-bump", action="store_true", help="skip the bump-and-reprice timing")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
+    ap.add_argument("--no-large", action="store_true", help="skip the 100x100 / 1260-step / 2^26-path record")
+    ap.add_argument("--launch", default="", help="fix the adjoint's launch shape as BLOCK,K instead of tuning it")
     ap.add_argument("--precision-study", action="store_true",
                     help="2^24-path precision workloads: binary64 vs Kahan level 2 against the FP64 oracle")
     ap.add_argument("--path-sweep", action="store_true",

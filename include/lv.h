@@ -252,6 +252,58 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
                          int32_t n_steps, int64_t n_paths, uint64_t seed, double eps,
                          double* out_price, double* out_delta, double* out_vega);
 
+/* Measured issue rates of the SM pipes the Monte Carlo path is bound by
+ * (it reads almost nothing from memory: its roofline is arithmetic, not
+ * HBM), the denominators of its roofline fractions. lv_measure_pipe_peaks
+ * runs one probe kernel per entry on the current device (eight independent
+ * chains of that instruction per thread, 8 blocks of 256 threads per SM,
+ * best of three runs timed with CUDA events) and writes
+ * out_ops_per_s[LV_PIPE_COUNT]: thread-instructions per second over the
+ * whole GPU at the clock the probes ran at. Synchronous; about 50 ms. */
+enum {
+    LV_PIPE_FFMA = 0,       /* fma.rn.f32 */
+    LV_PIPE_MUFU_EX2 = 1,   /* ex2.approx.ftz.f32 */
+    LV_PIPE_MUFU_LG2 = 2,   /* lg2.approx.ftz.f32 */
+    LV_PIPE_MUFU_SIN = 3,   /* sin.approx.ftz.f32 */
+    LV_PIPE_MUFU_COS = 4,   /* cos.approx.ftz.f32 */
+    LV_PIPE_MUFU_SQRT = 5,  /* sqrt.approx.ftz.f32 */
+    LV_PIPE_IMAD = 6,       /* mad.lo.u32 */
+    LV_PIPE_IMAD_WIDE = 7,  /* mad.wide.u32 (the Philox product) */
+    LV_PIPE_LOP3 = 8,       /* lop3.b32 */
+    LV_PIPE_IADD = 9,       /* add.u32 */
+    LV_PIPE_COUNT = 10
+};
+lv_status lv_measure_pipe_peaks(double* out_ops_per_s);
+
+/* lv_price_greeks_fp64_device -- the same outputs as lv_price_greeks_device
+ * (layout LV_OUT_*, device memory owned by the caller, on the handle's
+ * stream, not synchronised) with every path in binary64: the full-FP64
+ * reference against which the binary32 path's rounding is measured on the
+ * GPU (the precision study of Sec. IV-C's mixed-precision reading). Same
+ * random numbers (the uniforms are exact in binary64), the same model and
+ * decisions as the FP64 definition, the adjoint in its tangent-ratio form
+ * (see LV_ADJ_TANGENT) with binary64 sums; CUDA's binary64 exp, log, sqrt
+ * and sincospi. Binary64 arithmetic runs at a small fraction of the binary32
+ * rate on this part: a reference, not a fast path. Main reading only
+ * (LV_INTERP_S, LV_SCHEME_LOG; else LV_EINVAL); ignores lv_set_launch,
+ * lv_set_accumulation and lv_set_adjoint_method. A live path with
+ * |1 + g_n| < 2^-40 makes every output NaN, as in LV_ADJ_TANGENT.
+ * n_paths in [1, 2^48). */
+lv_status lv_price_greeks_fp64_device(lv_surface_t h, double S0, double r, double K, double T,
+                                      int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out);
+
+/* lv_bump_greeks_fp64 -- lv_bump_greeks (Sec. III: central differences,
+ * sigma_ij +- eps/2 and S0 +- eps_S/2, common random numbers) with every
+ * bumped path in binary64, so that the differences carry no binary32
+ * rounding noise: the bump baseline at the accuracy of the adjoint. The
+ * spot bump scales with eps here, eps_S = eps S0 (binary64 differences
+ * allow bumps far below the binary32 baseline's fixed 1e-4 S0). Outputs as in lv_bump_greeks (host memory, synchronous).
+ * Main reading only (else LV_EINVAL); eps > 0, finite; n_paths in
+ * [1, 2^48). */
+lv_status lv_bump_greeks_fp64(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                              int64_t n_paths, uint64_t seed, double eps, double* out_price, double* out_delta,
+                              double* out_vega);
+
 /* Per-path diagnostics for paths [path_begin, path_begin + m), m <= 2^26,
  * of RNG stream stream_id (< 65536, as in lv_price_greeks_sums_device):
  * terminal log-spot x_N, discounted payoff V and d V / d x_0, each [m]

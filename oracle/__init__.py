@@ -25,6 +25,7 @@ _HDR = os.path.join(_HERE, "lv_oracle.h")
 _LIB = os.path.join(_HERE, "_build", "liblv_oracle.so")
 
 NSCAL = 13
+VN_DELTA, VN_DELTA_2, VN_TOT, VN_TOT_2, VN_TINY, VN_NSCAL = 0, 1, 2, 3, 4, 5
 (SUM_V, SUM_V2, SUM_XBAR0, SUM_XBAR0_2, SUM_VTOT, SUM_VTOT_2, SUM_SN, KINK_COUNT, KINK_XBAR0,
  SUM_RHO, SUM_RHO_2, SUM_DVDT, SUM_DVDT_2) = range(13)
 
@@ -102,7 +103,8 @@ class Decisions:
 class _Point(ctypes.Structure):
     _fields_ = [("i", ctypes.c_int32), ("j", ctypes.c_int32), ("u", ctypes.c_double),
                 ("v", ctypes.c_double), ("w", ctypes.c_double * 4),
-                ("sigma", ctypes.c_double), ("dsigma_dS", ctypes.c_double), ("dsigma_dt", ctypes.c_double)]
+                ("sigma", ctypes.c_double), ("dsigma_dS", ctypes.c_double), ("dsigma_dt", ctypes.c_double),
+                ("inside", ctypes.c_int32), ("du_dS", ctypes.c_double)]
 
 
 def build(src: str = _SRC, out: str = _LIB, extra: tuple = ()) -> str:
@@ -165,6 +167,9 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.orc_bump.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_double, ctypes.c_double,
                              ctypes.c_int32, f64p, f64p]
     lib.orc_bump.restype = ctypes.c_int
+    lib.orc_run_vanna.argtypes = [P(_Surface), P(_Option), ctypes.c_int64, ctypes.c_int64, P(_Decisions),
+                                  ctypes.c_int32, f64p]
+    lib.orc_run_vanna.restype = ctypes.c_int
     return lib
 
 
@@ -241,7 +246,7 @@ def sigma_eval(surface, S: float, t: float, lib=None) -> dict:
     p = _Point()
     lib.orc_sigma_eval(ctypes.byref(a.surf), float(S), float(t), ctypes.byref(p))
     return dict(i=p.i, j=p.j, u=p.u, v=p.v, w=list(p.w), sigma=p.sigma, dsigma_dS=p.dsigma_dS,
-                dsigma_dt=p.dsigma_dt)
+                dsigma_dt=p.dsigma_dt, inside=bool(p.inside), du_dS=p.du_dS)
 
 
 def run_sums(surface, opt, path_begin: int = 0, path_end: Optional[int] = None,
@@ -309,3 +314,30 @@ def bump(surface, opt, eps_sigma: float, eps_S0: float, n_paths: Optional[int] =
                         float(eps_sigma), float(eps_S0), int(n_threads or default_threads()),
                         _ptr(vega), ctypes.byref(delta)), "bump")
     return vega.reshape(surface.n_spot, surface.n_time), delta.value
+
+
+def run_vanna(surface, opt, path_begin: int = 0, path_end: Optional[int] = None,
+              n_threads: Optional[int] = None, lib=None, decisions: Optional[Decisions] = None) -> dict:
+    """Second-order buckets d^2 price / (d S0 d sigma_ij) over paths
+    [path_begin, path_end) (lv_oracle.c, orc_run_vanna): dict with the raw
+    sums and the estimates: 'delta', 'vanna' [I, J], 'vanna_se' [I, J],
+    'total' (sum over buckets) and 'total_se'."""
+    lib = lib or load_library()
+    a = _args(surface, opt)
+    if path_end is None:
+        path_end = opt.n_paths
+    out = np.zeros(VN_NSCAL + 2 * a.IJ, dtype=np.float64)
+    st = lib.orc_run_vanna(ctypes.byref(a.surf), ctypes.byref(a.opt), int(path_begin), int(path_end),
+                           ctypes.byref(decisions.c) if decisions is not None else None,
+                           int(n_threads or default_threads()), _ptr(out))
+    _check(st, "run_vanna")
+    P = max(int(path_end - path_begin), 1)
+    I, J = surface.n_spot, surface.n_time
+    vs = out[VN_NSCAL:VN_NSCAL + a.IJ]
+    vq = out[VN_NSCAL + a.IJ:]
+    mean = vs / P
+    se = np.sqrt(np.maximum(vq / P - mean * mean, 0.0) / max(P - 1, 1))
+    tot = out[VN_TOT] / P
+    tot_se = np.sqrt(max(out[VN_TOT_2] / P - tot * tot, 0.0) / max(P - 1, 1))
+    return dict(sums=out, delta=out[VN_DELTA] / P, vanna=mean.reshape(I, J), vanna_se=se.reshape(I, J),
+                total=tot, total_se=tot_se, tiny=int(out[VN_TINY]))

@@ -196,6 +196,8 @@ static void orc_sigma_in_cell(const orc_surface* sf, double S, double t, int32_t
     p->w[2] = (1.0 - u) * v;           /* node (i,   j+1) */
     p->w[3] = u * v;                   /* node (i+1, j+1) */
     p->sigma = p->w[0] * s00 + p->w[1] * s10 + p->w[2] * s01 + p->w[3] * s11;
+    p->inside = inside;
+    p->du_dS = inside ? du_dS : 0.0;
     if (inside)
         p->dsigma_dS = ((1.0 - v) * (s10 - s00) + v * (s11 - s01)) * du_dS;
     else
@@ -761,5 +763,209 @@ int orc_bump(const orc_surface* sf, const orc_option* op, int64_t n_paths, doubl
         *out_delta = (up - dn) / (P * eps_S0);
     }
     free(bumped);
+    return st;
+}
+
+/* ------------------------------------------------ second-order buckets */
+
+/* Vanna buckets d^2 price / (d S0 d sigma_ij): the derivative of the delta
+ * with respect to every grid value, an extension of the first-order Greeks
+ * of Sec. V. The pathwise estimator of the delta,
+ *   Delta_p = e^{-rT} 1{phi (S_N - K) > 0} phi S_N D_N / S0,
+ *   D_N = prod_n (1 + g_n), g_n = h_n k_n, h_n = sqrt(dt) Z_n - sigma_n dt,
+ *   k_n = S_n d sigma / d S (S_n, t_n),
+ * is unbiased for the delta, but it jumps where S_N crosses the strike and
+ * where a spot crosses a node (d sigma / d S changes cell there), so its own
+ * pathwise derivative in sigma_ij would miss those jumps. Written as an
+ * integral over the path x = (x_0 .. x_N) against the density p(x) of the
+ * Euler chain, E[Delta_p] = int Delta_p(x; sigma) p(x; sigma) dx, and with
+ * the path held fixed the indicator and every cell are fixed, so
+ *   vanna_ij = E[ d Delta_p / d sigma_ij |_x + Delta_p d ln p(x) / d sigma_ij ].
+ * Per step, with w_ij(n) node ij's bilinear weight and at fixed x
+ *   d sigma_n / d sigma_ij = w_ij(n),
+ *   d k_n / d sigma_ij = S_n d w_ij / d S (n) (inside the grid, else 0),
+ *   d h_n / d sigma_n = -sqrt(dt) Z_n / sigma_n
+ *     (h_n = (x_{n+1} - x_n - r dt) / sigma_n - sigma_n dt / 2 at fixed x),
+ *   d ln p_n / d sigma_n = (Z_n^2 - 1) / sigma_n - sqrt(dt) Z_n
+ *     (the Gaussian step, mean x_n + (r - sigma_n^2/2) dt, sd sigma_n sqrt(dt)),
+ * so path p adds to bucket ij
+ *   Delta_p sum_n [ w_ij(n) a_n + S_n d w_ij / d S (n) b_n ],
+ *   a_n = (Z_n^2 - 1) / sigma_n - sqrt(dt) Z_n (1 + k_n / (sigma_n (1 + g_n))),
+ *   b_n = h_n / (1 + g_n). */
+static int orc_vanna_path(const orc_surface* sf, const orc_option* op, uint64_t path, orc_workspace* ws,
+                          const orc_decisions* dec, double* vsum, double* vsq, double* pv, int32_t* touched,
+                          double* scal, int64_t ov[2])
+{
+    const int32_t N = op->n_steps, J = sf->n_time;
+    const double dt = op->T / (double)N;
+    const double sqdt = sqrt(dt);
+    double* x = ws->x;
+    double* z = ws->z;
+    orc_point pt;
+    orc_normals(op->seed, op->stream_id, path, N, z);
+    int64_t c_first, c_last;
+    orc_cell_range(dec, path, &c_first, &c_last);
+    const double band = dec ? dec->band : 0.0;
+    int overridden, st;
+
+    /* the path and D_N */
+    x[0] = log(op->S0);
+    double D = 1.0;
+    int tiny = 0;
+    for (int32_t n = 0; n < N; ++n) {
+        const double t = (double)n * dt, S = exp(x[n]);
+        st = orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), band, &pt, &overridden);
+        if (st != ORC_OK) return st;
+        ov[0] += overridden;
+        const double h = sqdt * z[n] - pt.sigma * dt;
+        const double f = 1.0 + h * S * pt.dsigma_dS;
+        if (fabs(f) < 0x1p-40) tiny = 1;
+        D = D * f;
+        x[n + 1] = x[n] + (op->r - 0.5 * pt.sigma * pt.sigma) * dt + pt.sigma * sqdt * z[n];
+    }
+    const double SN = exp(x[N]);
+    const double itm = (double)op->phi * (SN - op->K);
+    const int forced = orc_forced_itm(dec, path);
+    const int own_itm = itm > 0.0;
+    if (forced >= 0 && forced != own_itm) {
+        if (!(fabs(SN - op->K) <= band * op->K)) return ORC_EDECISION;
+        ov[1] += 1;
+    }
+    const int in_money = forced >= 0 ? forced : own_itm;
+    const double delta = in_money ? exp(-op->r * op->T) * (double)op->phi * SN * D / op->S0 : 0.0;
+    scal[ORC_VN_DELTA] += delta;
+    scal[ORC_VN_DELTA_2] += delta * delta;
+    if (delta == 0.0) return ORC_OK;
+    if (tiny) {
+        scal[ORC_VN_TINY] += 1.0;
+        return ORC_OK;
+    }
+    /* the path's bucket values, then their sums and squares */
+    int32_t n_touched = 0;
+    double tot = 0.0;
+    for (int32_t n = 0; n < N; ++n) {
+        const double t = (double)n * dt, S = exp(x[n]);
+        st = orc_sigma_decided(sf, S, t, orc_forced_cell(dec, c_first, c_last, n), band, &pt, &overridden);
+        if (st != ORC_OK) return st;
+        const double kappa = S * pt.dsigma_dS;
+        const double h = sqdt * z[n] - pt.sigma * dt;
+        const double f = 1.0 + h * kappa;
+        const double a = (z[n] * z[n] - 1.0) / pt.sigma - sqdt * z[n] * (1.0 + kappa / (pt.sigma * f));
+        const double b = h / f;
+        /* d w / d S of the corners (i, j), (i+1, j), (i, j+1), (i+1, j+1) */
+        const double v = pt.v;
+        const double dw[4] = { -(1.0 - v) * pt.du_dS, (1.0 - v) * pt.du_dS, -v * pt.du_dS, v * pt.du_dS };
+        const int32_t nodes[4] = { pt.i * J + pt.j, (pt.i + 1) * J + pt.j, pt.i * J + pt.j + 1,
+                                   (pt.i + 1) * J + pt.j + 1 };
+        const int n_corners = (J > 1) ? 4 : 2;
+        for (int c = 0; c < n_corners; ++c) {
+            const double contrib = delta * (pt.w[c] * a + S * dw[c] * b);
+            if (pv[nodes[c]] == 0.0 && contrib != 0.0) touched[n_touched++] = nodes[c];
+            pv[nodes[c]] += contrib;
+            tot += contrib;
+        }
+    }
+    for (int32_t e = 0; e < n_touched; ++e) {
+        const int32_t node = touched[e];
+        vsum[node] += pv[node];
+        vsq[node] += pv[node] * pv[node];
+        pv[node] = 0.0;
+    }
+    scal[ORC_VN_TOT] += tot;
+    scal[ORC_VN_TOT_2] += tot * tot;
+    return ORC_OK;
+}
+
+typedef struct {
+    const orc_surface* sf;
+    const orc_option* op;
+    const orc_decisions* dec;
+    int64_t begin, end;
+    double* out;       /* ORC_VN_NSCAL + 2 I J */
+    int64_t ov[2];
+    int status;
+} orc_vanna_job;
+
+static void* orc_vanna_job_run(void* arg)
+{
+    orc_vanna_job* jb = (orc_vanna_job*)arg;
+    const int64_t IJ = (int64_t)jb->sf->n_spot * jb->sf->n_time;
+    orc_workspace ws;
+    ws.x = (double*)malloc(sizeof(double) * (size_t)(jb->op->n_steps + 1));
+    ws.z = (double*)malloc(sizeof(double) * (size_t)jb->op->n_steps);
+    double* pv = (double*)calloc((size_t)IJ, sizeof(double));
+    /* a path touches at most 4 nodes a step; a node may be counted more than once
+     * only when its running value returned to exactly 0 */
+    int32_t* touched = (int32_t*)malloc(sizeof(int32_t) * (size_t)(4 * jb->op->n_steps + IJ));
+    if (!ws.x || !ws.z || !pv || !touched) {
+        free(ws.x); free(ws.z); free(pv); free(touched);
+        jb->status = ORC_ENOMEM;
+        return NULL;
+    }
+    jb->status = ORC_OK;
+    for (int64_t p = jb->begin; p < jb->end; ++p) {
+        const int st = orc_vanna_path(jb->sf, jb->op, (uint64_t)p, &ws, jb->dec, jb->out + ORC_VN_NSCAL,
+                                      jb->out + ORC_VN_NSCAL + IJ, pv, touched, jb->out, jb->ov);
+        if (st != ORC_OK) {
+            jb->status = st;
+            break;
+        }
+    }
+    free(ws.x); free(ws.z); free(pv); free(touched);
+    return NULL;
+}
+
+int orc_run_vanna(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
+                  const orc_decisions* dec, int32_t n_threads, double* out)
+{
+    if (orc_check_decisions(dec) != ORC_OK) return ORC_EINVAL;
+    int st = orc_check(sf, op);
+    if (st != ORC_OK) return st;
+    if (sf->interp != ORC_INTERP_S || op->scheme != ORC_SCHEME_LOG) return ORC_EINVAL;
+    if (path_begin < 0 || path_end < path_begin || !out) return ORC_EINVAL;
+    const int64_t IJ = (int64_t)sf->n_spot * sf->n_time;
+    const int64_t width = ORC_VN_NSCAL + 2 * IJ;
+    memset(out, 0, sizeof(double) * (size_t)width);
+    const int64_t P = path_end - path_begin;
+    if (P == 0) return ORC_OK;
+    if (n_threads < 1) n_threads = 1;
+    if ((int64_t)n_threads > P) n_threads = (int32_t)P;
+    orc_vanna_job* jobs = (orc_vanna_job*)calloc((size_t)n_threads, sizeof(orc_vanna_job));
+    double* parts = (double*)calloc((size_t)(n_threads * width), sizeof(double));
+    pthread_t* th = (pthread_t*)calloc((size_t)n_threads, sizeof(pthread_t));
+    if (!jobs || !parts || !th) {
+        free(jobs); free(parts); free(th);
+        return ORC_ENOMEM;
+    }
+    for (int32_t k = 0; k < n_threads; ++k) {
+        jobs[k].sf = sf;
+        jobs[k].op = op;
+        jobs[k].dec = dec;
+        jobs[k].begin = path_begin + P * k / n_threads;
+        jobs[k].end = path_begin + P * (k + 1) / n_threads;
+        jobs[k].out = parts + (int64_t)k * width;
+        jobs[k].status = ORC_EINTERNAL;
+    }
+    int started = 0;
+    for (int32_t k = 1; k < n_threads; ++k) {
+        if (pthread_create(&th[k], NULL, orc_vanna_job_run, &jobs[k]) != 0) break;
+        started = k;
+    }
+    orc_vanna_job_run(&jobs[0]);
+    for (int32_t k = 1; k <= started; ++k) pthread_join(th[k], NULL);
+    for (int32_t k = started + 1; k < n_threads; ++k) orc_vanna_job_run(&jobs[k]);
+    st = ORC_OK;
+    int64_t ov[2] = { 0, 0 };
+    for (int32_t k = 0; k < n_threads; ++k) {     /* fixed order */
+        if (jobs[k].status != ORC_OK) st = jobs[k].status;
+        for (int64_t e = 0; e < width; ++e) out[e] += jobs[k].out[e];
+        ov[0] += jobs[k].ov[0];
+        ov[1] += jobs[k].ov[1];
+    }
+    if (dec && dec->out_overrides) {
+        dec->out_overrides[0] = ov[0];
+        dec->out_overrides[1] = ov[1];
+    }
+    free(jobs); free(parts); free(th);
     return st;
 }

@@ -67,6 +67,8 @@ typedef struct {
     double sigma;
     double dsigma_dS;
     double dsigma_dt;     /* 0 outside [t_0, t_{J-1}) and for one time node */
+    int32_t inside;       /* S in [s_0, s_{I-1}] (the weights then move with S) */
+    double du_dS;         /* d u / d S inside the grid, 0 outside */
 } orc_point;
 
 /* Decisions taken from outside for listed paths / steps (see lv_oracle.c):
@@ -112,6 +114,22 @@ int orc_paths_ex(const orc_surface* sf, const orc_option* op, int64_t path_begin
                  double* out_xbar0, double* out_amp);
 int orc_bump(const orc_surface* sf, const orc_option* op, int64_t n_paths, double eps_sigma,
              double eps_S0, int32_t n_threads, double* out_vega, double* out_delta);
+
+/* Second-order bucket sensitivities d^2 price / (d S0 d sigma_ij) (see
+ * lv_oracle.c), main reading only (ORC_INTERP_S, ORC_SCHEME_LOG; else
+ * ORC_EINVAL). out [ORC_VN_NSCAL + 2 I J]: the scalars below, then the sum
+ * over paths of each path's bucket value (spot-major), then the sum of
+ * their squares (standard errors). Decisions as in orc_run_ex. */
+enum {
+    ORC_VN_DELTA = 0,     /* sum of the pathwise delta Delta_p */
+    ORC_VN_DELTA_2 = 1,
+    ORC_VN_TOT = 2,       /* sum over paths of the path's sum over buckets */
+    ORC_VN_TOT_2 = 3,
+    ORC_VN_TINY = 4,      /* live paths with |1 + g_n| < 2^-40 (their values are not finite) */
+    ORC_VN_NSCAL = 5
+};
+int orc_run_vanna(const orc_surface* sf, const orc_option* op, int64_t path_begin, int64_t path_end,
+                  const orc_decisions* dec, int32_t n_threads, double* out);
 
 #ifdef __cplusplus
 }

@@ -151,6 +151,9 @@ void free_surface(lv_surface_s* h)
     cudaFree(h->d_ab);
     cudaFree(h->d_abl);
     cudaFree(h->d_tau);
+    cudaFree(h->d_spot64);
+    cudaFree(h->d_sig64);
+    cudaFreeHost(h->h_sig64_stage);
     cudaFree(h->d_scratch);
     cudaFree(h->d_res);
     cudaFreeHost(h->h_sig_stage);
@@ -509,6 +512,9 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
         cudaMalloc(&h->d_ab, sizeof(float2) * n_spot) != cudaSuccess ||
         cudaMalloc(&h->d_abl, sizeof(float2) * n_spot) != cudaSuccess ||
         cudaMalloc(&h->d_tau, sizeof(double) * n_time) != cudaSuccess ||
+        cudaMalloc(&h->d_spot64, sizeof(double) * n_spot) != cudaSuccess ||
+        cudaMalloc(&h->d_sig64, sizeof(double) * (size_t)n_spot * n_time) != cudaSuccess ||
+        cudaMallocHost(&h->h_sig64_stage, sizeof(double) * (size_t)n_spot * n_time) != cudaSuccess ||
         cudaMalloc(&h->d_res, sizeof(double) * nres) != cudaSuccess ||
         cudaMallocHost(&h->h_sig_stage, sizeof(float2) * nsig) != cudaSuccess ||
         cudaMallocHost(&h->h_res, sizeof(double) * nres) != cudaSuccess) {
@@ -534,7 +540,10 @@ lv_status lv_surface_create(const double* spot_nodes, int32_t n_spot, const doub
         cudaMemcpy(h->d_node, node.data(), sizeof(float) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_ab, ab.data(), sizeof(float2) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_abl, abl.data(), sizeof(float2) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(h->d_tau, time_nodes, sizeof(double) * n_time, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(h->d_tau, time_nodes, sizeof(double) * n_time, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_spot64, spot_nodes, sizeof(double) * n_spot, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(h->d_sig64, sigma, sizeof(double) * (size_t)n_spot * n_time, cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
         e = cudaGetLastError();
         return bail(LV_ECUDA, std::string("upload of the grid failed: ") + cudaGetErrorString(e));
     }
@@ -561,6 +570,9 @@ lv_status lv_surface_set_sigma(lv_surface_t h, const double* sigma)
     // the staging buffer may still feed an earlier asynchronous copy
     LV_CUDA(cudaStreamSynchronize(h->stream));
     pack_sigma(h, sigma, h->h_sig_stage);
+    std::memcpy(h->h_sig64_stage, sigma, sizeof(double) * (size_t)h->I * h->J);
+    LV_CUDA(cudaMemcpyAsync(h->d_sig64, h->h_sig64_stage, sizeof(double) * (size_t)h->I * h->J,
+                            cudaMemcpyHostToDevice, h->stream));
     LV_CUDA(cudaMemcpyAsync(h->d_sig, h->h_sig_stage, sizeof(float2) * (size_t)h->Je * (h->I - 1),
                             cudaMemcpyHostToDevice, h->stream));
     return LV_OK;
@@ -881,6 +893,155 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
     if (h->ev_end) LV_CUDA(cudaEventRecord(h->ev_end, h->stream));
     LV_CUDA(lv::launch_bump_finalize(B.partials, grid, row_words, reinterpret_cast<double*>(base + off_chunks),
                                      IJ, n_paths, eps, eps_S, h->d_res, B.mc.tile_counter, h->stream));
+    st = fetch_result(h);
+    if (st != LV_OK) return st;
+    *out_price = h->h_res[LV_OUT_PRICE];
+    *out_delta = h->h_res[LV_OUT_DELTA];
+    std::memcpy(out_vega, h->h_res + LV_OUT_VEGA, sizeof(double) * (size_t)IJ);
+    return LV_OK;
+}
+
+lv_status lv_measure_pipe_peaks(double* out_ops_per_s)
+{
+    if (!out_ops_per_s) return fail(LV_EINVAL, "NULL argument");
+    double tmp[LV_PIPE_COUNT] = {};
+    LV_CUDA(lv::measure_pipe_peaks(tmp));
+    std::memcpy(out_ops_per_s, tmp, sizeof tmp);
+    return LV_OK;
+}
+
+lv_status lv_price_greeks_fp64_device(lv_surface_t h, double S0, double r, double K, double T,
+                                      int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out)
+{
+    if (!h || !d_out) return fail(LV_EINVAL, "NULL argument");
+    lv_status st = check_option(S0, r, K, T, n_steps);
+    if (st != LV_OK) return st;
+    if (n_paths < 1 || n_paths > LV_MAX_PATH_INDEX) return fail(LV_EINVAL, "n_paths out of range");
+    if (h->interp != LV_INTERP_S || h->scheme != LV_SCHEME_LOG)
+        return fail(LV_EINVAL, "the binary64 reference runs the main reading (LV_INTERP_S, LV_SCHEME_LOG) only");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    const size_t smem = lv::adjoint64_smem_bytes(n_steps);
+    int bps = 0;
+    LV_CUDA(lv::f64_occupancy(false, smem, &bps));
+    if (bps < 1) return fail(LV_EINVAL, "binary64 launch does not fit on an SM");
+    const int64_t want = (n_paths + 127) / 128;
+    const int64_t slots = (int64_t)bps * h->num_sms;
+    const int grid = (int)(want < slots ? want : slots);
+    const int row_words = 3 + h->Je * h->I;
+    size_t o = 256;                                   // [0, 256): tile counter (unused), flag
+    const size_t off_part = o;
+    o = round_up(o + sizeof(double) * (size_t)grid * row_words, 256);
+    const size_t off_chunks = o;
+    o = round_up(o + sizeof(double) * (size_t)lv::finalize_chunks(grid) * row_words, 256);
+    st = ensure_scratch(h, o);
+    if (st != LV_OK) return st;
+    char* base = static_cast<char*>(h->d_scratch);
+    const double dt = T / (double)n_steps;
+    lv::F64Params P{};
+    P.spot = h->d_spot64;
+    P.sig = h->d_sig64;
+    P.tau = h->d_tau;
+    P.I = h->I;
+    P.J = h->J;
+    P.N = n_steps;
+    P.x0 = std::log(S0);
+    P.r = r;
+    P.dt = dt;
+    P.sqdt = std::sqrt(dt);
+    P.K = K;
+    P.disc = std::exp(-r * T);
+    P.phi = (double)h->phi;
+    P.k0 = (uint32_t)(seed & 0xffffffffu);
+    P.k1 = (uint32_t)(seed >> 32);
+    P.n_paths = n_paths;
+    P.partials = reinterpret_cast<double*>(base + off_part);
+    P.row_words = row_words;
+    P.flag = reinterpret_cast<unsigned int*>(base) + 1;    // zero; every finalize resets it
+    if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
+    LV_CUDA(lv::launch_adjoint64(P, grid, smem, h->stream));
+    if (h->ev_end) LV_CUDA(cudaEventRecord(h->ev_end, h->stream));
+    lv::FinalizeParams F{};
+    F.partials = P.partials;
+    F.G = grid;
+    F.row_words = row_words;
+    F.I = h->I;
+    F.J = h->J;
+    F.n_paths = n_paths;
+    F.S0 = S0;
+    F.chunks = reinterpret_cast<double*>(base + off_chunks);
+    F.out = d_out;
+    F.tile_counter = reinterpret_cast<unsigned int*>(base);
+    F.flag = P.flag;
+    LV_CUDA(lv::launch_finalize(F, h->stream));
+    return LV_OK;
+}
+
+lv_status lv_bump_greeks_fp64(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                              int64_t n_paths, uint64_t seed, double eps, double* out_price, double* out_delta,
+                              double* out_vega)
+{
+    if (!h || !out_price || !out_delta || !out_vega) return fail(LV_EINVAL, "NULL argument");
+    lv_status st = check_option(S0, r, K, T, n_steps);
+    if (st != LV_OK) return st;
+    if (!is_finite(eps) || !(eps > 0.0)) return fail(LV_EINVAL, "eps must be finite and > 0");
+    if (h->interp != LV_INTERP_S || h->scheme != LV_SCHEME_LOG)
+        return fail(LV_EINVAL, "the bump baseline runs the main reading (LV_INTERP_S, LV_SCHEME_LOG) only");
+    if (n_paths < 1 || n_paths > LV_MAX_PATH_INDEX) return fail(LV_EINVAL, "n_paths out of range");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    const int IJ = h->I * h->J;
+    const int row_words = 2 + IJ;
+    const int n_scen = 3 + 2 * IJ;
+    const int M = lv::bump64_slots_per_thread();
+    const size_t smem = lv::bump64_smem_bytes(n_steps, row_words);
+    if (smem > 200 * 1024) return fail(LV_EINVAL, "grid too large for the binary64 bump kernel's shared memory");
+    int bps = 0;
+    LV_CUDA(lv::f64_occupancy(true, smem, &bps));
+    if (bps < 1) return fail(LV_EINVAL, "binary64 bump launch does not fit on an SM");
+    const int64_t items = (n_paths + 127) / 128 * ((n_scen + M - 1) / M);
+    const int64_t slots = (int64_t)bps * h->num_sms;
+    const int grid = (int)(items < slots ? items : slots);
+    const int nch = lv::bump_chunks(grid);
+    size_t o = 256;
+    const size_t off_part = o;
+    o = round_up(o + sizeof(double) * (size_t)grid * row_words, 256);
+    const size_t off_chunks = o;
+    o = round_up(o + sizeof(double) * (size_t)nch * row_words, 256);
+    st = ensure_scratch(h, o);
+    if (st != LV_OK) return st;
+    char* base = static_cast<char*>(h->d_scratch);
+    const double dt = T / (double)n_steps;
+    const double eps_S = eps * S0;             // the spot bump of the same relative size
+    lv::F64Params P{};
+    P.spot = h->d_spot64;
+    P.sig = h->d_sig64;
+    P.tau = h->d_tau;
+    P.I = h->I;
+    P.J = h->J;
+    P.N = n_steps;
+    P.x0 = std::log(S0);
+    P.x0_up = std::log(S0 + 0.5 * eps_S);
+    P.x0_dn = std::log(S0 - 0.5 * eps_S);
+    P.r = r;
+    P.dt = dt;
+    P.sqdt = std::sqrt(dt);
+    P.K = K;
+    P.disc = std::exp(-r * T);
+    P.phi = (double)h->phi;
+    P.eps_half = 0.5 * eps;
+    P.k0 = (uint32_t)(seed & 0xffffffffu);
+    P.k1 = (uint32_t)(seed >> 32);
+    P.n_paths = n_paths;
+    P.partials = reinterpret_cast<double*>(base + off_part);
+    P.row_words = row_words;
+    P.n_scen = n_scen;
+    P.n_groups = (n_scen + M - 1) / M;
+    if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
+    LV_CUDA(lv::launch_bump64(P, grid, smem, h->stream));
+    if (h->ev_end) LV_CUDA(cudaEventRecord(h->ev_end, h->stream));
+    LV_CUDA(lv::launch_bump_finalize(P.partials, grid, row_words, reinterpret_cast<double*>(base + off_chunks), IJ,
+                                     n_paths, eps, eps_S, h->d_res, nullptr, h->stream));
     st = fetch_result(h);
     if (st != LV_OK) return st;
     *out_price = h->h_res[LV_OUT_PRICE];

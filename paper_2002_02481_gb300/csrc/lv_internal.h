@@ -121,6 +121,33 @@ cudaError_t launch_bump_finalize(const double* partials, int G, int row_words, d
 
 size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra = false);
 
+// Binary64 paths (lv_fp64.cu): the full-FP64 reference adjoint and the
+// binary64 bump baseline, main reading only.
+struct F64Params {
+    const double* spot;    // [I] spot nodes
+    const double* sig;     // [I * J] sigma, spot-major (as the ABI takes it)
+    const double* tau;     // [J] time nodes
+    int I, J, N;
+    double x0, x0_up, x0_dn;   // ln S0, ln(S0 +- eps_S / 2)
+    double r, dt, sqdt, K, disc, phi, eps_half;
+    uint32_t k0, k1, stream_id;
+    long long path_begin, n_paths;
+    double* partials;      // [gridDim.x][row_words]: adjoint 3 + Je I (time-major), bump 2 + I J
+    int row_words;
+    unsigned int* flag;    // adjoint: live paths with a vanishing 1 + g_n
+    int n_scen, n_groups;  // bump: 3 + 2 I J scenarios in groups of bump64_slots_per_thread()
+};
+
+size_t adjoint64_smem_bytes(int N);
+size_t bump64_smem_bytes(int N, int row_words);
+int bump64_slots_per_thread();
+cudaError_t f64_occupancy(bool bump, size_t smem, int* blocks_per_sm);
+cudaError_t launch_adjoint64(const F64Params& P, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_bump64(const F64Params& P, int grid, size_t smem, cudaStream_t s);
+
+// Pipe-rate probes (lv_probe.cu): out[LV_PIPE_COUNT] operations per second.
+cudaError_t measure_pipe_peaks(double* out);
+
 // Test-facing kernels (lv_debug.cu): Philox words and normals for listed
 // (path, block) counters; the per-step time table of a call.
 cudaError_t launch_debug_normals(uint64_t seed, uint32_t stream_id, const long long* paths, const uint32_t* blocks,
@@ -241,6 +268,9 @@ struct lv_surface_s {
     float2* d_ab = nullptr;
     float2* d_abl = nullptr;         // [I] cell coefficients of the ln-S weight, in y = log2 S
     double* d_tau = nullptr;
+    double* d_spot64 = nullptr;      // [I] spot nodes, binary64 (the binary64 kernels)
+    double* d_sig64 = nullptr;       // [I * J] sigma, binary64, spot-major
+    double* h_sig64_stage = nullptr; // pinned staging for its uploads
     float2* h_sig_stage = nullptr;   // pinned staging for sigma uploads
     int log_uniform = 0;
     float cell_scale = 0.0f, cell_shift = 0.0f, s_lo = 0.0f, s_hi = 0.0f;

@@ -107,6 +107,9 @@ def _optional_sigs(c):
     dp = c.POINTER(c.c_double)
     return {
         "lv_bump_greeks": [vp, d, d, d, d, i32, i64, u64, d, dp, dp, dp],
+        "lv_bump_greeks_fp64": [vp, d, d, d, d, i32, i64, u64, d, dp, dp, dp],
+        "lv_price_greeks_fp64_device": [vp, d, d, d, d, i32, i64, u64, vp],
+        "lv_measure_pipe_peaks": [dp],
     }
 
 
@@ -296,6 +299,21 @@ class Surface:
         e = ev[:n_ev.value]
         return xN, V, xb, (e[:, 0].astype(np.int64) + int(path_begin), e[:, 1].copy(), e[:, 2].copy())
 
+    def price_greeks_fp64_device(self, S0, r, K, T, n_steps, n_paths, seed, d_out_ptr: int) -> None:
+        """The binary64 reference run (lv_price_greeks_fp64_device)."""
+        _check(self.lib, self.lib.lv_price_greeks_fp64_device(self.h, S0, r, K, T, int(n_steps), int(n_paths),
+                                                              int(seed), ctypes.c_void_p(d_out_ptr)),
+               "lv_price_greeks_fp64_device")
+
+    def bump_greeks_fp64(self, S0, r, K, T, n_steps, n_paths, seed, eps):
+        """Central bump-and-reprice with binary64 paths (lv_bump_greeks_fp64)."""
+        p, d = ctypes.c_double(), ctypes.c_double()
+        vega = np.zeros(self.IJ, dtype=np.float64)
+        _check(self.lib, self.lib.lv_bump_greeks_fp64(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
+                                                      float(eps), ctypes.byref(p), ctypes.byref(d), _dp(vega)),
+               "lv_bump_greeks_fp64")
+        return p.value, d.value, vega.reshape(self.n_spot, self.n_time)
+
     def time_table(self, T, n_steps):
         """The kernels' (time cell j_n, binary32 weight v_n) for every step."""
         j = np.zeros(n_steps, dtype=np.int32)
@@ -312,6 +330,18 @@ class Surface:
                                                  float(eps), ctypes.byref(p), ctypes.byref(d), _dp(vega)),
                "lv_bump_greeks")
         return p.value, d.value, vega.reshape(self.n_spot, self.n_time)
+
+
+PIPES = ("ffma", "mufu_ex2", "mufu_lg2", "mufu_sin", "mufu_cos", "mufu_sqrt", "imad", "imad_wide", "lop3", "iadd")
+
+
+def measure_pipe_peaks(lib=None) -> dict:
+    """Measured thread-instructions per second of each probed pipe operation
+    on the current device (lv_measure_pipe_peaks)."""
+    lib = lib or load()
+    out = np.zeros(len(PIPES), dtype=np.float64)
+    _check(lib, lib.lv_measure_pipe_peaks(_dp(out)), "lv_measure_pipe_peaks")
+    return dict(zip(PIPES, out.tolist()))
 
 
 def debug_normals(seed, stream_id, paths, blocks, lib=None):

@@ -39,23 +39,34 @@ def sharded_sums(sums_fn: Callable[[int, int], "object"], n_paths: int, group=No
 
 
 def price_greeks_sharded(surface, S0, r, K, T, n_steps, n_paths, seed, stream_id: int = 0, group=None,
-                         device: Optional["object"] = None):
+                         device: Optional["object"] = None, sums=None, out=None):
     """Price, delta and vegas of one option over n_paths paths split across
     the ranks of `group` (NCCL for CUDA tensors): each rank runs the adjoint
-    on its range, the raw sums are summed across ranks, and each rank
-    finalizes them on its GPU. Returns a device tensor [3 + I*J] (LV_OUT_*)."""
+    on its range into raw sums, the sums are summed across ranks (the one
+    exchange), and each rank finalizes the totals on its device. Returns
+    `out` (or a new tensor) [3 + I*J] in the LV_OUT_* layout.
+
+    `sums` and `out` may be passed preallocated ([3 + I*J] float64 on
+    `device`) so that repeated calls allocate nothing. `surface` is an
+    lv.Surface, or anything with the same price_greeks_sums_device /
+    finalize_sums_device methods writing through data pointers."""
     import torch
+    import torch.distributed as dist
 
-    dev = device or torch.device("cuda", torch.cuda.current_device())
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     n = 3 + surface.n_spot * surface.n_time
-
-    def run(b, e):
-        out = torch.zeros(n, dtype=torch.float64, device=dev)
-        surface.price_greeks_sums_device(S0, r, K, T, n_steps, b, e, seed, stream_id, out.data_ptr())
-        return out
-
-    surface.set_stream(torch.cuda.current_stream(dev).cuda_stream)
-    total = sharded_sums(run, n_paths, group)
-    out = torch.zeros(n, dtype=torch.float64, device=dev)
-    surface.finalize_sums_device(total.data_ptr(), n_paths, S0, out.data_ptr())
-    return out
+    if dev.type == "cuda":
+        surface.set_stream(torch.cuda.current_stream(dev).cuda_stream)
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    rank = dist.get_rank(group) if dist.is_initialized() else 0
+    b, e = path_range(rank, world, n_paths)
+    part = sums if sums is not None else torch.empty(n, dtype=torch.float64, device=dev)
+    if e > b:
+        surface.price_greeks_sums_device(S0, r, K, T, n_steps, b, e, seed, stream_id, part.data_ptr())
+    else:
+        part.zero_()
+    if world > 1:
+        dist.all_reduce(part, op=dist.ReduceOp.SUM, group=group)
+    res = out if out is not None else torch.empty(n, dtype=torch.float64, device=dev)
+    surface.finalize_sums_device(part.data_ptr(), n_paths, S0, res.data_ptr())
+    return res

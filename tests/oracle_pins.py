@@ -478,9 +478,97 @@ def pin_rho_dvdt_vs_autograd(lib):
         assert abs(s[oracle.SUM_DVDT] / P - ref["dVdT"]) <= 1e-10 * max(1.0, abs(ref["dVdT"])), (name, ref["dVdT"])
 
 
+# ------------------------------------------------ second-order buckets
+
+def _path_and_cells(surf, opt, p, lib):
+    """ln S_0 .. ln S_N of path p (numpy restatement of the log-Euler step on
+    the oracle's normals and its pinned bilinear lookup) and, per step, the
+    cell and weights (i, j, u, v, inside)."""
+    z = oracle.normals(opt.seed, p, opt.n_steps, lib=lib)
+    dt = opt.T / opt.n_steps
+    x, cells = [math.log(opt.S0)], []
+    for n in range(opt.n_steps):
+        S = math.exp(x[-1])
+        e = oracle.sigma_eval(surf, S, n * dt, lib=lib)
+        cells.append((e["i"], e["j"], e["u"], e["v"], bool(surf.spot[0] <= S <= surf.spot[-1])))
+        x.append(x[-1] + (opt.r - 0.5 * e["sigma"] * e["sigma"]) * dt + e["sigma"] * math.sqrt(dt) * z[n])
+    return np.array(x), cells
+
+
+def pin_vanna_vs_autograd(lib):
+    """Per path, the oracle's second-order buckets equal torch.autograd of
+    the definitions: the gradient of the pathwise delta at the fixed path
+    plus the delta times the gradient of the path's log density, on tiny
+    grids (paths leaving the grid, one time node, a put, r > 0)."""
+    cases = [(W.random_surface(2, 3, 2, s_lo=92, s_hi=108, t_hi=0.5), 100.0, 0.01, 99.0, 0.5, 8, 1, 9),
+             (W.random_surface(1, 3, 1, s_lo=80, s_hi=125), 100.0, 0.0, 100.0, 1.0, 6, 1, 3),
+             (W.random_surface(4, 4, 3, s_lo=70, s_hi=140, t_hi=2.0), 100.0, 0.03, 104.0, 1.3, 9, -1, 6)]
+    checked = 0
+    for surf, S0, r, K, T, N, phi, seed in cases:
+        opt = W.Option(S0=S0, r=r, K=K, T=T, n_steps=N, n_paths=12, seed=seed, phi=phi)
+        for p in range(opt.n_paths):
+            x, cells = _path_and_cells(surf, opt, p, lib)
+            ref = torch_lv.vanna_at_fixed_path(surf.spot, surf.time, surf.sigma, S0, r, K, T, phi, x, cells)
+            got = oracle.run_vanna(surf, opt, p, p + 1, n_threads=1, lib=lib)["vanna"]
+            scale = max(1e-9, float(np.max(np.abs(ref))))
+            assert np.max(np.abs(got - ref)) <= 1e-9 * scale, (p, np.max(np.abs(got - ref)), scale)
+            checked += int(np.any(ref != 0.0))
+    assert checked >= 8
+
+
+def pin_vanna_flat_black_scholes(lib):
+    """On a flat grid log-Euler is exact in law, so the buckets summed over
+    the grid (a partition of unity) estimate Black-Scholes vanna
+    d^2 C / d S0 d sigma = -phi(d1) d2 / sigma, within 4 standard errors."""
+    sig, S0, K, T = 0.2, 100.0, 100.0, 1.0
+    surf = W.flat_surface(sig)
+    opt = W.Option(S0=S0, r=0.0, K=K, T=T, n_steps=4, n_paths=1 << 20, seed=31)
+    res = oracle.run_vanna(surf, opt, lib=lib)
+    sd = sig * math.sqrt(T)
+    d1 = (math.log(S0 / K) + 0.5 * sig * sig * T) / sd
+    d2 = d1 - sd
+    vanna = -math.exp(-0.5 * d1 * d1) / math.sqrt(2 * math.pi) * d2 / sig
+    assert abs(res["total"] - vanna) <= 4 * res["total_se"], (res["total"], vanna, res["total_se"])
+    assert res["total_se"] < 0.1 * abs(vanna)
+    _, delta, _ = bs_call_put(S0, K, T, 0.0, sig, 1)
+    assert abs(res["delta"] - delta) <= 0.01, (res["delta"], delta)
+
+
+def pin_vanna_one_step_closed_form(lib):
+    """One Euler step from inside a cell is exactly Black-Scholes with
+    sigma_0 = sigma(S0, 0), which depends on S0 and on the two nodes of the
+    cell: each bucket's estimate equals central differences (in S0 and in
+    sigma_ij) of that closed form, within 4 standard errors."""
+    surf = W.random_surface(7, 4, 3, s_lo=90, s_hi=111, t_hi=1.0)
+    S0, K, T, r = 100.0, 101.0, 0.4, 0.02
+    opt = W.Option(S0=S0, r=r, K=K, T=T, n_steps=1, n_paths=1 << 21, seed=17)
+    res = oracle.run_vanna(surf, opt, lib=lib)
+
+    def price(s0, sg):
+        i = int(np.searchsorted(surf.spot, s0, side="right") - 1)
+        u = (s0 - surf.spot[i]) / (surf.spot[i + 1] - surf.spot[i])
+        sigma0 = sg[i, 0] * (1 - u) + sg[i + 1, 0] * u
+        return bs_call_put(s0, K, T, r, sigma0, 1)[0]
+
+    hs, he = 1e-3, 1e-4
+    base = np.array(surf.sigma, dtype=np.float64)
+    ref = np.zeros_like(base)
+    for (i, j) in np.ndindex(base.shape):
+        def d_price_d_sig(s0):
+            up, dn = base.copy(), base.copy()
+            up[i, j] += he
+            dn[i, j] -= he
+            return (price(s0, up) - price(s0, dn)) / (2 * he)
+        ref[i, j] = (d_price_d_sig(S0 + hs) - d_price_d_sig(S0 - hs)) / (2 * hs)
+    assert np.count_nonzero(np.abs(ref) > 1e-6) == 2        # the two nodes of the cell, time row 0
+    err = np.abs(res["vanna"] - ref)
+    assert np.all(err <= 4 * res["vanna_se"] + 1e-5), (res["vanna"], ref, res["vanna_se"])
+
+
 ALL_PINS = [pin_philox_curand, pin_normals_from_curand_words, pin_uniform_exact, pin_normal_law,
             pin_black_scholes, pin_flat_closed_form_paths, pin_martingale, pin_put_call_parity,
             pin_adjoint_vs_autograd, pin_adjoint_vs_bump, pin_bilinear,
             pin_flat_closed_form_paths_euler_x, pin_martingale_euler_x, pin_log_interpolation,
             pin_adjoint_vs_autograd_readings, pin_adjoint_vs_bump_readings,
-            pin_black_scholes_rho_dvdt, pin_rho_dvdt_vs_bump, pin_rho_dvdt_vs_autograd]
+            pin_black_scholes_rho_dvdt, pin_rho_dvdt_vs_bump, pin_rho_dvdt_vs_autograd,
+            pin_vanna_vs_autograd, pin_vanna_flat_black_scholes, pin_vanna_one_step_closed_form]

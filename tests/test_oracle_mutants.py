@@ -16,9 +16,10 @@ from . import oracle_pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "lv_oracle.c")
 
 MUTANTS = {
-    "drift sign": ("(op->r - 0.5 * pt.sigma * pt.sigma) * dt",
-                   "(op->r + 0.5 * pt.sigma * pt.sigma) * dt"),
-    "dx/dsigma sign": ("sqdt * z[n] - pt.sigma * dt;", "sqdt * z[n] + pt.sigma * dt;"),
+    "drift sign": ("            x[n + 1] = x[n] + (op->r - 0.5 * pt.sigma * pt.sigma) * dt",
+                   "            x[n + 1] = x[n] + (op->r + 0.5 * pt.sigma * pt.sigma) * dt"),
+    "dx/dsigma sign": ("double h = on_x ? x[n] * sqdt * z[n] : sqdt * z[n] - pt.sigma * dt;",
+                       "double h = on_x ? x[n] * sqdt * z[n] : sqdt * z[n] + pt.sigma * dt;"),
     "dsigma/dx drops S": ("factor = 1.0 + h * S * pt.dsigma_dS;",
                           "factor = 1.0 + h * pt.dsigma_dS;"),
     "node weights transposed": ("p->w[1] = u * (1.0 - v);", "p->w[1] = (1.0 - u) * v;"),
@@ -41,8 +42,8 @@ MUTANTS = {
                              "&overridden);\n        if (st != ORC_OK) return st;\n        ov[0] += overridden;"),
     "inside test drops the upper edge": ("int inside = (S >= sf->spot[0] && S <= sf->spot[I - 1]);",
                                          "int inside = (S >= sf->spot[0]);"),
-    "payoff sign": ("const double itm = (double)op->phi * (SN - op->K);",
-                    "const double itm = (SN - op->K);"),
+    "payoff sign": ("const double itm = (double)op->phi * (SN - op->K);\n    res->V",
+                    "const double itm = (SN - op->K);\n    res->V"),
     "log-weight slope drops 1/S": ("double du_dS = logs ? 1.0 / (S * (log(hi_s) - log(lo_s)))",
                                    "double du_dS = logs ? 1.0 / (log(hi_s) - log(lo_s))"),
     "log weight taken in S": ("u = logs ? (log(S) - log(lo_s)) / (log(hi_s) - log(lo_s))",
@@ -53,6 +54,13 @@ MUTANTS = {
     "rho drops the discount's share": ("double rho = -op->T * res->V;", "double rho = 0.0;"),
     "d V / d T: step time factor off by one": ("h * pt.dsigma_dt * (double)n / (double)N",
                                                "h * pt.dsigma_dt * (double)(n + 1) / (double)N"),
+    "vanna: drops the slope term of d h / d sigma": ("sqdt * z[n] * (1.0 + kappa / (pt.sigma * f))",
+                                                     "sqdt * z[n] * (1.0)"),
+    "vanna: score sign": ("(z[n] * z[n] - 1.0) / pt.sigma - sqdt", "(1.0 - z[n] * z[n]) / pt.sigma - sqdt"),
+    "vanna: slope term without 1 / (1 + g)": ("const double b = h / f;", "const double b = h;"),
+    "vanna: weight slope sign": ("const double dw[4] = { -(1.0 - v) * pt.du_dS, (1.0 - v) * pt.du_dS,",
+                                 "const double dw[4] = { (1.0 - v) * pt.du_dS, -(1.0 - v) * pt.du_dS,"),
+    "vanna: delta without D_N": ("phi * SN * D / op->S0 : 0.0;", "phi * SN / op->S0 : 0.0;"),
     "d V / d T: drift term sign": ("dx_ddt = (op->r - 0.5 * pt.sigma * pt.sigma)", "dx_ddt = (op->r + 0.5 * pt.sigma * pt.sigma)"),
 }
 

@@ -6,6 +6,9 @@ oracle's hand-written reverse sweep (back-propagation, Sec. IV-C of arXiv
 It shares no code with the oracle; the only thing it takes from the oracle
 is the array of normals (pinned on its own against cuRAND).
 """
+import math
+
+import numpy as np
 import torch
 
 
@@ -82,3 +85,45 @@ def autograd_all(spot, time, sigma, S0, r, K, T, n_steps, phi, Z, interp=0, sche
     return dict(price=float(price.detach()), delta=float(d_s0), vega=d_sig.numpy(), rho=float(d_r),
                 dVdT=float(d_T))
 
+
+def vanna_at_fixed_path(spot, time, sigma, S0, r, K, T, phi, x, cells):
+    """Second-order buckets of one fixed Euler path on ln S: the gradient in
+    sigma of the path's pathwise delta at the fixed path, plus that delta
+    times the gradient of the path's log density (each step Gaussian with
+    mean x_n + (r - sigma_n^2/2) dt and standard deviation sigma_n sqrt(dt)),
+    both by torch.autograd, FP64.
+
+    x: [N + 1] ln S_0 .. ln S_N; cells: per step (i, j, u, v, inside), the
+    bilinear cell and weights at (S_n, t_n), fixed with the path. Returns
+    [I, J]."""
+    sp = [float(a) for a in spot]
+    I, J = len(sp), len(time)
+    sg = torch.tensor(sigma, dtype=torch.float64, requires_grad=True)
+    N = len(x) - 1
+    dt = T / N
+    D = torch.ones((), dtype=torch.float64)
+    logp = torch.zeros((), dtype=torch.float64)
+    for n in range(N):
+        i, j, u, v, inside = cells[n]
+        S = math.exp(x[n])
+        if J > 1:
+            lo = sg[i, j] * (1 - u) + sg[i + 1, j] * u
+            hi = sg[i, j + 1] * (1 - u) + sg[i + 1, j + 1] * u
+            sig = lo * (1 - v) + hi * v
+            slope = (1 - v) * (sg[i + 1, j] - sg[i, j]) + v * (sg[i + 1, j + 1] - sg[i, j + 1])
+        else:
+            sig = sg[i, 0] * (1 - u) + sg[i + 1, 0] * u
+            slope = sg[i + 1, 0] - sg[i, 0]
+        kappa = S * slope / (sp[i + 1] - sp[i]) if inside else torch.zeros((), dtype=torch.float64)
+        dx = x[n + 1] - x[n]
+        h = (dx - r * dt) / sig - sig * dt / 2            # d x_{n+1} / d sigma_n along the path
+        D = D * (1 + h * kappa)
+        e = dx - (r - sig * sig / 2) * dt
+        logp = logp - e * e / (2 * sig * sig * dt) - torch.log(sig)
+    SN = math.exp(x[N])
+    if not phi * (SN - K) > 0:
+        return np.zeros((I, J))
+    delta = math.exp(-r * T) * phi * SN * D / S0
+    (g_delta,) = torch.autograd.grad(delta, [sg], retain_graph=True)
+    (g_logp,) = torch.autograd.grad(logp, [sg])
+    return (g_delta + delta.detach() * g_logp).numpy()
