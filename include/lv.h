@@ -252,12 +252,38 @@ lv_status lv_bump_greeks(lv_surface_t h, double S0, double r, double K, double T
                          int32_t n_steps, int64_t n_paths, uint64_t seed, double eps,
                          double* out_price, double* out_delta, double* out_vega);
 
+/* lv_price_greeks_vanna -- second-order bucket sensitivities
+ * d^2 price / (d S0 d sigma_ij) ("vanna" buckets), an extension of Sec. V's
+ * first-order Greeks: out_price and out_delta as in lv_price_greeks, and
+ * out_vanna [n_spot * n_time] (spot-major, caller-owned host memory). The
+ * pathwise delta Delta_p = e^{-rT} 1{phi (S_N - K) > 0} phi S_N D_N / S0
+ * jumps where S_N crosses the strike and where a spot crosses a node, so
+ * its own pathwise derivative would be biased; with the path held fixed
+ * nothing jumps, and the estimator is the derivative of Delta_p at the
+ * fixed path plus Delta_p times the derivative of the path's log density
+ * (each Euler step Gaussian): per path and step n it adds
+ *   Delta_p [ w_ij(n) a_n + S_n d w_ij / d S (n) b_n ],
+ *   a_n = (Z_n^2 - 1) / sigma_n - sqrt(dt) Z_n (1 + k_n / (sigma_n (1 + g_n))),
+ *   b_n = h_n / (1 + g_n),
+ * k_n = S_n d sigma / d S, g_n = h_n k_n, w_ij the bilinear weights. Two
+ * forward passes (no checkpoints), binary32 paths, binary64 level 2. Main
+ * reading only (else LV_EINVAL); a live path with |1 + g_n| < 2^-20 gives
+ * LV_ENUMERIC (host outputs untouched) or NaN device outputs.
+ * lv_price_greeks_vanna_device: the same [3 + I J] (LV_OUT_* layout, the
+ * buckets in place of the vegas) into device memory, not synchronised. */
+lv_status lv_price_greeks_vanna(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                                int64_t n_paths, uint64_t seed, double* out_price, double* out_delta,
+                                double* out_vanna);
+lv_status lv_price_greeks_vanna_device(lv_surface_t h, double S0, double r, double K, double T,
+                                       int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out);
+
 /* Measured issue rates of the SM pipes the Monte Carlo path is bound by
  * (it reads almost nothing from memory: its roofline is arithmetic, not
  * HBM), the denominators of its roofline fractions. lv_measure_pipe_peaks
- * runs one probe kernel per entry on the current device (eight independent
- * chains of that instruction per thread, 8 blocks of 256 threads per SM,
- * best of three runs timed with CUDA events) and writes
+ * runs one probe kernel per entry on the current device (eight chains of
+ * that instruction per thread, integer chains fed by their neighbours so
+ * that none collapses, 8 blocks of 256 threads per SM, best of three runs
+ * timed with CUDA events) and writes
  * out_ops_per_s[LV_PIPE_COUNT]: thread-instructions per second over the
  * whole GPU at the clock the probes ran at. Synchronous; about 50 ms. */
 enum {
@@ -270,8 +296,7 @@ enum {
     LV_PIPE_IMAD = 6,       /* mad.lo.u32 */
     LV_PIPE_IMAD_WIDE = 7,  /* mad.wide.u32 (the Philox product) */
     LV_PIPE_LOP3 = 8,       /* lop3.b32 */
-    LV_PIPE_IADD = 9,       /* add.u32 */
-    LV_PIPE_COUNT = 10
+    LV_PIPE_COUNT = 9
 };
 lv_status lv_measure_pipe_peaks(double* out_ops_per_s);
 

@@ -220,7 +220,7 @@ void occ_store(const OccKey& key, int occ)
 }
 
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
-                        bool dbg = false, bool* grid_smem = nullptr, bool extra = false)
+                        bool dbg = false, bool* grid_smem = nullptr, bool extra = false, bool vanna = false)
 {
     *block = h->cfg_block ? h->cfg_block : 128;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
@@ -242,8 +242,8 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
     if (smem > 200 * 1024)
         return fail(LV_EINVAL, "time table does not fit in shared memory (" + std::to_string(smem) + " bytes)");
     int occ = 0;
-    const int acc = dbg || extra ? 0 : h->acc_mode;
-    const int method = dbg || extra ? LV_ADJ_REVERSE : h->adj_method;
+    const int acc = dbg || extra || vanna ? 0 : h->acc_mode;
+    const int method = vanna ? lv::kMethodVanna : (dbg || extra ? LV_ADJ_REVERSE : h->adj_method);
     const OccKey key{h->device, *block, *k, greeks, acc, dbg, gs, method, model, extra, smem};
     if (!occ_lookup(key, &occ)) {
         LV_CUDA(lv::mc_occupancy(*block, *k, greeks, acc, dbg, gs, method, model, extra, smem, &occ));
@@ -255,9 +255,9 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
 }
 
 lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, bool dbg, Plan* p,
-                    bool extra = false)
+                    bool extra = false, bool vanna = false)
 {
-    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem, extra);
+    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem, extra, vanna);
     if (st != LV_OK) return st;
     p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem, extra);
     const int warps = p->block / 32;
@@ -267,8 +267,8 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     const int64_t slots = (int64_t)p->bps * h->num_sms;
     p->grid = (int)(want_blocks < slots ? want_blocks : slots);
     if (p->grid < 1) p->grid = 1;
-    // the tangent-ratio adjoint keeps no checkpoints
-    const bool reverse = dbg || extra || h->adj_method == LV_ADJ_REVERSE;
+    // the tangent-ratio adjoint and the second-order buckets keep no checkpoints
+    const bool reverse = !vanna && (dbg || extra || h->adj_method == LV_ADJ_REVERSE);
     p->n_ck = greeks && reverse ? (n_steps + p->k - 1) / p->k : 0;
     const size_t nIJ = (size_t)h->Je * h->I;
     // price-only rows hold the scalars; extra rows end with the sums of d V / d r and d V / d T
@@ -280,7 +280,8 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
     p->off_part = o;    o = round_up(o + sizeof(double) * (size_t)p->grid * p->row_words, 256);
     p->off_chunks = o;  o = round_up(o + sizeof(double) * (size_t)p->n_chunks * p->row_words, 256);
     p->off_wrows = o;                   // per-warp rows: Kahan mode only
-    if (greeks && !extra && h->acc_mode == LV_ACC_KAHAN) o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
+    if (greeks && !extra && !vanna && h->acc_mode == LV_ACC_KAHAN)
+        o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
     p->off_l1 = o;      if (greeks) o = round_up(o + sizeof(float) * (size_t)p->grid * nIJ, 256);
     p->off_ckpt = o;
     o = round_up(o + sizeof(float) * (size_t)p->n_ck * total_warps * lv::ring_slots_per_warp(), 256);
@@ -327,6 +328,7 @@ struct McCall {
     double dbg_band = 0.0;
     // set after brace initialisation, never positionally
     bool extra = false;      // also d V / d r and d V / d T (after the vegas)
+    bool vanna = false;      // buckets are d^2 price / (d S0 d sigma_ij) instead of the vegas
 };
 
 lv::McParams base_params(const lv_surface_s* h, const McCall& c)
@@ -385,8 +387,10 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
         return fail(LV_EINVAL, "path indices must lie in [0, 2^48)");
     if (c.stream_id >= 65536u) return fail(LV_EINVAL, "stream_id must be < 65536");
     if (c.n_paths > 0x7fffffffLL) return fail(LV_EINVAL, "one call handles at most 2^31 - 1 paths");
+    if (c.vanna && (h->interp != LV_INTERP_S || h->scheme != LV_SCHEME_LOG))
+        return fail(LV_EINVAL, "second-order buckets run the main reading (LV_INTERP_S, LV_SCHEME_LOG) only");
     Plan p;
-    st = make_plan(h, c.n_steps, c.n_paths, c.greeks, c.dbg_xN != nullptr, &p, c.extra);
+    st = make_plan(h, c.n_steps, c.n_paths, c.greeks, c.dbg_xN != nullptr, &p, c.extra, c.vanna);
     if (st != LV_OK) return st;
     st = ensure_scratch(h, p.total);
     if (st != LV_OK) return st;
@@ -416,6 +420,11 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     if (c.greeks && !c.dbg_xN && !c.extra && h->adj_method == LV_ADJ_TANGENT) {
         P.method = LV_ADJ_TANGENT;
         P.flag = P.tile_counter + 1;      // in the zeroed counter section; the finalize resets it
+    }
+    if (c.vanna) {                        // two forward passes, binary64 level 2, the same flag
+        P.method = lv::kMethodVanna;
+        P.acc_mode = 0;
+        P.flag = P.tile_counter + 1;
     }
     if (h->ev_start) LV_CUDA(cudaEventRecord(h->ev_start, h->stream));
     LV_CUDA(lv::launch_mc(P, p.grid, p.block, p.k, c.greeks, p.smem, h->stream));
@@ -752,6 +761,38 @@ lv_status lv_price_greeks_ext_device(lv_surface_t h, double S0, double r, double
     McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, d_out};
     c.extra = true;
     return run_mc(h, c);
+}
+
+lv_status lv_price_greeks_vanna_device(lv_surface_t h, double S0, double r, double K, double T,
+                                       int32_t n_steps, int64_t n_paths, uint64_t seed, double* d_out)
+{
+    if (!h || !d_out) return fail(LV_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, d_out};
+    c.vanna = true;
+    return run_mc(h, c);
+}
+
+lv_status lv_price_greeks_vanna(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps,
+                                int64_t n_paths, uint64_t seed, double* out_price, double* out_delta,
+                                double* out_vanna)
+{
+    if (!h || !out_price || !out_delta || !out_vanna) return fail(LV_EINVAL, "NULL argument");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
+    McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, h->d_res};
+    c.vanna = true;
+    lv_status st = run_mc(h, c);
+    if (st != LV_OK) return st;
+    st = fetch_result(h);
+    if (st != LV_OK) return st;
+    if (std::isnan(h->h_res[LV_OUT_PRICE]))    // outputs left untouched, like every failure
+        return fail(LV_ENUMERIC, "a factor 1 + g_n vanished on a live path");
+    *out_price = h->h_res[LV_OUT_PRICE];
+    *out_delta = h->h_res[LV_OUT_DELTA];
+    std::memcpy(out_vanna, h->h_res + LV_OUT_VEGA, sizeof(double) * (size_t)h->I * h->J);
+    return LV_OK;
 }
 
 lv_status lv_price_greeks_sums_device(lv_surface_t h, double S0, double r, double K, double T,

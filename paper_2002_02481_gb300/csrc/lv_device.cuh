@@ -563,4 +563,76 @@ __device__ __forceinline__ void tangent_scatter(const McParams& P, const SmemGri
     }
 }
 
+// Second-order buckets d^2 price / (d S0 d sigma_ij), pass 2 of one live
+// path (main reading): regenerates the path and adds, per step n,
+//   Delta_p [ w_ij(n) a_n + S_n d w_ij / d S (n) b_n ]
+//   a_n = (Z_n^2 - 1) / sigma_n - sqrt(dt) Z_n (1 + k_n / (sigma_n (1 + g_n))),
+//   b_n = h_n / (1 + g_n),  k_n = S_n d sigma / d S,  g_n = h_n k_n,
+// to the corners of its cell: the derivative of the pathwise delta Delta_p at
+// the fixed path plus Delta_p times the derivative of the path's log
+// density (the Gaussian Euler step), which together are unbiased for the
+// second derivative although Delta_p itself jumps at the strike and at the
+// nodes. Run-length sums in registers while the cell is unchanged (the
+// weight terms as in reverse_path, the slope terms E0 = sum (1 - v) d,
+// E1 = sum v d), then binary32 reductions into `l1`.
+__device__ __forceinline__ void vanna_scatter(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
+                                              float delta, float* l1)
+{
+    float y = P.x0;
+    int cur = -1;
+    float A = 0.0f, AU = 0.0f, Bs = 0.0f, BU = 0.0f, E0 = 0.0f, E1 = 0.0f;
+    float z[4];
+    for (int n0 = 0; n0 < P.N; n0 += 4) {
+        normals4((uint32_t)(n0 >> 2), c1, c2, P.k0, P.k1, z);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = n0 + q;
+            if (n < P.N) {
+                const int4 tb = g.tab[n];
+                const StepEval e = eval_sigma<true, 0>(P, g, y, tb);
+                const float zq = z[q];
+                const float h = fmaf(P.sqdt, zq, -e.sigma * P.dt);
+                const float f = fmaf(h, e.sslope, 1.0f);                      // 1 + g_n
+                const float a = __fdividef(fmaf(zq, zq, -1.0f), e.sigma) -
+                                P.sqdt * zq * (1.0f + __fdividef(e.sslope, e.sigma * f));
+                const bool inside = (e.S >= P.s_lo) && (e.S <= P.s_hi);
+                const float sdu = inside ? e.S * g.ab[e.i].x : 0.0f;          // S d u / d S
+                const float c = delta * a;
+                const float d = delta * __fdividef(h, f) * sdu;
+                const int key = tb.z + e.i;
+                if (key != cur) {
+                    if (cur >= 0) {
+                        float* p0 = l1 + cur;
+                        float* p1 = p0 + P.I;
+                        atomicAdd(p0, A - AU - E0);
+                        atomicAdd(p0 + 1, AU + E0);
+                        atomicAdd(p1, Bs - BU - E1);
+                        atomicAdd(p1 + 1, BU + E1);
+                    }
+                    A = AU = Bs = BU = E0 = E1 = 0.0f;
+                    cur = key;
+                }
+                const float v = __int_as_float(tb.w);
+                const float cb = c * v, ca = c - cb;
+                const float db = d * v;
+                A += ca;
+                AU = fmaf(ca, e.u, AU);
+                Bs += cb;
+                BU = fmaf(cb, e.u, BU);
+                E0 += d - db;
+                E1 += db;
+                y = step_state<0>(P, y, e.sigma, zq);
+            }
+        }
+    }
+    if (cur >= 0) {
+        float* p0 = l1 + cur;
+        float* p1 = p0 + P.I;
+        atomicAdd(p0, A - AU - E0);
+        atomicAdd(p0 + 1, AU + E0);
+        atomicAdd(p1, Bs - BU - E1);
+        atomicAdd(p1 + 1, BU + E1);
+    }
+}
+
 }  // namespace lv

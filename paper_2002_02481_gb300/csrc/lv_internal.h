@@ -80,6 +80,10 @@ struct McParams {
     float dbg_band;                     // relative distance to a node that is logged
 };
 
+// McParams::method of the second-order bucket kernel (besides LV_ADJ_REVERSE
+// and LV_ADJ_TANGENT of lv.h).
+constexpr int kMethodVanna = 2;
+
 struct FinalizeParams {
     const double* partials;
     int G;                 // rows

@@ -422,6 +422,86 @@ __global__ void __launch_bounds__(128, 6) tangent_kernel(const __grid_constant__
     block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
 }
 
+// Second-order buckets (lv_price_greeks_vanna): the tangent-ratio kernel's
+// structure with pass 2 replaced by vanna_scatter. Pass 1 (tangent_forward)
+// gives the payoff and x_bar_0 = x_bar_N D_N, hence Delta_p = x_bar_0 / S0;
+// live paths are queued and scattered in full-warp batches. Main reading,
+// binary64 level 2. Rows: price sums as usual, buckets d^2 price / (d S0 d
+// sigma_ij) summed over paths.
+template <bool GS>
+__global__ void __launch_bounds__(128, 6) vanna_kernel(const __grid_constant__ McParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
+    stage_grid<GS>(P, smem, L);
+    float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);
+    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
+    float* q_c = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
+    double* s_red = reinterpret_cast<double*>(smem + L.red);
+    const int nIJ = P.Je * P.I;
+    for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
+    double* const row = P.partials + (size_t)blockIdx.x * P.row_words;
+    double* const wrow = row + 3;
+    for (int e = tid; e < nIJ; e += B) wrow[e] = 0.0;
+    __syncthreads();
+    const SmemGrid g{ reinterpret_cast<const int4*>(smem + L.tab),
+                      GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
+                      reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab) };
+    AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
+    acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
+    int q_head = 0, q_count = 0, batches = 0;
+    int tile = claim_tile(P.tile_counter);
+    while (true) {
+        const bool more = tile < P.n_tiles;
+        if (q_count >= 32 || (!more && q_count > 0)) {
+            const int nb = min(32, q_count);
+            if (lane < nb) {
+                const int e = (q_head + lane) & (kQueue - 1);
+                uint32_t c1, c2;
+                path_counter(P, q_rel[e], c1, c2);
+                vanna_scatter(P, g, c1, c2, q_c[e] * P.inv_S0, l1);
+            }
+            q_head = (q_head + nb) & (kQueue - 1);
+            q_count -= nb;
+            __syncwarp();
+            if (++batches % P.flush_every == 0) drain_buckets<0>(l1, nIJ, wrow);
+            continue;
+        }
+        if (!more) break;
+        const long long rel = (long long)tile * kTile + lane;
+        float xbarN = 0.0f, c = 0.0f;
+        if (rel < P.n_paths) {
+            uint32_t c1, c2;
+            path_counter(P, rel, c1, c2);
+            float D;
+            bool tiny;
+            const float y = tangent_forward<0>(P, g, c1, c2, D, tiny);
+            float V;
+            payoff<0>(P, y, V, xbarN);
+            c = xbarN * D;
+            acc_add<0>(acc[0], V);
+            acc_add<0>(acc[B], V * V);
+            acc_add<0>(acc[2 * B], c);
+            if (tiny && xbarN != 0.0f) atomicAdd(P.flag, 1u);
+        }
+        const bool live = xbarN != 0.0f;
+        const unsigned bal = __ballot_sync(0xffffffffu, live);
+        if (live) {
+            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
+            q_rel[e] = (int)rel;
+            q_c[e] = c;
+        }
+        q_count += __popc(bal);
+        __syncwarp();
+        tile = claim_tile(P.tile_counter);
+    }
+    __syncthreads();
+    for (int e = tid; e < nIJ; e += B) row[3 + e] += (double)l1[e];
+    block_scalars(acc_value<0>(acc[0]), acc_value<0>(acc[B]), acc_value<0>(acc[2 * B]), s_red, row);
+}
+
 template <int ACC, bool GS, int MODEL>
 __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ McParams P)
 {
@@ -492,6 +572,14 @@ cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
 template <int MODEL, bool GS, typename F>
 cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, bool extra, F&& f)
 {
+    if (method == kMethodVanna) {     // second-order buckets: main reading, binary64 level 2
+        if constexpr (MODEL == 0) {
+            static bool cv = false;
+            if (!greeks || dbg || extra || acc != 0) return cudaErrorInvalidValue;
+            return f(vanna_kernel<GS>, cv);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (extra) {           // d V / d r and d V / d T: reverse sweep, binary64 level 2, k = 4 or 8
         static bool ce[2] = {};
         if (!greeks || dbg || method != LV_ADJ_REVERSE || acc != 0) return cudaErrorInvalidValue;

@@ -1,10 +1,14 @@
 // lv_probe.cu -- measured issue rates of the SM pipes the Monte Carlo
 // kernels spend their time in: the roofline denominators of a path that is
 // bound by arithmetic, not by memory. Each probe kernel runs, per thread,
-// eight independent chains of one instruction kind (inline PTX, so that the
-// compiler neither folds nor fuses them), on 8 blocks of 256 threads per SM,
-// and is timed with CUDA events; the rate is operations (thread-instructions)
-// per second over the whole GPU at the clock it ran at.
+// eight chains of one instruction kind (inline PTX) on 8 blocks of 256
+// threads per SM, and is timed with CUDA events; the rate is operations
+// (thread-instructions) per second over the whole GPU at the clock it ran
+// at. Floating-point chains cannot be reassociated; in the integer chains
+// every step takes an operand from the neighbouring chain (so that no chain
+// of bitwise or modular operations on fixed operands collapses into fewer
+// instructions) while the eight chains still issue independently within an
+// iteration.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -30,11 +34,10 @@ __device__ __forceinline__ void step_f(float& x, float a)
 }
 
 template <int OP>
-__device__ __forceinline__ void step_i(uint32_t& x, uint32_t a, uint32_t b)
+__device__ __forceinline__ void step_i(uint32_t& x, uint32_t y, uint32_t b)
 {
-    if (OP == LV_PIPE_IMAD) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x) : "r"(a), "r"(b));
-    if (OP == LV_PIPE_LOP3) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x) : "r"(a), "r"(b));
-    if (OP == LV_PIPE_IADD) asm volatile("add.u32 %0, %0, %1;" : "+r"(x) : "r"(a));
+    if (OP == LV_PIPE_IMAD) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(x) : "r"(y), "r"(b));
+    if (OP == LV_PIPE_LOP3) asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(x) : "r"(y), "r"(b));
 }
 
 template <int OP>
@@ -57,10 +60,14 @@ __global__ void __launch_bounds__(256) probe_i(uint32_t a, uint32_t b, uint32_t*
 {
     uint32_t x[kChains];
 #pragma unroll
-    for (int k = 0; k < kChains; ++k) x[k] = threadIdx.x * 2654435761u + (uint32_t)k;
-    for (int it = 0; it < kIters; ++it)
+    for (int k = 0; k < kChains; ++k) x[k] = (threadIdx.x + a) * 2654435761u + (uint32_t)k;
+    for (int it = 0; it < kIters; ++it) {
+        uint32_t y[kChains];
 #pragma unroll
-        for (int k = 0; k < kChains; ++k) step_i<OP>(x[k], a, b);
+        for (int k = 0; k < kChains; ++k) y[k] = x[(k + 1) % kChains];       // this iteration's operands
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) step_i<OP>(x[k], y[k], b);
+    }
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kChains; ++k) s ^= x[k];
@@ -77,10 +84,13 @@ __global__ void __launch_bounds__(256) probe_imad_wide(uint32_t a, unsigned long
         acc[k] = k;
         x[k] = threadIdx.x * 2246822519u + (uint32_t)k;
     }
-    for (int it = 0; it < kIters; ++it)
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+        for (int k = 0; k < kChains; ++k) x[k] = (uint32_t)acc[(k + 1) % kChains];   // this iteration's operands
 #pragma unroll
         for (int k = 0; k < kChains; ++k)
             asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[k]) : "r"(x[k]), "r"(a));
+    }
     unsigned long long s = 0;
 #pragma unroll
     for (int k = 0; k < kChains; ++k) s ^= acc[k];
@@ -143,7 +153,6 @@ cudaError_t measure_pipe_peaks(double* out)
         probe_imad_wide<<<grid, block>>>(0xD2511F53u, static_cast<unsigned long long*>(sink));
     });
     rate(LV_PIPE_LOP3, [&] { probe_i<LV_PIPE_LOP3><<<grid, block>>>(0x9E3779B9u, 0xBB67AE85u, is); });
-    rate(LV_PIPE_IADD, [&] { probe_i<LV_PIPE_IADD><<<grid, block>>>(0x9E3779B9u, 0u, is); });
     cudaFree(sink);
     return e;
 }

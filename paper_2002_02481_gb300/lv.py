@@ -110,6 +110,8 @@ def _optional_sigs(c):
         "lv_bump_greeks_fp64": [vp, d, d, d, d, i32, i64, u64, d, dp, dp, dp],
         "lv_price_greeks_fp64_device": [vp, d, d, d, d, i32, i64, u64, vp],
         "lv_measure_pipe_peaks": [dp],
+        "lv_price_greeks_vanna": [vp, d, d, d, d, i32, i64, u64, dp, dp, dp],
+        "lv_price_greeks_vanna_device": [vp, d, d, d, d, i32, i64, u64, vp],
     }
 
 
@@ -299,6 +301,20 @@ class Surface:
         e = ev[:n_ev.value]
         return xN, V, xb, (e[:, 0].astype(np.int64) + int(path_begin), e[:, 1].copy(), e[:, 2].copy())
 
+    def price_greeks_vanna(self, S0, r, K, T, n_steps, n_paths, seed):
+        """(price, delta, d^2 price / (d S0 d sigma) [I, J]) (lv_price_greeks_vanna)."""
+        p, d = ctypes.c_double(), ctypes.c_double()
+        vn = np.zeros(self.IJ, dtype=np.float64)
+        _check(self.lib, self.lib.lv_price_greeks_vanna(self.h, S0, r, K, T, int(n_steps), int(n_paths), int(seed),
+                                                        ctypes.byref(p), ctypes.byref(d), _dp(vn)),
+               "lv_price_greeks_vanna")
+        return p.value, d.value, vn.reshape(self.n_spot, self.n_time)
+
+    def price_greeks_vanna_device(self, S0, r, K, T, n_steps, n_paths, seed, d_out_ptr: int) -> None:
+        _check(self.lib, self.lib.lv_price_greeks_vanna_device(self.h, S0, r, K, T, int(n_steps), int(n_paths),
+                                                               int(seed), ctypes.c_void_p(d_out_ptr)),
+               "lv_price_greeks_vanna_device")
+
     def price_greeks_fp64_device(self, S0, r, K, T, n_steps, n_paths, seed, d_out_ptr: int) -> None:
         """The binary64 reference run (lv_price_greeks_fp64_device)."""
         _check(self.lib, self.lib.lv_price_greeks_fp64_device(self.h, S0, r, K, T, int(n_steps), int(n_paths),
@@ -332,7 +348,7 @@ class Surface:
         return p.value, d.value, vega.reshape(self.n_spot, self.n_time)
 
 
-PIPES = ("ffma", "mufu_ex2", "mufu_lg2", "mufu_sin", "mufu_cos", "mufu_sqrt", "imad", "imad_wide", "lop3", "iadd")
+PIPES = ("ffma", "mufu_ex2", "mufu_lg2", "mufu_sin", "mufu_cos", "mufu_sqrt", "imad", "imad_wide", "lop3")
 
 
 def measure_pipe_peaks(lib=None) -> dict:

@@ -85,7 +85,7 @@ def test_fp64_bump_matches_the_oracle_bump(lib):
     s = lv.Surface.from_workload(surf, lib)
     for eps in (1e-4, 1e-6):
         p, d, v = s.bump_greeks_fp64(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, eps)
-        vref, dref = oracle.bump(surf, opt, eps, 1e-4 * opt.S0)
+        vref, dref = oracle.bump(surf, opt, eps, eps * opt.S0)       # the spot bump scales with eps
         vmax = np.max(np.abs(vref))
         assert np.max(np.abs(v - vref)) <= 1e-7 * vmax * (1e-4 / eps), eps
         assert abs(d - dref) <= 1e-7 * abs(dref) * (1e-4 / eps), (eps, d, dref)
