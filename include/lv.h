@@ -161,6 +161,17 @@ lv_status lv_set_scheme(lv_surface_t h, int32_t scheme);
  * on it beyond reduction-order rounding. */
 lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks_per_sm);
 
+/* Paths per lane of the adjoint's forward tiles: 1, or 2 (each lane runs two
+ * paths interleaved: two independent dependency chains per thread, the
+ * per-step grid data loaded once for both); 0 keeps the tuned or default
+ * value (1). Two paths per lane exist for the main reading's reverse sweep
+ * with checkpoints every 4 or 8 steps; elsewhere the call runs one. The
+ * results do not depend on it beyond reduction-order rounding.
+ * lv_get_paths_per_lane reads back the value the next call with n_steps
+ * steps will use. */
+lv_status lv_set_paths_per_lane(lv_surface_t h, int32_t ppl);
+lv_status lv_get_paths_per_lane(lv_surface_t h, int32_t n_steps, int32_t* ppl);
+
 /* Record two caller-owned CUDA events (cudaEvent_t, created with timing
  * enabled) on the handle's stream immediately before and after the Monte
  * Carlo kernel of every later call, so that a caller can time that kernel
@@ -169,10 +180,12 @@ lv_status lv_set_kernel_events(lv_surface_t h, void* start_event, void* end_even
 
 /* Autotuner for one option: times lv_price_greeks_device on this problem
  * over launch shapes (threads per block 64 / 128, checkpoint interval 4 / 8
- * / 16), keeps the fastest in the handle (as lv_set_launch would) and
- * appends it to the file named by LV_TUNE_CACHE when that variable is set;
- * later handles with the same grid size and step count then start from it.
- * Runs the problem about 18 times. Outputs may be NULL. */
+ * / 16, and for the main reading's reverse sweep at k = 4 and 8 one or two
+ * paths per lane), keeps the fastest in the handle (as lv_set_launch and
+ * lv_set_paths_per_lane would) and appends it (block, k, paths per lane) to
+ * the file named by LV_TUNE_CACHE when that variable is set; later handles
+ * with the same grid size and step count then start from it. Runs the
+ * problem about 40 times. Outputs may be NULL. */
 lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps, int64_t n_paths,
                   uint64_t seed, int32_t* out_block, int32_t* out_k, double* out_ms);
 

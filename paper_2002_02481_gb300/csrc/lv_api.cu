@@ -173,7 +173,7 @@ lv_status check_option(double S0, double r, double K, double T, int32_t n_steps)
 }
 
 struct Plan {
-    int block = 128, k = 4, bps = 1, grid = 1;
+    int block = 128, k = 4, bps = 1, grid = 1, ppl = 1;
     bool grid_smem = true;
     size_t smem = 0;
     int n_tiles = 0, n_ck = 0, row_words = 0, n_chunks = 0;
@@ -200,7 +200,7 @@ constexpr size_t kGridSmemLimit = 44 * 1024;
 // sweep, binary64 level 2, k = 4 or 8).
 // Blocks per SM of one kernel instantiation and launch shape, per device:
 // the runtime's occupancy query costs microseconds, so each answer is kept.
-using OccKey = std::tuple<int, int, int, bool, int, bool, bool, int, int, bool, size_t>;
+using OccKey = std::tuple<int, int, int, bool, int, bool, bool, int, int, bool, size_t, int>;
 std::mutex g_occ_mu;
 std::map<OccKey, int> g_occ;
 
@@ -220,33 +220,40 @@ void occ_store(const OccKey& key, int occ)
 }
 
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
-                        bool dbg = false, bool* grid_smem = nullptr, bool extra = false, bool vanna = false)
+                        bool dbg = false, bool* grid_smem = nullptr, bool extra = false, bool vanna = false,
+                        int* ppl_out = nullptr)
 {
     *block = h->cfg_block ? h->cfg_block : 128;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
+    int ppl = h->cfg_ppl ? h->cfg_ppl : 1;
     const char* cache = std::getenv("LV_TUNE_CACHE");
-    if (greeks && !dbg && !h->cfg_block && !h->cfg_k && cache && *cache) {
+    if (greeks && !dbg && !h->cfg_block && !h->cfg_k && !h->cfg_ppl && cache && *cache) {
         int v[3];
         if (lv::tune_cache_lookup(adjoint_tune_key(h, n_steps), v) && v[0] >= 32 && v[0] <= 128 &&
             v[0] % 32 == 0 && (v[1] == 4 || v[1] == 8 || v[1] == 16 || v[1] == 32)) {
             *block = v[0];
             *k = v[1];
+            ppl = v[2] == 2 ? 2 : 1;
         }
     }
     if (dbg) *k = 4;
     const int model = (h->interp == LV_INTERP_LOGS ? 1 : 0) | (h->scheme == LV_SCHEME_S ? 2 : 0);
     if ((model != 0 || extra) && *k > lv::kModelMaxK) *k = lv::kModelMaxK;
-    const bool gs = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, true, extra) <= kGridSmemLimit;
+    // two paths per lane: the main reading's reverse sweep with checkpoints every 4 or 8 steps
+    if (!greeks || dbg || extra || vanna || model != 0 || h->adj_method != LV_ADJ_REVERSE || (*k != 4 && *k != 8))
+        ppl = 1;
+    if (ppl_out) *ppl_out = ppl;
+    const bool gs = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, true, extra, ppl) <= kGridSmemLimit;
     if (grid_smem) *grid_smem = gs;
-    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, gs, extra);
+    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, gs, extra, ppl);
     if (smem > 200 * 1024)
         return fail(LV_EINVAL, "time table does not fit in shared memory (" + std::to_string(smem) + " bytes)");
     int occ = 0;
     const int acc = dbg || extra || vanna ? 0 : h->acc_mode;
     const int method = vanna ? lv::kMethodVanna : (dbg || extra ? LV_ADJ_REVERSE : h->adj_method);
-    const OccKey key{h->device, *block, *k, greeks, acc, dbg, gs, method, model, extra, smem};
+    const OccKey key{h->device, *block, *k, greeks, acc, dbg, gs, method, model, extra, smem, ppl};
     if (!occ_lookup(key, &occ)) {
-        LV_CUDA(lv::mc_occupancy(*block, *k, greeks, acc, dbg, gs, method, model, extra, smem, &occ));
+        LV_CUDA(lv::mc_occupancy(*block, *k, greeks, acc, dbg, gs, method, model, extra, smem, &occ, ppl));
         occ_store(key, occ);
     }
     if (occ < 1) return fail(LV_EINVAL, "launch shape does not fit on an SM");
@@ -257,9 +264,10 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
 lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool greeks, bool dbg, Plan* p,
                     bool extra = false, bool vanna = false)
 {
-    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem, extra, vanna);
+    lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem, extra, vanna,
+                                 &p->ppl);
     if (st != LV_OK) return st;
-    p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem, extra);
+    p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem, extra, p->ppl);
     const int warps = p->block / 32;
     const int64_t tiles = (n_paths + lv::paths_per_tile(greeks) - 1) / lv::paths_per_tile(greeks);   // claimed by warps
     p->n_tiles = (int)tiles;
@@ -284,7 +292,7 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
         o = round_up(o + sizeof(double) * total_warps * nIJ, 256);
     p->off_l1 = o;      if (greeks) o = round_up(o + sizeof(float) * (size_t)p->grid * nIJ, 256);
     p->off_ckpt = o;
-    o = round_up(o + sizeof(float) * (size_t)p->n_ck * total_warps * lv::ring_slots_per_warp(), 256);
+    o = round_up(o + sizeof(float) * (size_t)p->n_ck * total_warps * lv::ring_slots_per_warp() * p->ppl, 256);
     p->total = o;
     return LV_OK;
 }
@@ -397,6 +405,7 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     char* base = static_cast<char*>(h->d_scratch);
     lv::McParams P = base_params(h, c);
     P.n_tiles = p.n_tiles;
+    P.ppl = p.ppl;
     P.tile_counter = reinterpret_cast<unsigned int*>(base + p.off_counter);
     P.partials = reinterpret_cast<double*>(base + p.off_part);
     P.row_words = p.row_words;
@@ -659,6 +668,27 @@ lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks
     return LV_OK;
 }
 
+lv_status lv_set_paths_per_lane(lv_surface_t h, int32_t ppl)
+{
+    if (!h) return fail(LV_EINVAL, "handle is NULL");
+    if (ppl < 0 || ppl > 2) return fail(LV_EINVAL, "paths per lane must be 0, 1 or 2");
+    h->cfg_ppl = ppl;
+    return LV_OK;
+}
+
+lv_status lv_get_paths_per_lane(lv_surface_t h, int32_t n_steps, int32_t* ppl)
+{
+    if (!h || !ppl) return fail(LV_EINVAL, "NULL argument");
+    if (n_steps < 1 || n_steps > LV_MAX_STEPS) return fail(LV_EINVAL, "n_steps out of range");
+    DeviceGuard g(h->device);
+    int b = 0, kk = 0, bps = 0, p = 1;
+    bool gs = true;
+    lv_status st = choose_launch(h, n_steps, true, &b, &kk, &bps, false, &gs, false, false, &p);
+    if (st != LV_OK) return st;
+    *ppl = p;
+    return LV_OK;
+}
+
 lv_status lv_set_kernel_events(lv_surface_t h, void* start_event, void* end_event)
 {
     if (!h) return fail(LV_EINVAL, "handle is NULL");
@@ -818,17 +848,21 @@ lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32
     if (!g.ok) return fail(LV_ECUDA, "cannot select the handle's device");
     const int blocks[] = {64, 128};
     const int ks[] = {4, 8, 16};
-    const int keep_b = h->cfg_block, keep_k = h->cfg_k, keep_s = h->cfg_bps;
+    const int keep_b = h->cfg_block, keep_k = h->cfg_k, keep_s = h->cfg_bps, keep_p = h->cfg_ppl;
+    // two paths per lane exist for the main reading's reverse sweep at k = 4 and 8
+    const bool ppl2 = h->adj_method == LV_ADJ_REVERSE && h->interp == LV_INTERP_S && h->scheme == LV_SCHEME_LOG;
     cudaEvent_t e0, e1;
     LV_CUDA(cudaEventCreate(&e0));
     LV_CUDA(cudaEventCreate(&e1));
     double best = 1e300;
-    int bb = 128, bk = 4;
+    int bb = 128, bk = 4, bp = 1;
     for (int blk : blocks)
-        for (int k : ks) {
+        for (int k : ks)
+        for (int ppl = 1; ppl <= ((ppl2 && k <= 8) ? 2 : 1); ++ppl) {
             h->cfg_block = blk;
             h->cfg_k = k;
             h->cfg_bps = 0;
+            h->cfg_ppl = ppl;
             McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, h->d_res};
             if (run_mc(h, c) != LV_OK) continue;             // warm-up (and scratch growth)
             float t = 1e30f;
@@ -845,6 +879,7 @@ lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32
                 best = t;
                 bb = blk;
                 bk = k;
+                bp = ppl;
             }
         }
     cudaEventDestroy(e0);
@@ -853,12 +888,14 @@ lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32
         h->cfg_block = keep_b;
         h->cfg_k = keep_k;
         h->cfg_bps = keep_s;
+        h->cfg_ppl = keep_p;
         return fail(LV_EINTERNAL, "no launch shape ran");
     }
     h->cfg_block = bb;
     h->cfg_k = bk;
     h->cfg_bps = 0;
-    const int v[3] = {bb, bk, 0};
+    h->cfg_ppl = bp;
+    const int v[3] = {bb, bk, bp};
     lv::tune_cache_append(adjoint_tune_key(h, n_steps), v, best);
     if (out_block) *out_block = bb;
     if (out_k) *out_k = bk;
@@ -1250,7 +1287,7 @@ lv_status static_scratch(int device, char** out)
 
 // Scratch layout of one adjoint launch with `grid` blocks (same sections as
 // the allocating path); returns the bytes needed.
-size_t static_plan_bytes(const lv_surface_s* h, int grid, int block, int k, int n_steps, size_t* off_part,
+size_t static_plan_bytes(const lv_surface_s* h, int grid, int block, int k, int ppl, int n_steps, size_t* off_part,
                          size_t* off_chunks, size_t* off_wrows, size_t* off_l1, size_t* off_ckpt)
 {
     const size_t nIJ = (size_t)h->Je * h->I;
@@ -1263,7 +1300,7 @@ size_t static_plan_bytes(const lv_surface_s* h, int grid, int block, int k, int 
     *off_wrows = o;                                               // per-warp rows: Kahan mode only
     if (h->acc_mode == LV_ACC_KAHAN) o = round_up(o + sizeof(double) * warps * nIJ, 256);
     *off_l1 = o;     o = round_up(o + sizeof(float) * (size_t)grid * nIJ, 256);
-    *off_ckpt = o;   o = round_up(o + sizeof(float) * n_ck * warps * lv::ring_slots_per_warp(), 256);
+    *off_ckpt = o;   o = round_up(o + sizeof(float) * n_ck * warps * lv::ring_slots_per_warp() * ppl, 256);
     return o;
 }
 
@@ -1283,9 +1320,9 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     st = static_scratch(h->device, &base);
     if (st != LV_OK) return st;
 
-    int block = 0, k = 0, bps = 0;
+    int block = 0, k = 0, bps = 0, ppl = 1;
     bool grid_smem = true;
-    st = choose_launch(h, n_steps, true, &block, &k, &bps, false, &grid_smem);
+    st = choose_launch(h, n_steps, true, &block, &k, &bps, false, &grid_smem, false, false, &ppl);
     if (st != LV_OK) return st;
     const int warps = block / 32;
     const int64_t tiles = (n_paths + lv::paths_per_tile(true) - 1) / lv::paths_per_tile(true);
@@ -1295,12 +1332,12 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     size_t off_part = 0, off_chunks = 0, off_wrows = 0, off_l1 = 0, off_ckpt = 0;
     // the most blocks (at most the full-width grid) whose scratch fits in the static array;
     // the plan's size grows with the grid, so bisect
-    if (static_plan_bytes(h, grid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1, &off_ckpt) >
+    if (static_plan_bytes(h, grid, block, k, ppl, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1, &off_ckpt) >
         kStaticScratchBytes) {
         int lo = 1, hi = grid - 1;
         while (lo < hi) {
             const int mid = lo + (hi - lo + 1) / 2;
-            if (static_plan_bytes(h, mid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
+            if (static_plan_bytes(h, mid, block, k, ppl, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
                                   &off_ckpt) <= kStaticScratchBytes)
                 lo = mid;
             else
@@ -1308,8 +1345,8 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
         }
         grid = lo;
     }
-    const size_t need = static_plan_bytes(h, grid, block, k, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
-                                          &off_ckpt);
+    const size_t need = static_plan_bytes(h, grid, block, k, ppl, n_steps, &off_part, &off_chunks, &off_wrows,
+                                          &off_l1, &off_ckpt);
     if (need > kStaticScratchBytes)
         return fail(LV_EINVAL, "grid of " + std::to_string(h->I) + " x " + std::to_string(h->J) + " nodes with " +
                                std::to_string(n_steps) + " steps needs " + std::to_string(need) +
@@ -1319,6 +1356,7 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     McCall c{S0, r, K, T, n_steps, 0, n_paths, seed, 0u, true, false, d_out};
     lv::McParams P = base_params(h, c);
     P.n_tiles = (int)tiles;
+    P.ppl = ppl;
     P.tile_counter = reinterpret_cast<unsigned int*>(base);
     P.partials = reinterpret_cast<double*>(base + off_part);
     P.row_words = 3 + h->Je * h->I;
@@ -1335,7 +1373,7 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     // the array keeps the previous call's contents: the tile counter and the
     // flag must start at zero (every other section is written before it is read)
     LV_CUDA(cudaMemsetAsync(P.tile_counter, 0, 2 * sizeof(unsigned int), h->stream));
-    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, block, true, grid_smem);
+    const size_t smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, block, true, grid_smem, false, ppl);
     LV_CUDA(lv::launch_mc(P, grid, block, k, true, smem, h->stream));
     lv::FinalizeParams F{};
     F.partials = P.partials;

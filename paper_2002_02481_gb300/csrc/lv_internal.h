@@ -56,12 +56,13 @@ struct McParams {
 
     // work decomposition and scratch
     int n_tiles;           // ceil(n_paths / paths_per_tile()): tiles claimed by warps
+    int ppl;               // adjoint: paths per lane of a forward tile (1 or 2; a warp claims ppl tiles)
     unsigned int* tile_counter;   // zero before the launch, reset by the finalize
     double* partials;      // [gridDim.x][row_words] per-block binary64 rows
     int row_words;         // 3 + Je * I (adjoint) or 3 (price only)
     double* warp_rows;     // [gridDim.x * warps][Je * I] per-warp level-2 rows
     float* l1;             // [gridDim.x][Je * I] per-block level-1 binary32 buckets
-    float* ckpt;           // [n_ck][gridDim.x * warps * ring_slots_per_warp()] checkpoints of x
+    float* ckpt;           // [n_ck][gridDim.x * warps * ring_slots_per_warp() * ppl] checkpoints of x
     int n_ck;
     int flush_every;       // reverse batches between level-1 -> level-2 drains
     int grid_smem;         // 1: sigma pairs staged in shared memory, 0: read through L1
@@ -123,7 +124,8 @@ cudaError_t launch_bump_finalize(const double* partials, int G, int row_words, d
                                  long long n_paths, double eps, double eps_S, double* out,
                                  unsigned int* tile_counter, cudaStream_t s);
 
-size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra = false);
+size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra = false,
+                     int ppl = 1);
 
 // Binary64 paths (lv_fp64.cu): the full-FP64 reference adjoint and the
 // binary64 bump baseline, main reading only.
@@ -165,7 +167,7 @@ cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks
                       cudaStream_t s);
 cudaError_t launch_finalize(const FinalizeParams& f, cudaStream_t s);
 cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, int model,
-                         bool extra, size_t smem, int* blocks_per_sm);
+                         bool extra, size_t smem, int* blocks_per_sm, int ppl = 1);
 
 // The kernels of the other models (lv_model1.cu .. lv_model3.cu, one
 // translation unit each so that they compile in parallel); they exist for
@@ -281,7 +283,7 @@ struct lv_surface_s {
     int phi = 1;
     cudaStream_t stream = nullptr;
     int acc_mode = LV_ACC_FP64;
-    int cfg_block = 0, cfg_k = 0, cfg_bps = 0;
+    int cfg_block = 0, cfg_k = 0, cfg_bps = 0, cfg_ppl = 0;
     void* d_scratch = nullptr;
     size_t scratch_bytes = 0;
     double* d_res = nullptr;         // [3 + I*J] result of the host-output calls

@@ -102,9 +102,9 @@ __global__ void __launch_bounds__(32) finalize_kernel(const double* __restrict__
 
 }  // namespace
 
-size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra)
+size_t mc_smem_bytes(int I, int Je, int N, int block, bool greeks, bool grid_smem, bool extra, int ppl)
 {
-    return smem_layout(I, Je, N, block, greeks, grid_smem, extra).total;
+    return smem_layout(I, Je, N, block, greeks, grid_smem, extra, ppl).total;
 }
 
 int ring_slots_per_warp() { return kRing * kTile; }
@@ -123,10 +123,11 @@ cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks
 }
 
 cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, int model,
-                         bool extra, size_t smem, int* bps)
+                         bool extra, size_t smem, int* bps, int ppl)
 {
+    if (model != 0 && ppl != 1) return cudaErrorInvalidValue;
     switch (model) {
-    case 0: return occupancy_model_impl<0>(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
+    case 0: return occupancy_model_impl<0>(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps, ppl);
     case 1: return mc_occupancy_model1(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
     case 2: return mc_occupancy_model2(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
     case 3: return mc_occupancy_model3(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);

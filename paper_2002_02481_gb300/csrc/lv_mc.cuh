@@ -51,7 +51,8 @@ namespace {
 constexpr int kTile = 32;      // paths per warp tile of the adjoint kernel (one per lane)
 constexpr int kPriceTile = 64; // paths per warp tile of the price kernel (two per lane)
 constexpr int kRing = 4;       // checkpoint slot groups of kTile per warp
-constexpr int kQueue = 64;     // per-warp FIFO capacity (entries; < 32 + kTile never overflows)
+constexpr int kQueue = 64;     // per-warp FIFO capacity per path a lane runs in a forward tile
+                               // (entries; < 32 + kTile * ppl never overflows kQueue * ppl)
 constexpr int kMaxWarps = 8;   // blockDim.x <= 256 (the adjoint kernel runs at most 128)
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
@@ -69,9 +70,10 @@ struct SmemLayout {
 };
 
 // extra: the adjoint kernel that also sums d V / d r and d V / d T (the time
-// slope table and two more accumulators per thread).
+// slope table and two more accumulators per thread); ppl: paths per lane of
+// the adjoint's forward tiles (the FIFO grows with it).
 __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int block, bool greeks, bool grid_smem,
-                                                  bool extra = false)
+                                                  bool extra = false, int ppl = 1)
 {
     const int W = block / 32;
     SmemLayout L;
@@ -81,9 +83,9 @@ __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int bloc
     L.node = o;  o += align16(sizeof(float) * (size_t)I);
     L.ab = o;    o += align16(sizeof(float2) * (size_t)I);
     L.tdt = o;   if (extra) o += align16(sizeof(float) * (size_t)N);
-    L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
-    L.qrel = o;  if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue);
-    L.qxb = o;   if (greeks) o += align16(sizeof(float) * (size_t)W * kQueue);
+    L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue * ppl);
+    L.qrel = o;  if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue * ppl);
+    L.qxb = o;   if (greeks) o += align16(sizeof(float) * (size_t)W * kQueue * ppl);
     L.acc = o;   o += align16(sizeof(AccSlot) * (extra ? 5 : 3) * (size_t)block);
     L.red = o;   o += align16(sizeof(double) * 3 * kMaxWarps);
     L.total = o;
@@ -161,10 +163,11 @@ __device__ __forceinline__ void block_scalars(double a, double b, double c, doub
     }
 }
 
-__device__ __forceinline__ int claim_tile(unsigned int* counter)
+// Claims n consecutive tiles for the warp; returns the first.
+__device__ __forceinline__ int claim_tile(unsigned int* counter, unsigned n = 1u)
 {
     int t = 0;
-    if ((threadIdx.x & 31) == 0) t = (int)atomicAdd(counter, 1u);
+    if ((threadIdx.x & 31) == 0) t = (int)atomicAdd(counter, n);
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
@@ -189,18 +192,25 @@ __device__ __forceinline__ void drain_buckets(float* l1, int nIJ, double* wrow)
     }
 }
 
-template <int KCK, int ACC, bool DBG, bool GS, int MODEL, bool EXTRA = false>
+// PPL: paths per lane of a forward tile. With PPL = 2 a warp claims two
+// consecutive 32-path tiles and runs them interleaved (forward_path2: two
+// independent dependency chains per lane, the per-step time data loaded once);
+// each path's arithmetic is that of PPL = 1, the ring groups and the FIFO
+// hold twice as many entries, and the reverse batches are unchanged.
+template <int KCK, int ACC, bool DBG, bool GS, int MODEL, bool EXTRA = false, int PPL = 1>
 __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__ McParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int kSlots = kTile * PPL;      // checkpoint slots per ring group
+    constexpr int kQcap = kQueue * PPL;      // FIFO entries per warp
     const int B = blockDim.x, W = B >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS, EXTRA);
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS, EXTRA, PPL);
     stage_grid<GS, EXTRA>(P, smem, L);
     float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);    // this block's level-1 buckets
-    int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQueue;
-    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
-    float* q_xb = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
+    int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQcap;
+    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQcap;
+    float* q_xb = reinterpret_cast<float*>(smem + L.qxb) + warp * kQcap;
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     const int nIJ = P.Je * P.I;
     for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
@@ -222,25 +232,25 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                       GS ? reinterpret_cast<const float2*>(smem + L.sig) : P.sig2,
                       reinterpret_cast<const float*>(smem + L.node), reinterpret_cast<const float2*>(smem + L.ab),
                       reinterpret_cast<const float*>(smem + L.tdt) };
-    const size_t cks = (size_t)gridDim.x * W * kRing * kTile;   // checkpoint stride
-    float* const ckw = P.ckpt + (size_t)wid * kRing * kTile;     // this warp's slots
+    const size_t cks = (size_t)gridDim.x * W * kRing * kSlots;  // checkpoint stride
+    float* const ckw = P.ckpt + (size_t)wid * kRing * kSlots;    // this warp's slots
 
     AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
     acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
     if (EXTRA) acc[3 * B] = acc[4 * B] = AccSlot{0.0, 0.0f, 0.0f};    // d V / d r, d V / d T
     int q_head = 0, q_count = 0, batches = 0;
     unsigned fwd_count = 0;
-    int tile = claim_tile(P.tile_counter);
+    int tile = claim_tile(P.tile_counter, PPL);
 
     while (true) {
         const int g_next = (int)(fwd_count % kRing);
         const bool more = tile < P.n_tiles;
-        const bool reuse = more && q_count > 0 && q_slot[q_head] / kTile == g_next;
+        const bool reuse = more && q_count > 0 && q_slot[q_head] / kSlots == g_next;
         if (q_count >= 32 || (!more && q_count > 0) || reuse) {
             // ---------------- reverse batch over up to 32 queued paths
             const int nb = min(32, q_count);
             if (lane < nb) {
-                const int e = (q_head + lane) & (kQueue - 1);
+                const int e = (q_head + lane) & (kQcap - 1);
                 const int slot = q_slot[e];
                 const long long rel = q_rel[e];
                 float xbar = q_xb[e];
@@ -255,13 +265,54 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 }
                 if (DBG) P.dbg_xbar0[rel] = xbar;
             }
-            q_head = (q_head + nb) & (kQueue - 1);
+            q_head = (q_head + nb) & (kQcap - 1);
             q_count -= nb;
             __syncwarp();
             if (++batches % P.flush_every == 0) drain_buckets<ACC>(l1, nIJ, wrow);
             continue;
         }
         if (!more) break;
+
+        if constexpr (PPL == 2) {
+            // ---------------- forward tiles tile, tile + 1: two paths per lane
+            const long long rel_a = (long long)tile * kTile + lane, rel_b = rel_a + kTile;
+            const int slot_a = g_next * kSlots + lane, slot_b = slot_a + kTile;
+            float xa = 0.0f, xb = 0.0f;
+            if (rel_a < P.n_paths) {
+                uint32_t c1a, c2a, c1b, c2b;
+                path_counter(P, rel_a, c1a, c2a);
+                path_counter(P, rel_b, c1b, c2b);
+                float ya, yb;
+                forward_path2<KCK, true, false, MODEL>(P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b, cks,
+                                                       rel_a, rel_b, false, ya, yb);
+                float V;
+                payoff<MODEL>(P, ya, V, xa);
+                acc_add<ACC>(acc[0], V);
+                acc_add<ACC>(acc[B], V * V);
+                if (rel_b < P.n_paths) {
+                    payoff<MODEL>(P, yb, V, xb);
+                    acc_add<ACC>(acc[0], V);
+                    acc_add<ACC>(acc[B], V * V);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float xbarN = h ? xb : xa;
+                const bool live = xbarN != 0.0f;
+                const unsigned bal = __ballot_sync(0xffffffffu, live);
+                if (live) {
+                    const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
+                    q_slot[e] = h ? slot_b : slot_a;
+                    q_rel[e] = (int)(h ? rel_b : rel_a);
+                    q_xb[e] = xbarN;
+                }
+                q_count += __popc(bal);
+            }
+            ++fwd_count;
+            __syncwarp();
+            tile = claim_tile(P.tile_counter, PPL);
+            continue;
+        }
 
         // ---------------- forward tile of 32 paths into slot group g_next
         const long long rel = (long long)tile * kTile + lane;
@@ -289,7 +340,7 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
         const bool live = xbarN != 0.0f;
         const unsigned bal = __ballot_sync(0xffffffffu, live);
         if (live) {
-            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
+            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
             q_slot[e] = slot;
             q_rel[e] = (int)rel;
             q_xb[e] = xbarN;
@@ -297,7 +348,7 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
         q_count += __popc(bal);
         ++fwd_count;
         __syncwarp();
-        tile = claim_tile(P.tile_counter);
+        tile = claim_tile(P.tile_counter, PPL);
     }
 
     // fold: remaining level-1 buckets (and, in Kahan mode, every warp row of
@@ -570,8 +621,23 @@ cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
 // Calls f(kernel, flag) with the instantiation for (greeks, k, acc, dbg, gs)
 // of model MODEL: k in {4, 8, 16, 32} for model 0, {4, 8} for the others.
 template <int MODEL, bool GS, typename F>
-cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, bool extra, F&& f)
+cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, bool extra, F&& f, int ppl = 1)
 {
+    if (ppl == 2) {        // two paths per lane: the main reading's reverse sweep, k = 4 or 8
+        if constexpr (MODEL == 0) {
+            static bool cp[4] = {};
+            if (!greeks || dbg || extra || method != LV_ADJ_REVERSE) return cudaErrorInvalidValue;
+            switch (k * 2 + acc) {
+            case 8: return f(adjoint_kernel<4, 0, false, GS, 0, false, 2>, cp[0]);
+            case 9: return f(adjoint_kernel<4, 1, false, GS, 0, false, 2>, cp[1]);
+            case 16: return f(adjoint_kernel<8, 0, false, GS, 0, false, 2>, cp[2]);
+            case 17: return f(adjoint_kernel<8, 1, false, GS, 0, false, 2>, cp[3]);
+            default: break;
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
+    if (ppl != 1) return cudaErrorInvalidValue;
     if (method == kMethodVanna) {     // second-order buckets: main reading, binary64 level 2
         if constexpr (MODEL == 0) {
             static bool cv = false;
@@ -628,17 +694,18 @@ cudaError_t launch_model_impl(const McParams& p, int grid, int block, int k, boo
         return launch_configured(kernel, configured, p, grid, block, smem, s);
     };
     const bool dbg = p.dbg_xN != nullptr;
-    return p.grid_smem ? with_kernel_gs<MODEL, true>(greeks, k, p.acc_mode, dbg, p.method, p.extra != 0, run)
-                       : with_kernel_gs<MODEL, false>(greeks, k, p.acc_mode, dbg, p.method, p.extra != 0, run);
+    const int ppl = p.ppl > 1 ? p.ppl : 1;
+    return p.grid_smem ? with_kernel_gs<MODEL, true>(greeks, k, p.acc_mode, dbg, p.method, p.extra != 0, run, ppl)
+                       : with_kernel_gs<MODEL, false>(greeks, k, p.acc_mode, dbg, p.method, p.extra != 0, run, ppl);
 }
 
 template <int MODEL>
 cudaError_t occupancy_model_impl(int block, int k, bool greeks, int acc, bool dbg, bool gs, int method, bool extra,
-                                 size_t smem, int* bps)
+                                 size_t smem, int* bps, int ppl = 1)
 {
     auto occ = [&](auto kernel, bool&) { return occupancy(kernel, block, smem, bps); };
-    return gs ? with_kernel_gs<MODEL, true>(greeks, k, acc, dbg, method, extra, occ)
-              : with_kernel_gs<MODEL, false>(greeks, k, acc, dbg, method, extra, occ);
+    return gs ? with_kernel_gs<MODEL, true>(greeks, k, acc, dbg, method, extra, occ, ppl)
+              : with_kernel_gs<MODEL, false>(greeks, k, acc, dbg, method, extra, occ, ppl);
 }
 
 }  // namespace

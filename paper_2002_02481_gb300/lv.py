@@ -75,6 +75,8 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_set_scheme": [vp, i32],
         "lv_set_launch": [vp, i32, i32, i32],
         "lv_set_kernel_events": [vp, vp, vp],
+        "lv_set_paths_per_lane": [vp, i32],
+        "lv_get_paths_per_lane": [vp, i32, c.POINTER(i32)],
         "lv_tune": [vp, d, d, d, d, i32, i64, u64, c.POINTER(i32), c.POINTER(i32), c.POINTER(d)],
         "lv_get_launch": [vp, i32, i32, c.POINTER(i32), c.POINTER(i32), c.POINTER(i32)],
         "lv_price": [vp, d, d, d, d, i32, i64, u64, dp, dp],
@@ -222,6 +224,16 @@ class Surface:
 
     def set_launch(self, block: int = 0, k: int = 0, blocks_per_sm: int = 0) -> None:
         _check(self.lib, self.lib.lv_set_launch(self.h, int(block), int(k), int(blocks_per_sm)), "lv_set_launch")
+
+    def set_paths_per_lane(self, ppl: int) -> None:
+        """1 or 2 paths per lane in the adjoint's forward tiles (0: tuned / default)."""
+        _check(self.lib, self.lib.lv_set_paths_per_lane(self.h, int(ppl)), "lv_set_paths_per_lane")
+
+    def get_paths_per_lane(self, n_steps: int) -> int:
+        p = ctypes.c_int32()
+        _check(self.lib, self.lib.lv_get_paths_per_lane(self.h, int(n_steps), ctypes.byref(p)),
+               "lv_get_paths_per_lane")
+        return p.value
 
     def set_kernel_events(self, start_ptr: int, end_ptr: int) -> None:
         _check(self.lib, self.lib.lv_set_kernel_events(self.h, ctypes.c_void_p(start_ptr or None),

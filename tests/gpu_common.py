@@ -40,7 +40,7 @@ DRIFT_FACTOR = 4.0       # decision band = DRIFT_FACTOR * max |dx_N| + INDEX_ROU
 INDEX_ROUNDING = 2.0 ** -20   # relative error of the kernel's binary32 cell index, in S
 
 
-def make_surface(w_surf, opt, lib, launch=None, accumulation=0, method=lv.LV_ADJ_REVERSE):
+def make_surface(w_surf, opt, lib, launch=None, accumulation=0, method=lv.LV_ADJ_REVERSE, ppl=0):
     s = lv.Surface.from_workload(w_surf, lib)
     s.set_option_type(opt.phi)
     s.set_accumulation(accumulation)
@@ -49,6 +49,8 @@ def make_surface(w_surf, opt, lib, launch=None, accumulation=0, method=lv.LV_ADJ
     s.set_scheme(getattr(opt, "scheme", 0))
     if launch:
         s.set_launch(*launch)
+    if ppl:
+        s.set_paths_per_lane(ppl)
     return s
 
 
@@ -115,12 +117,12 @@ def compare_aggregates(gpu_price, gpu_delta, gpu_vega, ref, label=""):
     return dict(price_rel=e_p, delta_rel=e_d, vega_of_max=e_v)
 
 
-def full_parity(w_surf, opt, lib, launch=None, accumulation=0, label="", method=lv.LV_ADJ_REVERSE):
+def full_parity(w_surf, opt, lib, launch=None, accumulation=0, label="", method=lv.LV_ADJ_REVERSE, ppl=0):
     """Per-path check on every path, then aggregates against the oracle with
     the kernel's kink decisions imposed. The per-path check and the decisions
     come from the reverse sweep's diagnostics kernel, whose forward arithmetic
     the tangent-ratio kernel shares."""
-    gs = make_surface(w_surf, opt, lib, launch, accumulation, method)
+    gs = make_surface(w_surf, opt, lib, launch, accumulation, method, ppl)
     decisions, stats = per_path(gs, w_surf, opt)
     ref = oracle.finalize(oracle.run_sums(w_surf, opt, decisions=decisions), opt.n_paths, opt.S0,
                           w_surf.n_spot * w_surf.n_time)

@@ -103,6 +103,55 @@ def test_large_grid_timed_shape(lib):
             G.full_parity(surf, opt, lib, launch=(128, 4, 0), label="large k=4"))
 
 
+@pytest.mark.parametrize("ppl_case", ["small", "paper 2^18", "edge: 33 paths", "edge: put, uneven grid"])
+def test_two_paths_per_lane(ppl_case, lib):
+    """Two paths per lane in the forward tiles (a warp claims two tiles and
+    runs them interleaved): the same per-path arithmetic, checked against the
+    oracle path for path, at k = 4 and 8 and in both level-2 modes."""
+    if ppl_case == "small":
+        surf, opt = W.config_small()
+        cases = [((128, 4, 0), 0), ((128, 8, 0), 1)]
+    elif ppl_case == "paper 2^18":
+        surf, opt = W.config_paper_shape()
+        opt.n_paths = 1 << 18
+        cases = [((128, 4, 0), 0)]
+    elif ppl_case == "edge: 33 paths":
+        _, surf, opt = EDGE[5]
+        cases = [((64, 4, 0), 0)]
+    else:
+        _, surf, opt = EDGE[2]
+        cases = [((128, 8, 0), 1)]
+    for launch, acc in cases:
+        s = G.make_surface(surf, opt, lib, launch=launch, accumulation=acc, ppl=2)
+        assert s.get_paths_per_lane(opt.n_steps) == 2
+        s.close()
+        _report(f"two paths per lane: {ppl_case} {launch} acc={acc}",
+                G.full_parity(surf, opt, lib, launch=launch, accumulation=acc, ppl=2, label=ppl_case))
+
+
+def test_two_paths_per_lane_equals_one(lib):
+    """Same paths, same per-path arithmetic: one or two paths per lane agree to
+    reduction-order rounding; where two paths per lane do not exist the call
+    runs one."""
+    surf, opt = W.config_paper_shape()
+    opt.n_paths = 1 << 17
+    a = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=1)
+    b = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=2)
+    pa, da, va = a.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    pb, db, vb = b.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert abs(pb - pa) <= 1e-12 * abs(pa) and abs(db - da) <= 1e-9 * abs(da)
+    assert np.max(np.abs(vb - va)) <= 1e-6 * np.max(np.abs(va))
+    b.set_launch(128, 16, 0)
+    assert b.get_paths_per_lane(opt.n_steps) == 1
+    b.set_launch(128, 4, 0)
+    b.set_scheme(lv.LV_SCHEME_S)
+    assert b.get_paths_per_lane(opt.n_steps) == 1
+    with pytest.raises(lv.LVError):
+        b.set_paths_per_lane(3)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("launch", [(128, 4, 0), (96, 8, 0), (128, 16, 0), (128, 32, 1), (64, 8, 2), (32, 4, 0)])
 def test_launch_shape_invariance(launch, lib):
     """Per-path arithmetic does not depend on the launch shape; results agree

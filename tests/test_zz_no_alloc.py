@@ -121,3 +121,32 @@ def test_kahan_mode_on_a_narrowed_launch():
         assert abs(o[1] - r[1]) <= 1e-8 * abs(r[1]), (call, o[1], r[1])
         assert np.max(np.abs(o[3:] - r[3:])) <= 1e-6 * np.max(np.abs(r[3:])), call
     s.close()
+
+
+def test_two_paths_per_lane():
+    """With two paths per lane the checkpoint ring per warp doubles; the plan
+    inside the array accounts for it, and two calls in a row match the
+    allocating entry point."""
+    lib, lv, torch = _lib()
+    surf, opt = W.config_paper_shape()
+    s = lv.Surface.from_workload(surf, lib)
+    s.set_launch(128, 4, 0)
+    s.set_paths_per_lane(2)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    n = 3 + surf.n_spot * surf.n_time
+    ref = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, ref.data_ptr())
+    torch.cuda.synchronize()
+    r = ref.cpu().numpy()
+    for call in range(2):
+        out = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.lv_price_greeks_device_noalloc(s.h, opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths,
+                                                opt.seed, out.data_ptr())
+        assert st == lv.LV_OK, lib.lv_last_error().decode()
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert np.all(np.isfinite(o)), f"call {call}: non-finite output"
+        assert abs(o[0] - r[0]) <= 1e-12 * abs(r[0]), (call, o[0], r[0])
+        assert abs(o[1] - r[1]) <= 1e-9 * abs(r[1]), (call, o[1], r[1])
+        assert np.max(np.abs(o[3:] - r[3:])) <= 1e-6 * np.max(np.abs(r[3:])), call
+    s.close()
