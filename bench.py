@@ -235,7 +235,8 @@ def other_workloads(lib, dev, ev0, ev1):
         ms = time_call(lambda: S.price_greeks_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths,
                                                       opt.seed, d.data_ptr()), ev0, ev1)
         res[name] = {"adjoint_kernel_ms": ms, "path_steps_per_s": opt.n_paths * opt.n_steps / (ms * 1e-3),
-                     "launch": list(S.get_launch(opt.n_steps, True))}
+                     "launch": list(S.get_launch(opt.n_steps, True)),
+                     "paths_per_lane": S.get_paths_per_lane(opt.n_steps)}
         S.close()
 
     single("small 20x10, 52 steps, 2^14 paths", *W.config_small())
@@ -287,6 +288,7 @@ def other_workloads(lib, dev, ev0, ev1):
     res["book 8 grids x 64 options, graph replay"] = {
         "ms_per_run_wall": wall * 1e3, "path_steps": ps, "path_steps_per_s": ps / wall,
         "paths": sum(it.n_paths for it in items), "tuned": {"block": blk, "k": k, "item_paths": item_paths,
+                                                            "paths_per_lane": book.paths_per_lane(),
                                                             "kernel_ms": tune_ms}}
     # the same book as aggregated risk per surface (position weights +-1)
     book.set_weights([1.0 if it.phi > 0 else -1.0 for it in items])
@@ -591,7 +593,9 @@ def run_ours(args):
         live = live_fraction(S, opt)
         roofline = roofline_block(kern, P * opt.n_steps, live, pipe_peaks, mhz, n_sm, profiled_record())
         blk, kk, bps = S.get_launch(opt.n_steps, True)
-        roofline["kernel"] = f"adjoint_kernel<k={kk},binary64 level 2> (block {blk}, {bps} blocks/SM)"
+        ppl = S.get_paths_per_lane(opt.n_steps)
+        roofline["kernel"] = (f"adjoint_kernel<k={kk},binary64 level 2,{ppl} path(s) per lane> "
+                              f"(block {blk}, {bps} blocks/SM)")
         roofline["clock_mhz"] = mhz
         workloads = None
         if not args.no_extra:
@@ -629,7 +633,7 @@ def run_ours(args):
             "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": "30x60", "n_steps": opt.n_steps, "n_paths_per_gpu": P,
-                       "launch": {"block": tuned[0], "k": tuned[1],
+                       "launch": {"block": tuned[0], "k": tuned[1], "paths_per_lane": ppl,
                                   "source": "--launch" if args.launch else "lv_tune"},
                        "l2": "256 MB buffer rewritten between timed steps (outside the timed region)",
                        "parallelism": f"path-range shards x{ws}" + (", one all-reduce of 3+1800 sums per step"

@@ -446,12 +446,22 @@ lv_status lv_book_run(lv_book_t b, double S0, double r, uint64_t seed, double* o
  * enqueued on the book's stream without synchronising. */
 lv_status lv_book_run_device(lv_book_t b, double S0, double r, uint64_t seed, double* d_out);
 
-/* Autotuner: times the book over launch shapes (threads per block,
- * checkpoint interval, paths per work item), keeps the fastest, and appends
- * it to the LV_TUNE_CACHE file when that variable is set. Outputs the
- * chosen shape and its time in milliseconds (any pointer may be NULL). */
+/* Autotuner: times the book over launch shapes (threads per block 64 / 128,
+ * checkpoint interval 4 / 8, paths per work item 2K / 8K / 32K, one or two
+ * paths per lane of the forward tiles), keeps the fastest, and appends it
+ * to the LV_TUNE_CACHE file when that variable is set (a new book of the
+ * same shape starts from it). Outputs the chosen shape and its time in
+ * milliseconds (any pointer may be NULL); lv_book_paths_per_lane reads the
+ * paths per lane in use. */
 lv_status lv_book_tune(lv_book_t b, double S0, double r, uint64_t seed, int32_t* out_block, int32_t* out_k,
                        int32_t* out_item_paths, double* out_ms);
+lv_status lv_book_paths_per_lane(lv_book_t b, int32_t* ppl);
+
+/* Sets the book's launch shape explicitly (as the tuner would): threads per
+ * block (multiple of 32 in [32, 128]), checkpoint interval k (4 or 8),
+ * paths per work item (a multiple of 32), paths per lane (1 or 2). Drops a
+ * captured graph; the next lv_book_run captures again. */
+lv_status lv_book_set_launch(lv_book_t b, int32_t block, int32_t k, int32_t item_paths, int32_t ppl);
 
 /* Book-level aggregated risk (the portfolio view of the first-order risk of
  * Sec. I and V: one set of vega buckets per surface instead of one per

@@ -34,7 +34,7 @@ namespace {
 std::mutex g_tune_mu;
 }  // namespace
 
-bool lv::tune_cache_lookup(const std::string& key, int vals[3])
+bool lv::tune_cache_lookup(const std::string& key, int vals[4])
 {
     const char* path = std::getenv("LV_TUNE_CACHE");
     if (!path || !*path) return false;
@@ -45,12 +45,13 @@ bool lv::tune_cache_lookup(const std::string& key, int vals[3])
     bool found = false;
     while (std::fgets(line, sizeof line, f)) {
         char kbuf[512];
-        int a = 0, b = 0, c = 0;
+        int a = 0, b = 0, c = 0, d = 0;
         double ms = 0.0;
-        if (std::sscanf(line, "%511s %d %d %d %lf", kbuf, &a, &b, &c, &ms) == 5 && key == kbuf) {
+        if (std::sscanf(line, "%511s %d %d %d %d %lf", kbuf, &a, &b, &c, &d, &ms) == 6 && key == kbuf) {
             vals[0] = a;
             vals[1] = b;
             vals[2] = c;
+            vals[3] = d;
             found = true;
         }
     }
@@ -58,14 +59,14 @@ bool lv::tune_cache_lookup(const std::string& key, int vals[3])
     return found;
 }
 
-void lv::tune_cache_append(const std::string& key, const int vals[3], double ms)
+void lv::tune_cache_append(const std::string& key, const int vals[4], double ms)
 {
     const char* path = std::getenv("LV_TUNE_CACHE");
     if (!path || !*path) return;
     std::lock_guard<std::mutex> lock(g_tune_mu);
     FILE* f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "%s %d %d %d %.4f\n", key.c_str(), vals[0], vals[1], vals[2], ms);
+    std::fprintf(f, "%s %d %d %d %d %.4f\n", key.c_str(), vals[0], vals[1], vals[2], vals[3], ms);
     std::fclose(f);
 }
 
@@ -228,7 +229,7 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
     int ppl = h->cfg_ppl ? h->cfg_ppl : 1;
     const char* cache = std::getenv("LV_TUNE_CACHE");
     if (greeks && !dbg && !h->cfg_block && !h->cfg_k && !h->cfg_ppl && cache && *cache) {
-        int v[3];
+        int v[4];
         if (lv::tune_cache_lookup(adjoint_tune_key(h, n_steps), v) && v[0] >= 32 && v[0] <= 128 &&
             v[0] % 32 == 0 && (v[1] == 4 || v[1] == 8 || v[1] == 16 || v[1] == 32)) {
             *block = v[0];
@@ -895,7 +896,7 @@ lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32
     h->cfg_k = bk;
     h->cfg_bps = 0;
     h->cfg_ppl = bp;
-    const int v[3] = {bb, bk, bp};
+    const int v[4] = {bb, bk, bp, 0};
     lv::tune_cache_append(adjoint_tune_key(h, n_steps), v, best);
     if (out_block) *out_block = bb;
     if (out_k) *out_k = bk;

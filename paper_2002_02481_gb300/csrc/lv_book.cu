@@ -30,7 +30,7 @@ struct BookSmem {
     size_t params, tab, sig, node, ab, qslot, qrel, qxb, acc, red, ctl, total;
 };
 
-__host__ __device__ inline BookSmem book_layout(int maxI, int maxJe, int maxN, int block)
+__host__ __device__ inline BookSmem book_layout(int maxI, int maxJe, int maxN, int block, int ppl = 1)
 {
     const int W = block / 32;
     BookSmem L;
@@ -40,9 +40,9 @@ __host__ __device__ inline BookSmem book_layout(int maxI, int maxJe, int maxN, i
     L.sig = o;    o += b16(sizeof(float2) * (size_t)maxJe * (maxI - 1));
     L.node = o;   o += b16(sizeof(float) * (size_t)maxI);
     L.ab = o;     o += b16(sizeof(float2) * (size_t)maxI);
-    L.qslot = o;  o += b16(sizeof(int) * (size_t)W * kBQueue);
-    L.qrel = o;   o += b16(sizeof(int) * (size_t)W * kBQueue);
-    L.qxb = o;    o += b16(sizeof(float) * (size_t)W * kBQueue);
+    L.qslot = o;  o += b16(sizeof(int) * (size_t)W * kBQueue * ppl);
+    L.qrel = o;   o += b16(sizeof(int) * (size_t)W * kBQueue * ppl);
+    L.qxb = o;    o += b16(sizeof(float) * (size_t)W * kBQueue * ppl);
     L.acc = o;    o += b16(sizeof(double) * 3 * (size_t)block);
     L.red = o;    o += b16(sizeof(double) * 3 * kBMaxWarps);
     L.ctl = o;    o += b16(sizeof(int) * 4);
@@ -50,10 +50,11 @@ __host__ __device__ inline BookSmem book_layout(int maxI, int maxJe, int maxN, i
     return L;
 }
 
-__device__ __forceinline__ int warp_claim(int* counter)
+// Claims n consecutive tiles of the block's current item for the warp.
+__device__ __forceinline__ int warp_claim(int* counter, int n = 1)
 {
     int t = 0;
-    if ((threadIdx.x & 31) == 0) t = atomicAdd(counter, 1);
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(counter, n);
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
@@ -97,26 +98,31 @@ __device__ void build_params(const BookParams& B, int inst, McParams* out)
     *out = P;
 }
 
-template <int KCK>
+// PPL: paths per lane of a forward tile, as in the single-option kernel: a
+// warp claims PPL consecutive 32-path tiles of its item and runs them
+// interleaved; the ring groups and the FIFO grow with it.
+template <int KCK, int PPL>
 __global__ void __launch_bounds__(128, 5) book_kernel(const __grid_constant__ BookParams B)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int kSlots = 32 * PPL;
+    constexpr int kQcap = kBQueue * PPL;
     const int Bk = blockDim.x, W = Bk >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const BookSmem L = book_layout(B.max_I, B.max_Je, B.max_N, Bk);
+    const BookSmem L = book_layout(B.max_I, B.max_Je, B.max_N, Bk, PPL);
     McParams* s_par = reinterpret_cast<McParams*>(smem + L.params);
     int4* s_tab = reinterpret_cast<int4*>(smem + L.tab);
     float2* s_sig = reinterpret_cast<float2*>(smem + L.sig);
     float* s_node = reinterpret_cast<float*>(smem + L.node);
     float2* s_ab = reinterpret_cast<float2*>(smem + L.ab);
-    int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kBQueue;
-    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kBQueue;
-    float* q_xb = reinterpret_cast<float*>(smem + L.qxb) + warp * kBQueue;
+    int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQcap;
+    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQcap;
+    float* q_xb = reinterpret_cast<float*>(smem + L.qxb) + warp * kQcap;
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     int* s_ctl = reinterpret_cast<int*>(smem + L.ctl);   // [0] item, [1] next tile, [2] staged option
     float* l1 = B.l1 + (size_t)blockIdx.x * B.max_IJe;
-    const size_t cks = (size_t)gridDim.x * W * kBRing * 32;
-    float* const ckw = B.ckpt + (size_t)(blockIdx.x * W + warp) * kBRing * 32;
+    const size_t cks = (size_t)gridDim.x * W * kBRing * kSlots;
+    float* const ckw = B.ckpt + (size_t)(blockIdx.x * W + warp) * kBRing * kSlots;
     const SmemGrid g{ s_tab, s_sig, s_node, s_ab };
 
     for (int e = tid; e < B.max_IJe; e += Bk) l1[e] = 0.0f;
@@ -150,27 +156,70 @@ __global__ void __launch_bounds__(128, 5) book_kernel(const __grid_constant__ Bo
         acc[0] = acc[Bk] = acc[2 * Bk] = 0.0;
         int q_head = 0, q_count = 0;
         unsigned fwd_count = 0;
-        int tile = warp_claim(&s_ctl[1]);
+        int tile = warp_claim(&s_ctl[1], PPL);
         while (true) {
             const int g_next = (int)(fwd_count % kBRing);
             const bool more = tile < tile_end;
-            const bool reuse = more && q_count > 0 && (q_slot[q_head] >> 5) == g_next;
+            const bool reuse = more && q_count > 0 && q_slot[q_head] / kSlots == g_next;
             if (q_count >= 32 || (!more && q_count > 0) || reuse) {
                 const int nb = min(32, q_count);
                 if (lane < nb) {
-                    const int e = (q_head + lane) & (kBQueue - 1);
+                    const int e = (q_head + lane) & (kQcap - 1);
                     const long long rel = q_rel[e];
                     uint32_t c1, c2;
                     path_counter(P, rel, c1, c2);
                     const float xbar = reverse_path<KCK>(P, g, c1, c2, ckw + q_slot[e], cks, q_xb[e], l1);
                     acc[2 * Bk] += (double)xbar;
                 }
-                q_head = (q_head + nb) & (kBQueue - 1);
+                q_head = (q_head + nb) & (kQcap - 1);
                 q_count -= nb;
                 __syncwarp();
                 continue;
             }
             if (!more) break;
+            if constexpr (PPL == 2) {
+                // tiles tile and tile + 1 of this item: two paths per lane (tile + 1 may lie
+                // beyond the item, whose paths belong to another block's item)
+                const long long rel_a = (long long)tile * 32 + lane, rel_b = rel_a + 32;
+                const bool act_b = tile + 1 < tile_end && rel_b < P.n_paths;
+                const int slot_a = g_next * kSlots + lane, slot_b = slot_a + 32;
+                float xa = 0.0f, xb = 0.0f;
+                if (rel_a < P.n_paths) {
+                    uint32_t c1a, c2a, c1b, c2b;
+                    path_counter(P, rel_a, c1a, c2a);
+                    path_counter(P, rel_b, c1b, c2b);
+                    float ya, yb;
+                    forward_path2<KCK, true, false>(P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b, cks, rel_a,
+                                                    rel_b, false, ya, yb);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        if (h == 1 && !act_b) break;
+                        const float SN = exp2f(h ? yb : ya);
+                        const float itm = P.phi * (SN - P.K);
+                        const float V = itm > 0.0f ? P.disc * itm : 0.0f;
+                        (h ? xb : xa) = itm > 0.0f ? P.disc * P.phi * SN : 0.0f;
+                        acc[0] += (double)V;
+                        acc[Bk] += (double)V * (double)V;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float xbarN = h ? xb : xa;
+                    const bool live = xbarN != 0.0f;
+                    const unsigned bal = __ballot_sync(0xffffffffu, live);
+                    if (live) {
+                        const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
+                        q_slot[e] = h ? slot_b : slot_a;
+                        q_rel[e] = (int)(h ? rel_b : rel_a);
+                        q_xb[e] = xbarN;
+                    }
+                    q_count += __popc(bal);
+                }
+                ++fwd_count;
+                __syncwarp();
+                tile = warp_claim(&s_ctl[1], PPL);
+                continue;
+            }
             const long long rel = (long long)tile * 32 + lane;
             const bool active = rel < P.n_paths;
             const int slot = g_next * 32 + lane;
@@ -189,7 +238,7 @@ __global__ void __launch_bounds__(128, 5) book_kernel(const __grid_constant__ Bo
             const bool live = xbarN != 0.0f;
             const unsigned bal = __ballot_sync(0xffffffffu, live);
             if (live) {
-                const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kBQueue - 1);
+                const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
                 q_slot[e] = slot;
                 q_rel[e] = (int)rel;
                 q_xb[e] = xbarN;
@@ -197,7 +246,7 @@ __global__ void __launch_bounds__(128, 5) book_kernel(const __grid_constant__ Bo
             q_count += __popc(bal);
             ++fwd_count;
             __syncwarp();
-            tile = warp_claim(&s_ctl[1]);
+            tile = warp_claim(&s_ctl[1], PPL);
         }
 
         // end of item: add this block's sums to the option's binary64 sums
@@ -298,44 +347,58 @@ __global__ void book_risk_finalize_kernel(const BookInst* __restrict__ insts, co
     }
 }
 
-template <int KCK>
+template <int KCK, int PPL>
 cudaError_t book_launch_k(const BookParams& b, int grid, int block, size_t smem, cudaStream_t s)
 {
-    book_kernel<KCK><<<grid, block, smem, s>>>(b);
+    book_kernel<KCK, PPL><<<grid, block, smem, s>>>(b);
     return cudaGetLastError();
 }
 
-}  // namespace
-
-size_t book_smem_bytes(int maxI, int maxJe, int maxN, int block)
+// The book kernel of (k, paths per lane): k in {4, 8}, ppl in {1, 2}.
+template <typename F>
+cudaError_t with_book_kernel(int k, int ppl, F&& f)
 {
-    return book_layout(maxI, maxJe, maxN, block).total;
-}
-
-int book_ring_slots_per_warp() { return kBRing * 32; }
-
-cudaError_t book_prepare(int k)
-{
-    switch (k) {
-    case 4: return cudaFuncSetAttribute(book_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    case 8: return cudaFuncSetAttribute(book_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    switch (k * 4 + ppl) {
+    case 17: return f(book_kernel<4, 1>);
+    case 18: return f(book_kernel<4, 2>);
+    case 33: return f(book_kernel<8, 1>);
+    case 34: return f(book_kernel<8, 2>);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t book_occupancy(int block, int k, size_t smem, int* bps)
+}  // namespace
+
+size_t book_smem_bytes(int maxI, int maxJe, int maxN, int block, int ppl)
 {
-    cudaError_t e = book_prepare(k);
-    if (e != cudaSuccess) return e;
-    return k == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, book_kernel<4>, block, smem)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, book_kernel<8>, block, smem);
+    return book_layout(maxI, maxJe, maxN, block, ppl).total;
 }
 
-cudaError_t launch_book(const BookParams& b, int grid, int block, int k, size_t smem, cudaStream_t s)
+int book_ring_slots_per_warp() { return kBRing * 32; }
+
+cudaError_t book_prepare(int k, int ppl)
 {
-    switch (k) {
-    case 4: return book_launch_k<4>(b, grid, block, smem, s);
-    case 8: return book_launch_k<8>(b, grid, block, smem, s);
+    return with_book_kernel(k, ppl, [](auto kernel) {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    });
+}
+
+cudaError_t book_occupancy(int block, int k, int ppl, size_t smem, int* bps)
+{
+    cudaError_t e = book_prepare(k, ppl);
+    if (e != cudaSuccess) return e;
+    return with_book_kernel(k, ppl, [&](auto kernel) {
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, kernel, block, smem);
+    });
+}
+
+cudaError_t launch_book(const BookParams& b, int grid, int block, int k, int ppl, size_t smem, cudaStream_t s)
+{
+    switch (k * 4 + ppl) {
+    case 17: return book_launch_k<4, 1>(b, grid, block, smem, s);
+    case 18: return book_launch_k<4, 2>(b, grid, block, smem, s);
+    case 33: return book_launch_k<8, 1>(b, grid, block, smem, s);
+    case 34: return book_launch_k<8, 2>(b, grid, block, smem, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -60,7 +60,7 @@ struct lv_book_s {
     float* d_l1 = nullptr;
     float* d_ckpt = nullptr;
     // launch shape
-    int block = 128, k = 4, item_tiles = 256, grid = 1;
+    int block = 128, k = 4, item_tiles = 256, grid = 1, ppl = 1;
     size_t smem = 0;
     // stream and graph
     cudaStream_t stream = nullptr;
@@ -138,14 +138,14 @@ std::vector<lv::BookItem> make_items(const std::vector<lv::BookInst>& insts, int
 }
 
 // (Re)builds items and scratch for a launch shape; drops the captured graph.
-lv_status configure(lv_book_s* b, int block, int k, int item_tiles)
+lv_status configure(lv_book_s* b, int block, int k, int item_tiles, int ppl)
 {
     drop_graph(b);
     LV_BCUDA(cudaStreamSynchronize(b->stream));
-    const size_t smem = lv::book_smem_bytes(b->max_I, b->max_Je, b->max_N, block);
+    const size_t smem = lv::book_smem_bytes(b->max_I, b->max_Je, b->max_N, block, ppl);
     if (smem > 200 * 1024) return set_error(LV_EINVAL, "book grids too large for shared memory");
     int bps = 0;
-    LV_BCUDA(lv::book_occupancy(block, k, smem, &bps));
+    LV_BCUDA(lv::book_occupancy(block, k, ppl, smem, &bps));
     if (bps < 1) return set_error(LV_EINVAL, "book launch shape does not fit on an SM");
     std::vector<lv::BookItem> items = make_items(b->insts, item_tiles);
     cudaFree(b->d_items);
@@ -163,7 +163,7 @@ lv_status configure(lv_book_s* b, int block, int k, int item_tiles)
     const size_t off_l1 = o;
     o = up256(o + sizeof(float) * (size_t)grid * b->max_IJe);
     const size_t off_ck = o;
-    o = up256(o + sizeof(float) * n_ck * warps * lv::book_ring_slots_per_warp());
+    o = up256(o + sizeof(float) * n_ck * warps * lv::book_ring_slots_per_warp() * ppl);
     if (o > b->scratch_bytes) {
         cudaFree(b->d_scratch);
         b->d_scratch = nullptr;
@@ -181,6 +181,7 @@ lv_status configure(lv_book_s* b, int block, int k, int item_tiles)
     b->block = block;
     b->k = k;
     b->item_tiles = item_tiles;
+    b->ppl = ppl;
     b->grid = grid;
     b->smem = smem;
     return LV_OK;
@@ -217,7 +218,7 @@ lv_status enqueue_run(lv_book_s* b, double* d_out)
     LV_BCUDA(cudaMemsetAsync(b->d_sums, 0, sizeof(double) * n_out, b->stream));
     LV_BCUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream));
     const lv::BookParams P = params(b);
-    LV_BCUDA(lv::launch_book(P, b->grid, b->block, b->k, b->smem, b->stream));
+    LV_BCUDA(lv::launch_book(P, b->grid, b->block, b->k, b->ppl, b->smem, b->stream));
     LV_BCUDA(lv::launch_book_finalize(P, (int)b->insts.size(), b->max_IJ, d_out, b->stream));
     return LV_OK;
 }
@@ -232,7 +233,7 @@ lv_status enqueue_risk(lv_book_s* b, double* d_out)
     LV_BCUDA(cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned int), b->stream));
     lv::BookParams P = params(b);
     P.risk = b->d_risk;
-    LV_BCUDA(lv::launch_book(P, b->grid, b->block, b->k, b->smem, b->stream));
+    LV_BCUDA(lv::launch_book(P, b->grid, b->block, b->k, b->ppl, b->smem, b->stream));
     LV_BCUDA(lv::launch_book_risk_finalize(P, (int)b->surfs.size(), (int)b->insts.size(), b->max_IJ, d_out,
                                            b->stream));
     return LV_OK;
@@ -260,20 +261,22 @@ std::string tune_key(const lv_book_s* b)
            "|insts" + std::to_string(b->insts.size());
 }
 
-bool read_tuned(const std::string& key, int* block, int* k, int* item_tiles)
+bool read_tuned(const std::string& key, int* block, int* k, int* item_tiles, int* ppl)
 {
-    int v[3];
+    int v[4];
     if (!lv::tune_cache_lookup(key, v)) return false;
     if (!(v[1] == 4 || v[1] == 8) || v[0] < 32 || v[0] > 128 || v[0] % 32 != 0 || v[2] < 1) return false;
+    if (v[3] != 1 && v[3] != 2) return false;
     *block = v[0];
     *k = v[1];
     *item_tiles = v[2];
+    *ppl = v[3];
     return true;
 }
 
-void write_tuned(const std::string& key, int block, int k, int item_tiles, double ms)
+void write_tuned(const std::string& key, int block, int k, int item_tiles, int ppl, double ms)
 {
-    const int v[3] = {block, k, item_tiles};
+    const int v[4] = {block, k, item_tiles, ppl};
     lv::tune_cache_append(key, v, ms);
 }
 
@@ -293,7 +296,7 @@ lv_status run_captured(lv_book_s* b, double S0, double r, uint64_t seed, bool ri
     double* d_res = risk ? b->d_rout : b->d_out;
     double* h_res = risk ? b->h_rout : b->h_out;
     if (!exec) {
-        LV_BCUDA(lv::book_prepare(b->k));
+        LV_BCUDA(lv::book_prepare(b->k, b->ppl));
         cudaGraph_t graph = nullptr;
         LV_BCUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         lv_status cst = LV_OK;
@@ -452,9 +455,9 @@ lv_status lv_book_create(const lv_surface_t* surfaces, int32_t n_surfaces, const
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(set_error(LV_ECUDA, "cannot create the book's stream"));
     b->own_stream = true;
-    int block = 128, k = 4, item_tiles = 256;
-    read_tuned(tune_key(b), &block, &k, &item_tiles);
-    lv_status st = configure(b, block, k, item_tiles);
+    int block = 128, k = 4, item_tiles = 256, ppl = 1;
+    read_tuned(tune_key(b), &block, &k, &item_tiles, &ppl);
+    lv_status st = configure(b, block, k, item_tiles, ppl);
     if (st != LV_OK) return bail(st);
     *out = b;
     return LV_OK;
@@ -551,6 +554,25 @@ lv_status lv_book_risk_offsets(lv_book_t b, int64_t* offsets)
     return LV_OK;
 }
 
+lv_status lv_book_set_launch(lv_book_t b, int32_t block, int32_t k, int32_t item_paths, int32_t ppl)
+{
+    if (!b) return set_error(LV_EINVAL, "NULL book");
+    if (block < 32 || block > 128 || block % 32 != 0)
+        return set_error(LV_EINVAL, "block must be a multiple of 32 in [32, 128]");
+    if (k != 4 && k != 8) return set_error(LV_EINVAL, "k must be 4 or 8");
+    if (item_paths < 32 || item_paths % 32 != 0) return set_error(LV_EINVAL, "item_paths must be a multiple of 32");
+    if (ppl != 1 && ppl != 2) return set_error(LV_EINVAL, "paths per lane must be 1 or 2");
+    BookDevice guard(b->device);
+    return configure(b, block, k, item_paths / 32, ppl);
+}
+
+lv_status lv_book_paths_per_lane(lv_book_t b, int32_t* ppl)
+{
+    if (!b || !ppl) return set_error(LV_EINVAL, "NULL argument");
+    *ppl = b->ppl;
+    return LV_OK;
+}
+
 lv_status lv_book_tune(lv_book_t b, double S0, double r, uint64_t seed, int32_t* out_block, int32_t* out_k,
                        int32_t* out_item_paths, double* out_ms)
 {
@@ -562,14 +584,15 @@ lv_status lv_book_tune(lv_book_t b, double S0, double r, uint64_t seed, int32_t*
     const int ks[] = {4, 8};
     const int items[] = {64, 256, 1024};
     double best = 1e300;
-    int bb = b->block, bk = b->k, bi = b->item_tiles;
+    int bb = b->block, bk = b->k, bi = b->item_tiles, bp = b->ppl;
     cudaEvent_t e0, e1;
     LV_BCUDA(cudaEventCreate(&e0));
     LV_BCUDA(cudaEventCreate(&e1));
     for (int blk : blocks)
         for (int k : ks)
-            for (int it : items) {
-                st = configure(b, blk, k, it);
+            for (int it : items)
+            for (int ppl = 1; ppl <= 2; ++ppl) {
+                st = configure(b, blk, k, it, ppl);
                 if (st != LV_OK) continue;
                 float ms = 0.0f, t = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
@@ -587,13 +610,14 @@ lv_status lv_book_tune(lv_book_t b, double S0, double r, uint64_t seed, int32_t*
                     bb = blk;
                     bk = k;
                     bi = it;
+                    bp = ppl;
                 }
             }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    st = configure(b, bb, bk, bi);
+    st = configure(b, bb, bk, bi, bp);
     if (st != LV_OK) return st;
-    if (best < 1e299) write_tuned(tune_key(b), bb, bk, bi, best);
+    if (best < 1e299) write_tuned(tune_key(b), bb, bk, bi, bp, best);
     if (out_block) *out_block = bb;
     if (out_k) *out_k = bk;
     if (out_item_paths) *out_item_paths = bi * 32;

@@ -234,11 +234,13 @@ struct BookParams {
     int max_I, max_Je, max_N, max_IJe;
 };
 
-size_t book_smem_bytes(int maxI, int maxJe, int maxN, int block);
+// ppl: paths per lane of the forward tiles (1 or 2); the FIFO and the
+// checkpoint ring (book_ring_slots_per_warp() * ppl per warp) grow with it.
+size_t book_smem_bytes(int maxI, int maxJe, int maxN, int block, int ppl);
 int book_ring_slots_per_warp();
-cudaError_t book_prepare(int k);
-cudaError_t book_occupancy(int block, int k, size_t smem, int* blocks_per_sm);
-cudaError_t launch_book(const BookParams& b, int grid, int block, int k, size_t smem, cudaStream_t s);
+cudaError_t book_prepare(int k, int ppl);
+cudaError_t book_occupancy(int block, int k, int ppl, size_t smem, int* blocks_per_sm);
+cudaError_t launch_book(const BookParams& b, int grid, int block, int k, int ppl, size_t smem, cudaStream_t s);
 cudaError_t launch_book_finalize(const BookParams& b, int n_inst, int max_IJ, double* out, cudaStream_t s);
 cudaError_t launch_book_risk_finalize(const BookParams& b, int n_surf, int n_inst, int max_IJ, double* out,
                                       cudaStream_t s);
@@ -253,10 +255,10 @@ namespace lv {
 // Records the thread-local message lv_last_error() returns; returns s.
 lv_status set_error(lv_status s, const std::string& msg);
 
-// Launch-shape cache shared by the autotuners: lines "key v0 v1 v2 ms" in
+// Launch-shape cache shared by the autotuners: lines "key v0 v1 v2 v3 ms" in
 // the file named by LV_TUNE_CACHE (the last line of a key wins).
-bool tune_cache_lookup(const std::string& key, int vals[3]);
-void tune_cache_append(const std::string& key, const int vals[3], double ms);
+bool tune_cache_lookup(const std::string& key, int vals[4]);
+void tune_cache_append(const std::string& key, const int vals[4], double ms);
 std::string gpu_name(int device);
 }  // namespace lv
 

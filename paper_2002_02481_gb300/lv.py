@@ -410,6 +410,8 @@ def _declare_book(lib):
         "lv_book_risk_offsets": [vp, c.POINTER(i64)],
         "lv_book_run_risk": [vp, d, d, u64, c.POINTER(d)],
         "lv_book_run_risk_device": [vp, d, d, u64, vp],
+        "lv_book_paths_per_lane": [vp, c.POINTER(i32)],
+        "lv_book_set_launch": [vp, i32, i32, i32, i32],
     }
     for name, args in sigs.items():
         f = getattr(lib, name)
@@ -467,6 +469,15 @@ class Book:
         _check(self.lib, self.lib.lv_book_tune(self.h, S0, r, int(seed), ctypes.byref(b), ctypes.byref(k),
                                                ctypes.byref(p), ctypes.byref(ms)), "lv_book_tune")
         return b.value, k.value, p.value, ms.value
+
+    def set_launch(self, block: int, k: int, item_paths: int, ppl: int) -> None:
+        _check(self.lib, self.lib.lv_book_set_launch(self.h, int(block), int(k), int(item_paths), int(ppl)),
+               "lv_book_set_launch")
+
+    def paths_per_lane(self) -> int:
+        p = ctypes.c_int32()
+        _check(self.lib, self.lib.lv_book_paths_per_lane(self.h, ctypes.byref(p)), "lv_book_paths_per_lane")
+        return p.value
 
     def set_weights(self, weights) -> None:
         """Position weight per option for the aggregated risk."""

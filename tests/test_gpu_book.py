@@ -86,6 +86,7 @@ def test_book_matches_single_option_calls(lib):
     # autotuner: keeps a shape that still reproduces the results
     blk, k, item_paths, ms = book.tune(S0, r, seed)
     assert blk in (64, 128) and k in (4, 8) and item_paths > 0 and ms > 0
+    assert book.paths_per_lane() in (1, 2)
     out3 = book.run(S0, r, seed)
     for o in range(len(items)):
         _close(out3[book.offsets[o]:book.offsets[o + 1]], out[book.offsets[o]:book.offsets[o + 1]], f"tuned {o}")
@@ -206,4 +207,27 @@ def test_benchmark_book_against_oracle(lib):
                               surfs_w[0].n_spot * surfs_w[0].n_time)
         p, d, _, v = book.result(out, o)
         G.compare_aggregates(p, d, v, ref, label=f"book option {o} (T={it.T}, P={it.n_paths}, phi={it.phi})")
+    book.close()
+
+
+def test_book_two_paths_per_lane_against_single_calls(lib):
+    """The book at two paths per lane equals the single-option sums calls
+    option by option, at small item sizes so that many items end with a
+    single tile (the second tile of a claim then lies beyond the item and
+    belongs to another block's item), at k = 4 and 8."""
+    surfs, items = _book_inputs()
+    handles = [lv.Surface.from_workload(s, lib) for s in surfs]
+    book = lv.Book(handles, items, lib)
+    for h in handles:
+        h.close()
+    S0, r, seed = 100.0, 0.02, 9
+    for blk, k, item_paths in ((128, 4, 96), (64, 8, 2048)):
+        book.set_launch(blk, k, item_paths, 2)
+        assert book.paths_per_lane() == 2
+        out = book.run(S0, r, seed)
+        for o, it in enumerate(items):
+            ref = _single(lib, surfs[it.surface], it, S0, r, seed)
+            _close(out[book.offsets[o]:book.offsets[o + 1]], ref, f"option {o} ({blk}, {k}, {item_paths})")
+    with pytest.raises(lv.LVError):
+        book.set_launch(128, 4, 96, 3)
     book.close()
