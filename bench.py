@@ -471,9 +471,10 @@ def run_ours(args):
     S.set_stream(stream.cuda_stream)
     # launch shape from the project's autotuner, on this workload (or fixed by --launch)
     if args.launch:
-        blk, kk = (int(v) for v in args.launch.split(","))
-        S.set_launch(blk, kk, 0)
-        tuned = (blk, kk, None)
+        vals = [int(v) for v in args.launch.split(",")]
+        S.set_launch(vals[0], vals[1], 0)
+        S.set_paths_per_lane(vals[2] if len(vals) > 2 else 1)
+        tuned = (vals[0], vals[1], None)
     else:
         tuned = S.tune(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, P, opt.seed)
     n_out = 3 + surf.n_spot * surf.n_time
@@ -758,7 +759,8 @@ def main():
     ap.add_argument("--no-bump", action="store_true", help="skip the bump-and-reprice timing")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-large", action="store_true", help="skip the 100x100 / 1260-step / 2^26-path record")
-    ap.add_argument("--launch", default="", help="fix the adjoint's launch shape as BLOCK,K instead of tuning it")
+    ap.add_argument("--launch", default="",
+                    help="fix the adjoint's launch shape as BLOCK,K[,PATHS_PER_LANE] instead of tuning it")
     ap.add_argument("--precision-study", action="store_true",
                     help="2^24-path precision workloads: binary64 vs Kahan level 2 against the FP64 oracle")
     ap.add_argument("--path-sweep", action="store_true",
