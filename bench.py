@@ -50,8 +50,11 @@ REV_OPS_PER_PATH_STEP = 19.0
 # Issue rate of an SM: 4 schedulers x 32 lanes per clock (the fallback peak
 # when the pipe probe cannot run).
 LANES_PER_SM_CLOCK = 128
-# ncu pipe of each probed rate: warp instructions issued to that pipe
-PIPE_OF_PROBE = {"fma": "ffma", "fmaheavy": "imad_wide", "alu": "lop3", "xu": "mufu_ex2"}
+# ncu pipe -> the probed instruction whose rate is that pipe's issue rate (one warp instruction
+# per pipe issue): fma.rn.f32 on either FMA half, mad.lo.u32 on the heavy half, lop3 on the ALU,
+# lg2 on the transcendental unit (ex2 issues at twice that rate; the 64-bit mad.wide takes two
+# issues of the heavy half)
+PIPE_OF_PROBE = {"fma": "ffma", "fmaheavy": "imad", "alu": "lop3", "xu": "mufu_lg2"}
 
 
 def dist_env():
@@ -143,7 +146,7 @@ def run_reference(args):
     oracle.load_library()
     surf, opt = W.config_paper_shape()
     threads = oracle.default_threads()
-    sample = 1 << 14
+    sample = opt.n_paths                  # the whole 2^20-path workload each step (~22 CPU-seconds)
     for _ in range(args.warmup):
         time_oracle(surf, opt, sample, threads)
     secs = [time_oracle(surf, opt, sample, threads) for _ in range(args.steps)]
@@ -156,7 +159,7 @@ def run_reference(args):
         "config": {"workload": WORKLOAD, "grid": "30x60", "n_steps": opt.n_steps,
                    "n_paths_timed_per_step": sample, "cpu": cpu_model()},
         "cpu_baseline": {"value": value, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
-                         "sample": f"first {sample} of the 2^20 paths per step, full 156 steps, "
+                         "sample": f"all {sample} paths of the workload per step, 156 steps, "
                                    "price+delta+1800 vegas"},
         "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -256,6 +259,16 @@ def other_workloads(lib, dev, ev0, ev1):
                                                       d.data_ptr()), ev0, ev1)
     res["with rho and dV/dT (lv_price_greeks_ext), 30x60, 156 steps, 2^20 paths"] = {
         "adjoint_kernel_ms": ms, "path_steps_per_s": o.n_paths * o.n_steps / (ms * 1e-3), "r": 0.01}
+    S.close()
+    # second-order buckets d^2 price / (d S0 d sigma_ij) (two forward passes)
+    S = lv.Surface.from_workload(W.config_paper_shape()[0], lib)
+    S.set_stream(stream.cuda_stream)
+    S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+    d = torch.zeros(3 + S.IJ, dtype=torch.float64, device=dev)
+    ms = time_call(lambda: S.price_greeks_vanna_device(o.S0, o.r, o.K, o.T, o.n_steps, o.n_paths, o.seed,
+                                                        d.data_ptr()), ev0, ev1)
+    res["second-order buckets (lv_price_greeks_vanna), 30x60, 156 steps, 2^20 paths"] = {
+        "kernel_ms": ms, "path_steps_per_s": o.n_paths * o.n_steps / (ms * 1e-3)}
     S.close()
     # the tangent-ratio form of the adjoint (two forward passes, no checkpoints)
     single("tangent-ratio adjoint, 30x60, 156 steps, 2^20 paths", *W.config_paper_shape(),
@@ -606,14 +619,13 @@ def run_ours(args):
         S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
         import oracle
         threads = oracle.default_threads()
+        cpu_s = time_oracle(surf, opt, P, threads)
+        cpu = {"value": P * opt.n_steps / cpu_s, "unit": "path-steps/s", "cores": threads,
+               "kind": "oracle", "sample": f"all {P} paths of the workload, 156 steps, price+delta+1800 vegas, "
+                                           f"{cpu_s:.1f} s on {threads} threads ({cpu_model()})"}
         sample = 1 << 13
         o_s = W.Option(**{**opt.__dict__, "n_paths": sample})
-        t0 = time.perf_counter()
         ref = oracle.price_greeks(surf, o_s, n_threads=threads)
-        cpu_s = time.perf_counter() - t0
-        cpu = {"value": sample * opt.n_steps / cpu_s, "unit": "path-steps/s", "cores": threads,
-               "kind": "oracle", "sample": f"first {sample} of the 2^20 paths, 156 steps, "
-                                           f"price+delta+1800 vegas ({cpu_model()})"}
         # accuracy of the adjoint and of the bump baseline against the FP64 oracle's
         # pathwise estimator on the same paths (same counters)
         vmax = float(np.max(np.abs(ref["vega"])))
