@@ -762,6 +762,57 @@ def path_sweep():
     return 0
 
 
+def only(which: str, launch: str, reps: int):
+    """One workload alone at a fixed shape (for profiling and quick timing):
+    'book' (8 x 64 options, per-option outputs, graph replay), 'vanna' (the
+    second-order buckets on the bench workload), 'large' (100 x 100, 1,260
+    steps, 2^26 paths) or 'fp64' (the binary64 reference run, 2^20 paths).
+    Prints one JSON line with the kernel (or replay) times."""
+    import torch
+
+    from paper_2002_02481_gb300 import lv
+
+    lib = lv.load()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    vals = [int(v) for v in launch.split(",")] if launch else []
+    out = {"only": which, "launch": vals, "ms": []}
+    if which == "book":
+        handles = [lv.Surface.from_workload(sf, lib) for sf in W.book_surfaces()]
+        book = lv.Book(handles, W.book_items(), lib)
+        for h in handles:
+            h.close()
+        if vals:
+            book.set_launch(*vals)
+        for rep in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            book.run(100.0, 0.0, 1 + rep)
+            out["ms"].append((time.perf_counter() - t0) * 1e3)
+        book.close()
+    else:
+        surf, opt = W.config_large() if which == "large" else W.config_paper_shape()
+        S = lv.Surface.from_workload(surf, lib)
+        S.set_stream(stream.cuda_stream)
+        if vals:
+            S.set_launch(vals[0], vals[1], 0)
+            S.set_paths_per_lane(vals[2] if len(vals) > 2 else 1)
+        S.set_kernel_events(ev0.cuda_event, ev1.cuda_event)
+        d = torch.zeros(3 + S.IJ, dtype=torch.float64, device="cuda")
+        call = {"vanna": S.price_greeks_vanna_device, "large": S.price_greeks_device,
+                "fp64": S.price_greeks_fp64_device}[which]
+        for _ in range(reps):
+            call(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, d.data_ptr())
+            ev1.synchronize()
+            out["ms"].append(ev0.elapsed_time(ev1))
+        S.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -771,6 +822,8 @@ def main():
     ap.add_argument("--no-bump", action="store_true", help="skip the bump-and-reprice timing")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-large", action="store_true", help="skip the 100x100 / 1260-step / 2^26-path record")
+    ap.add_argument("--only", default="", choices=["", "book", "vanna", "large", "fp64"],
+                    help="time one workload alone at a fixed shape (for profiling)")
     ap.add_argument("--launch", default="",
                     help="fix the adjoint's launch shape as BLOCK,K[,PATHS_PER_LANE] instead of tuning it")
     ap.add_argument("--precision-study", action="store_true",
@@ -784,6 +837,8 @@ def main():
         return precision_study()
     if args.path_sweep:
         return path_sweep()
+    if args.only:
+        return only(args.only, args.launch, max(1, args.steps))
     return run_ours(args)
 
 
