@@ -239,7 +239,7 @@ def other_workloads(lib, dev, ev0, ev1):
                                                       opt.seed, d.data_ptr()), ev0, ev1)
         res[name] = {"adjoint_kernel_ms": ms, "path_steps_per_s": opt.n_paths * opt.n_steps / (ms * 1e-3),
                      "launch": list(S.get_launch(opt.n_steps, True)),
-                     "paths_per_lane": S.get_paths_per_lane(opt.n_steps)}
+                     "paths_per_lane": S.get_paths_per_lane(opt.n_steps, opt.n_paths)}
         S.close()
 
     single("small 20x10, 52 steps, 2^14 paths", *W.config_small())
@@ -434,8 +434,9 @@ def large_record(lib, dev, peaks, n_sm, mhz, reps=3):
         ms = statistics.median(step_ms)
         res[f"k={k}"] = {"ms_per_step": ms, "value": ps / (ms * 1e-3), "kernel_ms": statistics.median(kern_ms)}
     S.set_launch(128, 4, 0)
-    res["launch"] = {"block": 128, "k": 4, "source": "tuned (k=4 fastest of 4, 8, 16); k=32 is the configured "
-                                                     "interval, reported beside it"}
+    res["launch"] = {"block": 128, "k": 4, "paths_per_lane": S.get_paths_per_lane(opt.n_steps, opt.n_paths),
+                     "source": "tuned (k=4 fastest of 4, 8, 16; two paths per lane, packed pairs); k=32 is the "
+                               "configured interval, reported beside it"}
     res["value"] = res["k=4"]["value"]
     res["ms_per_step"] = res["k=4"]["ms_per_step"]
     live = live_fraction(S, opt, 1 << 14)
@@ -607,7 +608,7 @@ def run_ours(args):
         live = live_fraction(S, opt)
         roofline = roofline_block(kern, P * opt.n_steps, live, pipe_peaks, mhz, n_sm, profiled_record())
         blk, kk, bps = S.get_launch(opt.n_steps, True)
-        ppl = S.get_paths_per_lane(opt.n_steps)
+        ppl = S.get_paths_per_lane(opt.n_steps, opt.n_paths)
         roofline["kernel"] = (f"adjoint_kernel<k={kk},binary64 level 2,{ppl} path(s) per lane> "
                               f"(block {blk}, {bps} blocks/SM)")
         roofline["clock_mhz"] = mhz

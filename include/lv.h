@@ -163,14 +163,17 @@ lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks
 
 /* Paths per lane of the adjoint's forward tiles: 1, or 2 (each lane runs two
  * paths interleaved: two independent dependency chains per thread, the
- * per-step grid data loaded once for both); 0 keeps the tuned or default
- * value (1). Two paths per lane exist for the main reading's reverse sweep
- * with checkpoints every 4 or 8 steps; elsewhere the call runs one. The
- * results do not depend on it beyond reduction-order rounding.
- * lv_get_paths_per_lane reads back the value the next call with n_steps
- * steps will use. */
+ * per-step grid data loaded once for both, and on the main reading their
+ * binary32 arithmetic in packed pairs where that keeps the occupancy); 0 keeps
+ * the tuned value, or the default: 2 for calls of at least 6,144 paths per SM
+ * (933,888 on 152 SMs), where every warp still gets four pairs of tiles, else 1.
+ * Two paths per lane exist for the main reading's reverse sweep with
+ * checkpoints every 4 or 8 steps; elsewhere the call runs one. The results do
+ * not depend on it beyond reduction-order rounding.
+ * lv_get_paths_per_lane reads back the value the next call with n_steps steps
+ * and n_paths >= 1 paths will use. */
 lv_status lv_set_paths_per_lane(lv_surface_t h, int32_t ppl);
-lv_status lv_get_paths_per_lane(lv_surface_t h, int32_t n_steps, int32_t* ppl);
+lv_status lv_get_paths_per_lane(lv_surface_t h, int32_t n_steps, int64_t n_paths, int32_t* ppl);
 
 /* Record two caller-owned CUDA events (cudaEvent_t, created with timing
  * enabled) on the handle's stream immediately before and after the Monte
@@ -189,7 +192,9 @@ lv_status lv_set_kernel_events(lv_surface_t h, void* start_event, void* end_even
 lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32_t n_steps, int64_t n_paths,
                   uint64_t seed, int32_t* out_block, int32_t* out_k, double* out_ms);
 
-/* Read back the launch shape the next call will use for (n_steps, greeks). */
+/* Read back the launch shape the next call will use for (n_steps, greeks);
+ * blocks_per_sm is that of a call large enough for two paths per lane by
+ * default (lv_get_paths_per_lane). */
 lv_status lv_get_launch(lv_surface_t h, int32_t n_steps, int32_t greeks,
                         int32_t* block, int32_t* k, int32_t* blocks_per_sm);
 

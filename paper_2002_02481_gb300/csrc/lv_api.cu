@@ -220,13 +220,21 @@ void occ_store(const OccKey& key, int occ)
     g_occ[key] = occ;
 }
 
+// A call of at least this many paths per SM runs two paths per lane unless
+// told otherwise: every warp of the adjoint kernel (at most 24 resident per
+// SM) then gets at least four pairs of 32-path tiles. Smaller calls run one
+// path per lane; measured on a GB300 (k = 4), two paths per lane took 1.03-1.07x
+// the time at 2^18 and 2^19 paths and 0.96-0.99x from 2^20 on.
+constexpr int64_t kPairMinPathsPerSm = 4 * 64 * 24;
+
+// n_paths < 0: a call large enough for two paths per lane.
 lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* block, int* k, int* bps,
                         bool dbg = false, bool* grid_smem = nullptr, bool extra = false, bool vanna = false,
-                        int* ppl_out = nullptr)
+                        int* ppl_out = nullptr, int64_t n_paths = -1)
 {
     *block = h->cfg_block ? h->cfg_block : 128;
     *k = greeks ? (h->cfg_k ? h->cfg_k : 4) : 4;
-    int ppl = h->cfg_ppl ? h->cfg_ppl : 1;
+    int ppl = h->cfg_ppl ? h->cfg_ppl : (n_paths < 0 || n_paths >= kPairMinPathsPerSm * h->num_sms ? 2 : 1);
     const char* cache = std::getenv("LV_TUNE_CACHE");
     if (greeks && !dbg && !h->cfg_block && !h->cfg_k && !h->cfg_ppl && cache && *cache) {
         int v[4];
@@ -266,7 +274,7 @@ lv_status make_plan(lv_surface_s* h, int32_t n_steps, int64_t n_paths, bool gree
                     bool extra = false, bool vanna = false)
 {
     lv_status st = choose_launch(h, n_steps, greeks, &p->block, &p->k, &p->bps, dbg, &p->grid_smem, extra, vanna,
-                                 &p->ppl);
+                                 &p->ppl, n_paths);
     if (st != LV_OK) return st;
     p->smem = lv::mc_smem_bytes(h->I, h->Je, n_steps, p->block, greeks, p->grid_smem, extra, p->ppl);
     const int warps = p->block / 32;
@@ -677,14 +685,15 @@ lv_status lv_set_paths_per_lane(lv_surface_t h, int32_t ppl)
     return LV_OK;
 }
 
-lv_status lv_get_paths_per_lane(lv_surface_t h, int32_t n_steps, int32_t* ppl)
+lv_status lv_get_paths_per_lane(lv_surface_t h, int32_t n_steps, int64_t n_paths, int32_t* ppl)
 {
     if (!h || !ppl) return fail(LV_EINVAL, "NULL argument");
     if (n_steps < 1 || n_steps > LV_MAX_STEPS) return fail(LV_EINVAL, "n_steps out of range");
+    if (n_paths < 1) return fail(LV_EINVAL, "n_paths must be >= 1");
     DeviceGuard g(h->device);
     int b = 0, kk = 0, bps = 0, p = 1;
     bool gs = true;
-    lv_status st = choose_launch(h, n_steps, true, &b, &kk, &bps, false, &gs, false, false, &p);
+    lv_status st = choose_launch(h, n_steps, true, &b, &kk, &bps, false, &gs, false, false, &p, n_paths);
     if (st != LV_OK) return st;
     *ppl = p;
     return LV_OK;
@@ -1323,7 +1332,7 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
 
     int block = 0, k = 0, bps = 0, ppl = 1;
     bool grid_smem = true;
-    st = choose_launch(h, n_steps, true, &block, &k, &bps, false, &grid_smem, false, false, &ppl);
+    st = choose_launch(h, n_steps, true, &block, &k, &bps, false, &grid_smem, false, false, &ppl, n_paths);
     if (st != LV_OK) return st;
     const int warps = block / 32;
     const int64_t tiles = (n_paths + lv::paths_per_tile(true) - 1) / lv::paths_per_tile(true);

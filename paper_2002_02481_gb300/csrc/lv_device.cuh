@@ -86,6 +86,103 @@ __device__ __forceinline__ void normals4(uint32_t blk, uint32_t c1, uint32_t c2,
     }
 }
 
+// Packed binary32 pairs (add/sub/mul/fma .f32x2, sm_100 and later): one
+// instruction rounds each element exactly as the scalar instruction would, so
+// two independent paths advanced through them get bit-identical results with
+// half the issue slots for that arithmetic. The operands are register pairs;
+// constants cannot come from the parameter bank as in scalar code, so each
+// constant pair costs two registers.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+__device__ __forceinline__ float lo2(f32x2 r)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    return a;
+}
+
+__device__ __forceinline__ float hi2(f32x2 r)
+{
+    float a, b;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    return b;
+}
+
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// The normals of normals4 for two paths at once, as pairs (path a, path b),
+// NEGATED: nz[q] = (-Z_q of a, -Z_q of b), i.e. rho cos / rho sin of the
+// shifted angle without normals4's sign flip. Every element is rounded as in
+// normals4 (a negation is exact), so -nz[q] is normals4's z[q] bit for bit.
+__device__ __forceinline__ void normals4x2_neg(uint32_t blk, uint32_t c1a, uint32_t c2a, uint32_t c1b, uint32_t c2b,
+                                               uint32_t k0, uint32_t k1, f32x2 nz[4])
+{
+    uint32_t a0 = blk, a1 = c1a, a2 = c2a, a3 = 0u;
+    uint32_t b0 = blk, b1 = c1b, b2 = c2b, b3 = 0u;
+    philox4x32_10(a0, a1, a2, a3, k0, k1);
+    philox4x32_10(b0, b1, b2, b3, k0, k1);
+    const f32x2 one_m = pk2(__uint_as_float(0x3f7fffffu), __uint_as_float(0x3f7fffffu));
+    const f32x2 half = pk2(0.5f, 0.5f);
+    const f32x2 m2ln2 = pk2(-1.3862943611198906f, -1.3862943611198906f);
+    const f32x2 two_pi = pk2(6.2831853071795865f, 6.2831853071795865f);
+#define LV_U2(x, y) sub2(pk2(__uint_as_float(((x) >> 9) | 0x3f800000u), __uint_as_float(((y) >> 9) | 0x3f800000u)), one_m)
+    const f32x2 u0 = LV_U2(a0, b0), u1 = LV_U2(a1, b1), u2 = LV_U2(a2, b2), u3 = LV_U2(a3, b3);
+#undef LV_U2
+    {
+        const f32x2 l = mul2(m2ln2, pk2(lg2_approx(lo2(u0)), lg2_approx(hi2(u0))));
+        const f32x2 rho = pk2(sqrt_approx(lo2(l)), sqrt_approx(hi2(l)));
+        const f32x2 ang = mul2(two_pi, sub2(u1, half));
+        float sa, ca, sb, cb;
+        __sincosf(lo2(ang), &sa, &ca);
+        __sincosf(hi2(ang), &sb, &cb);
+        nz[0] = mul2(rho, pk2(ca, cb));
+        nz[1] = mul2(rho, pk2(sa, sb));
+    }
+    {
+        const f32x2 l = mul2(m2ln2, pk2(lg2_approx(lo2(u2)), lg2_approx(hi2(u2))));
+        const f32x2 rho = pk2(sqrt_approx(lo2(l)), sqrt_approx(hi2(l)));
+        const f32x2 ang = mul2(two_pi, sub2(u3, half));
+        float sa, ca, sb, cb;
+        __sincosf(lo2(ang), &sa, &ca);
+        __sincosf(hi2(ang), &sb, &cb);
+        nz[2] = mul2(rho, pk2(ca, cb));
+        nz[3] = mul2(rho, pk2(sa, sb));
+    }
+}
+
 // Time data of step n: t_n = n dt, j_n = the largest j <= J-2 with
 // tau_j <= t_n, v_n = (t_n - tau_j) / (tau_{j+1} - tau_j) clamped to
 // [0, 1], decided in binary64. Returned as (j (I-1), (j+1) (I-1), j I, bits
@@ -335,16 +432,68 @@ __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid&
 // independent dependency chains; each path's arithmetic is exactly that of
 // forward_path (its checkpoints and terminal state are bit-identical), and
 // the per-step time data is loaded once for both. Path b is logged only
-// when log_b (it may lie past the end of the call's range).
-template <int KCK, bool STORE, bool DBG, int MODEL = 0>
+// when log_b (it may lie past the end of the call's range). With PACK (main
+// reading, no logging) the two paths' binary32 arithmetic runs in packed
+// pairs: the Box-Muller products and shifts, the spot-cell index, the time
+// blend of sigma and the whole log-Euler step; the loads and the
+// transcendental unit stay per path. The Euler step uses
+// sqdt2 Z = (-sqdt2)(-Z), exact, so the negated normals need no sign flip.
+template <int KCK, bool STORE, bool DBG, int MODEL = 0, bool PACK = false>
 __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid& g, uint32_t c1a, uint32_t c2a,
                                               uint32_t c1b, uint32_t c2b, float* cka, float* ckb, size_t cks,
                                               long long rel_a, long long rel_b, bool log_b, float& ya_out,
                                               float& yb_out)
 {
+    const int nseg = (P.N + KCK - 1) / KCK;
+    if constexpr (PACK && MODEL == 0 && !DBG) {
+        const f32x2 csc = pk2(P.cell_scale, P.cell_scale), csh = pk2(P.cell_shift, P.cell_shift);
+        const f32x2 nsq = pk2(-P.sqdt2, -P.sqdt2), nhdt = pk2(-P.hdt, -P.hdt), rdt = pk2(P.rdt, P.rdt);
+        f32x2 y = pk2(P.x0, P.x0);
+        f32x2 nz[4];
+        for (int m = 0; m < nseg; ++m) {
+            if (STORE) {
+                cka[(size_t)m * cks] = lo2(y);
+                ckb[(size_t)m * cks] = hi2(y);
+            }
+#pragma unroll
+            for (int q = 0; q < KCK; ++q) {
+                const int n = m * KCK + q;
+                if (n < P.N) {
+                    if ((q & 3) == 0) normals4x2_neg((uint32_t)(n >> 2), c1a, c2a, c1b, c2b, P.k0, P.k1, nz);
+                    const int4 tb = g.tab[n];
+                    const float v = __int_as_float(tb.w);
+                    // eval_sigma<false, 0> for both paths
+                    const float Sa = ex2_approx(lo2(y)), Sb = ex2_approx(hi2(y));
+                    int ia, ib;
+                    if (P.log_uniform) {
+                        const f32x2 ci = fma2(y, csc, csh);
+                        ia = min(max(__float2int_rd(lo2(ci)), 0), P.I - 2);
+                        ib = min(max(__float2int_rd(hi2(ci)), 0), P.I - 2);
+                    } else {
+                        ia = spot_cell(P, g, lo2(y), Sa);
+                        ib = spot_cell(P, g, hi2(y), Sb);
+                    }
+                    const float2 aba = g.ab[ia], abb = g.ab[ib];
+                    const float ua = __saturatef(fmaf(Sa, aba.x, aba.y));
+                    const float ub = __saturatef(fmaf(Sb, abb.x, abb.y));
+                    const float2 loa = g.sig2[tb.x + ia], hia = g.sig2[tb.y + ia];
+                    const float2 lob = g.sig2[tb.x + ib], hib = g.sig2[tb.y + ib];
+                    const f32x2 top = pk2(fmaf(ua, loa.y, loa.x), fmaf(ub, lob.y, lob.x));
+                    const f32x2 bot = pk2(fmaf(ua, hia.y, hia.x), fmaf(ub, hib.y, hib.x));
+                    const f32x2 sig = fma2(pk2(v, v), sub2(bot, top), top);
+                    // euler_step for both paths
+                    const f32x2 t1 = mul2(nsq, nz[q & 3]);
+                    const f32x2 t3 = fma2(mul2(nhdt, sig), sig, rdt);
+                    y = add2(y, fma2(sig, t1, t3));
+                }
+            }
+        }
+        ya_out = lo2(y);
+        yb_out = hi2(y);
+        return;
+    }
     float ya = P.x0, yb = P.x0;
     float za[4], zb[4];
-    const int nseg = (P.N + KCK - 1) / KCK;
     for (int m = 0; m < nseg; ++m) {
         if (STORE) {
             cka[(size_t)m * cks] = ya;

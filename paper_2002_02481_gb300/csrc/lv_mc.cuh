@@ -51,6 +51,16 @@ namespace {
 constexpr int kTile = 32;      // paths per warp tile of the adjoint kernel (one per lane)
 constexpr int kPriceTile = 64; // paths per warp tile of the price kernel (two per lane)
 constexpr int kRing = 4;       // checkpoint slot groups of kTile per warp
+
+// Whether the adjoint kernel's two-paths-per-lane forward tiles use the
+// packed binary32 pairs of forward_path2. The pairs cost 4-6 registers; at
+// k = 4 with binary64 level 2 and the grid in shared memory the scalar form
+// compiles to 80 registers (6 blocks of 128 threads per SM) and the packed one
+// to 84 (5 blocks), which lost 2 % on a GB300. Every other instantiation runs
+// the same number of blocks either way, or (the grid through L1) gains more
+// from packing than the block costs.
+template <int KCK, int ACC, bool GS>
+constexpr bool kPackForward = !(KCK == 4 && ACC == 0 && GS);
 constexpr int kQueue = 64;     // per-warp FIFO capacity per path a lane runs in a forward tile
                                // (entries; < 32 + kTile * ppl never overflows kQueue * ppl)
 constexpr int kMaxWarps = 8;   // blockDim.x <= 256 (the adjoint kernel runs at most 128)
@@ -283,8 +293,8 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 path_counter(P, rel_a, c1a, c2a);
                 path_counter(P, rel_b, c1b, c2b);
                 float ya, yb;
-                forward_path2<KCK, true, false, MODEL>(P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b, cks,
-                                                       rel_a, rel_b, false, ya, yb);
+                forward_path2<KCK, true, false, MODEL, kPackForward<KCK, ACC, GS>>(
+                    P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b, cks, rel_a, rel_b, false, ya, yb);
                 float V;
                 payoff<MODEL>(P, ya, V, xa);
                 acc_add<ACC>(acc[0], V);
@@ -573,8 +583,8 @@ __global__ void __launch_bounds__(256, 4) price_kernel(const __grid_constant__ M
             path_counter(P, rel_a, c1a, c2a);
             path_counter(P, rel_b, c1b, c2b);
             float ya, yb;
-            forward_path2<4, false, false, MODEL>(P, g, c1a, c2a, c1b, c2b, nullptr, nullptr, 0, rel_a, rel_b, false,
-                                                  ya, yb);
+            forward_path2<4, false, false, MODEL, true>(P, g, c1a, c2a, c1b, c2b, nullptr, nullptr, 0, rel_a, rel_b,
+                                                        false, ya, yb);
             float V, xb;
             payoff<MODEL>(P, ya, V, xb);
             acc_add<ACC>(acc[0], V);

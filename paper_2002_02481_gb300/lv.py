@@ -76,7 +76,7 @@ def _declare(lib: ctypes.CDLL) -> ctypes.CDLL:
         "lv_set_launch": [vp, i32, i32, i32],
         "lv_set_kernel_events": [vp, vp, vp],
         "lv_set_paths_per_lane": [vp, i32],
-        "lv_get_paths_per_lane": [vp, i32, c.POINTER(i32)],
+        "lv_get_paths_per_lane": [vp, i32, i64, c.POINTER(i32)],
         "lv_tune": [vp, d, d, d, d, i32, i64, u64, c.POINTER(i32), c.POINTER(i32), c.POINTER(d)],
         "lv_get_launch": [vp, i32, i32, c.POINTER(i32), c.POINTER(i32), c.POINTER(i32)],
         "lv_price": [vp, d, d, d, d, i32, i64, u64, dp, dp],
@@ -229,9 +229,9 @@ class Surface:
         """1 or 2 paths per lane in the adjoint's forward tiles (0: tuned / default)."""
         _check(self.lib, self.lib.lv_set_paths_per_lane(self.h, int(ppl)), "lv_set_paths_per_lane")
 
-    def get_paths_per_lane(self, n_steps: int) -> int:
+    def get_paths_per_lane(self, n_steps: int, n_paths: int) -> int:
         p = ctypes.c_int32()
-        _check(self.lib, self.lib.lv_get_paths_per_lane(self.h, int(n_steps), ctypes.byref(p)),
+        _check(self.lib, self.lib.lv_get_paths_per_lane(self.h, int(n_steps), int(n_paths), ctypes.byref(p)),
                "lv_get_paths_per_lane")
         return p.value
 

@@ -103,17 +103,25 @@ def test_large_grid_timed_shape(lib):
             G.full_parity(surf, opt, lib, launch=(128, 4, 0), label="large k=4"))
 
 
-@pytest.mark.parametrize("ppl_case", ["small", "paper 2^18", "edge: 33 paths", "edge: put, uneven grid"])
+@pytest.mark.parametrize("ppl_case", ["small", "paper 2^18", "edge: 33 paths", "edge: put, uneven grid",
+                                      "large 100x100, grid through L1"])
 def test_two_paths_per_lane(ppl_case, lib):
     """Two paths per lane in the forward tiles (a warp claims two tiles and
     runs them interleaved): the same per-path arithmetic, checked against the
-    oracle path for path, at k = 4 and 8 and in both level-2 modes."""
+    oracle path for path, at k = 4 and 8 and in both level-2 modes. Every
+    instantiation but (k = 4, binary64, grid in shared memory) runs the two
+    paths' binary32 arithmetic in packed pairs; the cases cover both forms, the
+    binary search for the cell (uneven grid) and the grid read through L1."""
     if ppl_case == "small":
         surf, opt = W.config_small()
         cases = [((128, 4, 0), 0), ((128, 8, 0), 1)]
     elif ppl_case == "paper 2^18":
         surf, opt = W.config_paper_shape()
         opt.n_paths = 1 << 18
+        cases = [((128, 4, 0), 0), ((128, 4, 0), 1), ((128, 8, 0), 0)]
+    elif ppl_case == "large 100x100, grid through L1":
+        surf, opt = W.config_large()
+        opt.n_paths = 1 << 14
         cases = [((128, 4, 0), 0)]
     elif ppl_case == "edge: 33 paths":
         _, surf, opt = EDGE[5]
@@ -123,7 +131,7 @@ def test_two_paths_per_lane(ppl_case, lib):
         cases = [((128, 8, 0), 1)]
     for launch, acc in cases:
         s = G.make_surface(surf, opt, lib, launch=launch, accumulation=acc, ppl=2)
-        assert s.get_paths_per_lane(opt.n_steps) == 2
+        assert s.get_paths_per_lane(opt.n_steps, opt.n_paths) == 2
         s.close()
         _report(f"two paths per lane: {ppl_case} {launch} acc={acc}",
                 G.full_parity(surf, opt, lib, launch=launch, accumulation=acc, ppl=2, label=ppl_case))
@@ -131,25 +139,61 @@ def test_two_paths_per_lane(ppl_case, lib):
 
 def test_two_paths_per_lane_equals_one(lib):
     """Same paths, same per-path arithmetic: one or two paths per lane agree to
-    reduction-order rounding; where two paths per lane do not exist the call
-    runs one."""
+    reduction-order rounding, with the two paths in scalar registers (k = 4,
+    binary64 level 2) and in packed pairs (k = 8, and Kahan level 2); where two
+    paths per lane do not exist the call runs one."""
     surf, opt = W.config_paper_shape()
     opt.n_paths = 1 << 17
-    a = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=1)
-    b = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=2)
-    pa, da, va = a.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
-    pb, db, vb = b.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
-    assert abs(pb - pa) <= 1e-12 * abs(pa) and abs(db - da) <= 1e-9 * abs(da)
-    assert np.max(np.abs(vb - va)) <= 1e-6 * np.max(np.abs(va))
+    for launch, acc in [((128, 4, 0), 0), ((128, 8, 0), 0), ((128, 4, 0), 1)]:
+        a = G.make_surface(surf, opt, lib, launch=launch, accumulation=acc, ppl=1)
+        b = G.make_surface(surf, opt, lib, launch=launch, accumulation=acc, ppl=2)
+        assert a.get_paths_per_lane(opt.n_steps, opt.n_paths) == 1
+        assert b.get_paths_per_lane(opt.n_steps, opt.n_paths) == 2
+        pa, da, va = a.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+        pb, db, vb = b.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+        # Kahan level 2 keeps each thread's scalar sums as compensated binary32
+        # pairs (within about 2^-23 of that thread's sum), and which paths share
+        # a thread depends on the paths per lane: the binary64 totals of the two
+        # runs then differ by about 1e-10 relative (the binary64 mode: 1e-14)
+        tp, td = (1e-12, 1e-9) if acc == 0 else (1e-8, 1e-8)
+        assert abs(pb - pa) <= tp * abs(pa) and abs(db - da) <= td * abs(da), (launch, acc)
+        assert np.max(np.abs(vb - va)) <= 1e-6 * np.max(np.abs(va)), (launch, acc)
+        a.close()
+        b.close()
+    # the default: two where they exist, for calls that give every warp two pairs of tiles
+    b = G.make_surface(surf, opt, lib, launch=(128, 4, 0))
+    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 2
+    assert b.get_paths_per_lane(opt.n_steps, 1 << 12) == 1
     b.set_launch(128, 16, 0)
-    assert b.get_paths_per_lane(opt.n_steps) == 1
+    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 1
     b.set_launch(128, 4, 0)
     b.set_scheme(lv.LV_SCHEME_S)
-    assert b.get_paths_per_lane(opt.n_steps) == 1
+    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 1
+    with pytest.raises(lv.LVError):
+        b.get_paths_per_lane(opt.n_steps, 0)
     with pytest.raises(lv.LVError):
         b.set_paths_per_lane(3)
-    a.close()
     b.close()
+
+
+@pytest.mark.parametrize("case", ["paper 2^18", "uneven 7x5 grid (binary search), put", "large 100x100"])
+def test_price_only_matches_adjoint_price(case, lib):
+    """The forward-only kernel (two paths per lane in packed binary32 pairs)
+    and the adjoint kernel at one path per lane (scalar arithmetic) compute the
+    same paths bit for bit: their prices agree to binary64 reduction order."""
+    if case == "paper 2^18":
+        surf, opt = W.config_paper_shape()
+        opt.n_paths = 1 << 18
+    elif case == "large 100x100":
+        surf, opt = W.config_large()
+        opt.n_paths = 1 << 16
+    else:
+        _, surf, opt = next(e for e in EDGE if e[0] == case)
+    gs = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=1)
+    p, d, v = gs.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    pp, se = gs.price(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert abs(pp - p) <= 1e-11 * max(abs(p), 1e-300) and se >= 0
+    gs.close()
 
 
 @pytest.mark.parametrize("launch", [(128, 4, 0), (96, 8, 0), (128, 16, 0), (128, 32, 1), (64, 8, 2), (32, 4, 0)])

@@ -24,7 +24,7 @@ def test_tune_and_cache(tmp_path, monkeypatch):
     args = (opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
     p0, d0, v0 = a.price_greeks(*args)
     blk, k, ms = a.tune(*args)
-    ppl = a.get_paths_per_lane(opt.n_steps)
+    ppl = a.get_paths_per_lane(opt.n_steps, opt.n_paths)
     assert blk in (64, 128) and k in (4, 8, 16) and ms > 0
     assert ppl in (1, 2) and (ppl == 1 or k in (4, 8))
     assert a.get_launch(opt.n_steps, True)[:2] == (blk, k)
@@ -34,6 +34,6 @@ def test_tune_and_cache(tmp_path, monkeypatch):
     assert cache.exists() and str(blk) in cache.read_text()
     b = lv.Surface.from_workload(surf, lib)          # fresh handle: shape from the cache
     assert b.get_launch(opt.n_steps, True)[:2] == (blk, k)
-    assert b.get_paths_per_lane(opt.n_steps) == ppl
+    assert b.get_paths_per_lane(opt.n_steps, opt.n_paths) == ppl
     a.close()
     b.close()
