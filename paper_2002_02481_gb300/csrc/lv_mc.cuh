@@ -52,15 +52,6 @@ constexpr int kTile = 32;      // paths per warp tile of the adjoint kernel (one
 constexpr int kPriceTile = 64; // paths per warp tile of the price kernel (two per lane)
 constexpr int kRing = 4;       // checkpoint slot groups of kTile per warp
 
-// Whether the adjoint kernel's two-paths-per-lane forward tiles use the
-// packed binary32 pairs of forward_path2. The pairs cost 4-6 registers; at
-// k = 4 with binary64 level 2 and the grid in shared memory the scalar form
-// compiles to 80 registers (6 blocks of 128 threads per SM) and the packed one
-// to 84 (5 blocks), which lost 2 % on a GB300. Every other instantiation runs
-// the same number of blocks either way, or (the grid through L1) gains more
-// from packing than the block costs.
-template <int KCK, int ACC, bool GS>
-constexpr bool kPackForward = !(KCK == 4 && ACC == 0 && GS);
 constexpr int kQueue = 64;     // per-warp FIFO capacity per path a lane runs in a forward tile
                                // (entries; < 32 + kTile * ppl never overflows kQueue * ppl)
 constexpr int kMaxWarps = 8;   // blockDim.x <= 256 (the adjoint kernel runs at most 128)
@@ -93,6 +84,9 @@ __host__ __device__ inline SmemLayout smem_layout(int I, int Je, int N, int bloc
     L.node = o;  o += align16(sizeof(float) * (size_t)I);
     L.ab = o;    o += align16(sizeof(float2) * (size_t)I);
     L.tdt = o;   if (extra) o += align16(sizeof(float) * (size_t)N);
+    // the adjoint kernel slices these three per warp from L.qslot: they stay
+    // contiguous because each size is a multiple of 16 bytes (kQueue is)
+    static_assert(kQueue % 4 == 0, "FIFO arrays must stay contiguous");
     L.qslot = o; if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue * ppl);
     L.qrel = o;  if (greeks) o += align16(sizeof(int) * (size_t)W * kQueue * ppl);
     L.qxb = o;   if (greeks) o += align16(sizeof(float) * (size_t)W * kQueue * ppl);
@@ -218,9 +212,12 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
     const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS, EXTRA, PPL);
     stage_grid<GS, EXTRA>(P, smem, L);
     float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);    // this block's level-1 buckets
-    int* q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * kQcap;
-    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQcap;
-    float* q_xb = reinterpret_cast<float*>(smem + L.qxb) + warp * kQcap;
+    // the three FIFO arrays of all warps are contiguous from L.qslot (each
+    // W * kQcap words): one base per warp, the others at fixed offsets, which
+    // keeps two registers free for the packed forward pass
+    int* const q_slot = reinterpret_cast<int*>(smem + L.qslot) + warp * 3 * kQcap;
+    int* const q_rel = q_slot + kQcap;
+    float* const q_xb = reinterpret_cast<float*>(q_slot + 2 * kQcap);
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     const int nIJ = P.Je * P.I;
     for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
@@ -278,7 +275,9 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
             q_head = (q_head + nb) & (kQcap - 1);
             q_count -= nb;
             __syncwarp();
-            if (++batches % P.flush_every == 0) drain_buckets<ACC>(l1, nIJ, wrow);
+            if (++batches % P.flush_every == 0)      // the level-2 row, recomputed (one register less)
+                drain_buckets<ACC>(l1, nIJ, ACC == 1 ? P.warp_rows + (size_t)wid * nIJ
+                                                     : P.partials + (size_t)blockIdx.x * P.row_words + 3);
             continue;
         }
         if (!more) break;
@@ -293,8 +292,8 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 path_counter(P, rel_a, c1a, c2a);
                 path_counter(P, rel_b, c1b, c2b);
                 float ya, yb;
-                forward_path2<KCK, true, false, MODEL, kPackForward<KCK, ACC, GS>>(
-                    P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b, cks, rel_a, rel_b, false, ya, yb);
+                forward_path2<KCK, true, false, MODEL, true>(P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b,
+                                                             cks, rel_a, rel_b, false, ya, yb);
                 float V;
                 payoff<MODEL>(P, ya, V, xa);
                 acc_add<ACC>(acc[0], V);
