@@ -363,6 +363,10 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
     // fold: remaining level-1 buckets (and, in Kahan mode, every warp row of
     // this block) into the block's binary64 row (after the barrier nothing adds)
     __syncthreads();
+    // the kernel that also sums d V / d r and d V / d T recomputes its row here
+    // instead of keeping the pointer live through the loop (80 registers, 6
+    // blocks per SM, instead of 87 and 5)
+    double* const row_f = EXTRA ? P.partials + (size_t)blockIdx.x * P.row_words : row;
     const double* rows0 = P.warp_rows + (size_t)blockIdx.x * W * nIJ;
     for (int e = tid; e < nIJ; e += B) {
         if (ACC == 1) {
@@ -371,15 +375,15 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 const float2 k = reinterpret_cast<const float2*>(rows0 + (size_t)w * nIJ)[e];
                 s += (double)k.x - (double)k.y;
             }
-            row[3 + e] = s;
+            row_f[3 + e] = s;
         } else {
-            row[3 + e] += (double)l1[e];
+            row_f[3 + e] += (double)l1[e];
         }
     }
-    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row);
+    block_scalars(acc_value<ACC>(acc[0]), acc_value<ACC>(acc[B]), acc_value<ACC>(acc[2 * B]), s_red, row_f);
     if (EXTRA) {
         __syncthreads();                       // s_red is reused
-        block_scalars(acc_value<ACC>(acc[3 * B]), acc_value<ACC>(acc[4 * B]), 0.0, s_red, row + 3 + nIJ, 2);
+        block_scalars(acc_value<ACC>(acc[3 * B]), acc_value<ACC>(acc[4 * B]), 0.0, s_red, row_f + 3 + nIJ, 2);
     }
 }
 
