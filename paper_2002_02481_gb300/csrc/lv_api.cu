@@ -465,6 +465,18 @@ lv_status run_mc(lv_surface_s* h, const McCall& c)
     return LV_OK;
 }
 
+// Brings the binary64 sigma on the device up to the last lv_surface_set_sigma
+// (stream-ordered before the caller's launches).
+lv_status sigma64_current(lv_surface_s* h)
+{
+    if (h->sig64_stale) {
+        LV_CUDA(cudaMemcpyAsync(h->d_sig64, h->h_sig64_stage, sizeof(double) * (size_t)h->I * h->J,
+                                cudaMemcpyHostToDevice, h->stream));
+        h->sig64_stale = false;
+    }
+    return LV_OK;
+}
+
 lv_status fetch_result(lv_surface_s* h, bool extra = false)
 {
     const size_t n = 3 + (size_t)h->I * h->J + (extra ? 2 : 0);
@@ -597,9 +609,10 @@ lv_status lv_surface_set_sigma(lv_surface_t h, const double* sigma)
     // the staging buffer may still feed an earlier asynchronous copy
     LV_CUDA(cudaStreamSynchronize(h->stream));
     pack_sigma(h, sigma, h->h_sig_stage);
+    // the binary64 copy only feeds the binary64 reference and bump calls, which
+    // upload it when they run (sigma64_current); the binary32 pairs go now
     std::memcpy(h->h_sig64_stage, sigma, sizeof(double) * (size_t)h->I * h->J);
-    LV_CUDA(cudaMemcpyAsync(h->d_sig64, h->h_sig64_stage, sizeof(double) * (size_t)h->I * h->J,
-                            cudaMemcpyHostToDevice, h->stream));
+    h->sig64_stale = true;
     LV_CUDA(cudaMemcpyAsync(h->d_sig, h->h_sig_stage, sizeof(float2) * (size_t)h->Je * (h->I - 1),
                             cudaMemcpyHostToDevice, h->stream));
     return LV_OK;
@@ -1026,6 +1039,8 @@ lv_status lv_price_greeks_fp64_device(lv_surface_t h, double S0, double r, doubl
     if (st != LV_OK) return st;
     char* base = static_cast<char*>(h->d_scratch);
     const double dt = T / (double)n_steps;
+    st = sigma64_current(h);
+    if (st != LV_OK) return st;
     lv::F64Params P{};
     P.spot = h->d_spot64;
     P.sig = h->d_sig64;
@@ -1101,6 +1116,8 @@ lv_status lv_bump_greeks_fp64(lv_surface_t h, double S0, double r, double K, dou
     char* base = static_cast<char*>(h->d_scratch);
     const double dt = T / (double)n_steps;
     const double eps_S = eps * S0;             // the spot bump of the same relative size
+    st = sigma64_current(h);
+    if (st != LV_OK) return st;
     lv::F64Params P{};
     P.spot = h->d_spot64;
     P.sig = h->d_sig64;

@@ -279,6 +279,7 @@ struct lv_surface_s {
     double* d_spot64 = nullptr;      // [I] spot nodes, binary64 (the binary64 kernels)
     double* d_sig64 = nullptr;       // [I * J] sigma, binary64, spot-major
     double* h_sig64_stage = nullptr; // pinned staging for its uploads
+    bool sig64_stale = false;        // d_sig64 behind h_sig64_stage: uploaded by the binary64 calls
     float2* h_sig_stage = nullptr;   // pinned staging for sigma uploads
     int log_uniform = 0;
     float cell_scale = 0.0f, cell_shift = 0.0f, s_lo = 0.0f, s_hi = 0.0f;

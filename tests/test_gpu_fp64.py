@@ -108,3 +108,31 @@ def test_fp64_bump_converges_to_the_pathwise_adjoint(lib):
     assert np.max(np.abs(v - ref["vega"])) <= 1e-4 * vmax
     assert abs(d - ref["delta"]) <= 1e-4 * abs(ref["delta"])
     s.close()
+
+
+def test_fp64_follows_set_sigma(lib):
+    """lv_surface_set_sigma uploads the binary64 copy of sigma only when a
+    binary64 call needs it: a handle created with one grid and then given
+    another gives the binary64 results of a handle created with the second,
+    also after a binary32 call in between and with two grid changes before
+    the binary64 call."""
+    import dataclasses
+    import torch
+    surf, opt = W.config_small()
+    opt.n_paths = 1 << 12
+    rng = np.random.default_rng(11)
+    sig2 = surf.sigma * (1.0 + 0.2 * rng.random(surf.sigma.shape))
+    sig3 = surf.sigma * (1.0 - 0.1 * rng.random(surf.sigma.shape))
+    ref = _fp64(lib, dataclasses.replace(surf, sigma=sig3), opt)
+    s = lv.Surface.from_workload(surf, lib)
+    s.set_stream(torch.cuda.current_stream().cuda_stream)
+    d = torch.zeros(3 + surf.n_spot * surf.n_time, dtype=torch.float64, device="cuda")
+    s.set_sigma(sig2)
+    s.price_greeks(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    s.set_sigma(sig3)
+    s.price_greeks_fp64_device(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed, d.data_ptr())
+    torch.cuda.synchronize()
+    got = d.cpu().numpy()
+    s.close()
+    assert abs(got[0] - ref[0]) <= 1e-12 * abs(ref[0]) and abs(got[1] - ref[1]) <= 1e-12 * abs(ref[1])
+    assert np.max(np.abs(got[3:] - ref[3:])) <= 1e-12 * np.max(np.abs(ref[3:]))
