@@ -65,8 +65,14 @@ def test_small_skew_16384_paths(lib):
 
 def test_paper_shape_full_size(lib):
     """30x60 grid, 156 steps, 2^20 paths: every path checked, aggregates at
-    full size in the default launch shape."""
+    full size in the default launch shape, which is the one the benchmark's
+    tuner picks on GB300 (block 128, checkpoints every 4 steps, two paths per
+    lane in packed pairs)."""
     surf, opt = W.config_paper_shape()
+    s = G.make_surface(surf, opt, lib)
+    assert s.get_launch(opt.n_steps, True)[:2] == (128, 4)
+    assert s.get_paths_per_lane(opt.n_steps, opt.n_paths) == 2
+    s.close()
     _report("30x60 grid, 156 steps, 2^20 paths", G.full_parity(surf, opt, lib, label="paper shape"))
 
 
