@@ -393,7 +393,9 @@ lv_status lv_debug_time_table(lv_surface_t h, double T, int32_t n_steps, int32_t
  * synchronising.
  *  - It calls no allocator: its scratch is a static 64 MiB device array that
  *    every GPU loading this library keeps until the process exits. When a
- *    launch at full width does not fit, fewer blocks run; a problem whose
+ *    launch at full width does not fit, it runs one path per lane (unless
+ *    lv_set_paths_per_lane or the tuner chose two) and then, if still
+ *    needed, fewer blocks; a problem whose
  *    single block does not fit (very large n_spot * n_time with many steps)
  *    is rejected with LV_EINVAL and a message giving the bytes needed.
  *  - The first call on each device looks up the array's device address

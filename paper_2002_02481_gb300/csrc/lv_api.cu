@@ -1354,9 +1354,22 @@ extern "C" lv_status lv_price_greeks_device_noalloc(lv_surface_t h, double S0, d
     const int warps = block / 32;
     const int64_t tiles = (n_paths + lv::paths_per_tile(true) - 1) / lv::paths_per_tile(true);
     const int64_t want_blocks = (tiles + warps - 1) / warps;
+    size_t off_part = 0, off_chunks = 0, off_wrows = 0, off_l1 = 0, off_ckpt = 0;
+    // two paths per lane double each block's checkpoint ring: unless the caller
+    // asked for them, run one path per lane when the full-width grid would not
+    // fit in the static array at two (one fits about twice as many blocks)
+    if (ppl == 2 && h->cfg_ppl == 0) {
+        const int64_t full = want_blocks < (int64_t)bps * h->num_sms ? want_blocks : (int64_t)bps * h->num_sms;
+        if (static_plan_bytes(h, (int)full, block, k, 2, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1,
+                              &off_ckpt) > kStaticScratchBytes) {
+            h->cfg_ppl = 1;
+            st = choose_launch(h, n_steps, true, &block, &k, &bps, false, &grid_smem, false, false, &ppl, n_paths);
+            h->cfg_ppl = 0;
+            if (st != LV_OK) return st;
+        }
+    }
     const int64_t slots = (int64_t)bps * h->num_sms;
     int grid = (int)(want_blocks < slots ? want_blocks : slots);
-    size_t off_part = 0, off_chunks = 0, off_wrows = 0, off_l1 = 0, off_ckpt = 0;
     // the most blocks (at most the full-width grid) whose scratch fits in the static array;
     // the plan's size grows with the grid, so bisect
     if (static_plan_bytes(h, grid, block, k, ppl, n_steps, &off_part, &off_chunks, &off_wrows, &off_l1, &off_ckpt) >
