@@ -23,7 +23,11 @@
 //       corner buckets with the bilinear weights.
 // A reverse batch runs when 32 paths are queued, when the oldest queued
 // path's checkpoint slots are about to be reused by the next forward tile,
-// and at the end; so the reverse sweeps run on full warps.
+// and at the end; so the reverse sweeps run on full warps. With two paths
+// per lane (PPL = 2) a warp claims two consecutive tiles and advances each
+// lane's two paths together, their binary32 arithmetic in packed .f32x2
+// pairs (forward_path2); the slot groups and the FIFO double, the reverse
+// batches stay at 32 paths.
 //
 // Bucket accumulation: run-length sums in registers while the cell is
 // unchanged (level 0); binary32 reductions (red.global.add.f32, resolved in
