@@ -183,6 +183,35 @@ __device__ __forceinline__ void normals4x2_neg(uint32_t blk, uint32_t c1a, uint3
     }
 }
 
+// normals4 of one path, NEGATED (nz[q] = -z[q] bit for bit), with the pairs
+// (0, 2) and (1, 3) of its binary32 arithmetic in packed pairs: the uniforms'
+// shift, the -2 ln 2 scale, the angle's shift and scale, and the rho cos / rho
+// sin products, each element rounded as in normals4.
+__device__ __forceinline__ void normals4_neg(uint32_t blk, uint32_t c1, uint32_t c2, uint32_t k0, uint32_t k1,
+                                             float nz[4])
+{
+    uint32_t w0 = blk, w1 = c1, w2 = c2, w3 = 0u;
+    philox4x32_10(w0, w1, w2, w3, k0, k1);
+    const f32x2 one_m = pk2(__uint_as_float(0x3f7fffffu), __uint_as_float(0x3f7fffffu));
+    const f32x2 u02 = sub2(pk2(__uint_as_float((w0 >> 9) | 0x3f800000u), __uint_as_float((w2 >> 9) | 0x3f800000u)),
+                           one_m);
+    const f32x2 u13 = sub2(pk2(__uint_as_float((w1 >> 9) | 0x3f800000u), __uint_as_float((w3 >> 9) | 0x3f800000u)),
+                           one_m);
+    const f32x2 l = mul2(pk2(-1.3862943611198906f, -1.3862943611198906f),
+                         pk2(lg2_approx(lo2(u02)), lg2_approx(hi2(u02))));
+    const f32x2 rho = pk2(sqrt_approx(lo2(l)), sqrt_approx(hi2(l)));
+    const f32x2 ang = mul2(pk2(6.2831853071795865f, 6.2831853071795865f), sub2(u13, pk2(0.5f, 0.5f)));
+    float s0, c0, s2, c2v;
+    __sincosf(lo2(ang), &s0, &c0);
+    __sincosf(hi2(ang), &s2, &c2v);
+    const f32x2 zc = mul2(rho, pk2(c0, c2v));
+    const f32x2 zs = mul2(rho, pk2(s0, s2));
+    nz[0] = lo2(zc);
+    nz[1] = lo2(zs);
+    nz[2] = hi2(zc);
+    nz[3] = hi2(zs);
+}
+
 // Time data of step n: t_n = n dt, j_n = the largest j <= J-2 with
 // tau_j <= t_n, v_n = (t_n - tau_j) / (tau_{j+1} - tau_j) clamped to
 // [0, 1], decided in binary64. Returned as (j (I-1), (j+1) (I-1), j I, bits
@@ -542,7 +571,10 @@ __device__ __forceinline__ void path_counter(const McParams& P, long long rel, u
 // (i+1, j+1) with the bilinear weights. Corner sums are kept in registers
 // while the cell is unchanged and then added to the block's binary32 buckets
 // `l1` (time-major, row j * I) with red.global.add.f32. Returns d V / d x_0.
-template <int KCK, int MODEL = 0, bool EXTRA = false>
+// With NEG (main reading, no extra sums) the recompute takes its normals from
+// normals4_neg and uses sqdt Z = (-sqdt)(-Z) and sqdt2 Z = (-sqdt2)(-Z),
+// which are exact, so every value is the same bit for bit.
+template <int KCK, int MODEL = 0, bool EXTRA = false, bool NEG = false>
 __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid& g, uint32_t c1, uint32_t c2,
                                               const float* ck, size_t cks, float xbar, float* l1,
                                               float* rho_acc = nullptr, float* t_acc = nullptr)
@@ -562,14 +594,24 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
         for (int q = 0; q < KCK; ++q) {
             const int n = m * KCK + q;
             if (n < P.N) {
-                if ((q & 3) == 0) normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
+                constexpr bool kNeg = NEG && MODEL == 0 && !EXTRA;
+                if ((q & 3) == 0) {
+                    if (kNeg) normals4_neg((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
+                    else normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
+                }
                 const int4 tb = g.tab[n];
                 const StepEval ev = eval_sigma<true, MODEL>(P, g, x, tb);
-                adjoint_factors<MODEL>(P, ev, z[q & 3], hq[q], gq[q]);
+                if (kNeg) {                    // z holds -Z
+                    hq[q] = fmaf(-P.sqdt, z[q & 3], -ev.sigma * P.dt);
+                    gq[q] = hq[q] * ev.sslope;
+                } else {
+                    adjoint_factors<MODEL>(P, ev, z[q & 3], hq[q], gq[q]);
+                }
                 if (EXTRA) extra_factors<MODEL>(P, ev, z[q & 3], hq[q], g.tdt[n], aq[EXTRA ? q : 0], tq[EXTRA ? q : 0]);
                 uq[q] = ev.u;
                 iq[q] = ev.i;
-                x = step_state<MODEL>(P, x, ev.sigma, z[q & 3]);
+                if (kNeg) x = x + fmaf(ev.sigma, -P.sqdt2 * z[q & 3], fmaf(-P.hdt * ev.sigma, ev.sigma, P.rdt));
+                else x = step_state<MODEL>(P, x, ev.sigma, z[q & 3]);
             }
         }
 #pragma unroll

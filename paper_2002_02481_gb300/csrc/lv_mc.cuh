@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 uint32_t c1, c2;
                 path_counter(P, rel, c1, c2);
                 float ra = 0.0f, ta = 0.0f;
-                xbar = reverse_path<KCK, MODEL, EXTRA>(P, g, c1, c2, ckw + slot, cks, xbar, l1, &ra, &ta);
+                xbar = reverse_path<KCK, MODEL, EXTRA, PPL == 2>(P, g, c1, c2, ckw + slot, cks, xbar, l1, &ra, &ta);
                 acc_add<ACC>(acc[2 * B], xbar);
                 if (EXTRA) {
                     acc_add<ACC>(acc[3 * B], ra);
