@@ -697,6 +697,74 @@ __device__ __forceinline__ float tangent_forward(const McParams& P, const SmemGr
     return y;
 }
 
+// Pass 1 for two paths at once (main reading), their binary32 arithmetic in
+// packed pairs as in forward_path2: per path every value is rounded as in
+// tangent_forward (same y_N, D_N and tiny flag). The slope's time blend and
+// spot factor, h = sqdt Z - sigma dt = (-sqdt)(-Z) + (-dt) sigma, 1 + g_n and
+// the product D run in pairs; the inside-grid test and the running minimum of
+// |1 + g_n| stay per path.
+__device__ __forceinline__ void tangent_forward2(const McParams& P, const SmemGrid& g, uint32_t c1a, uint32_t c2a,
+                                                 uint32_t c1b, uint32_t c2b, float& ya_out, float& yb_out,
+                                                 float& Da, float& Db, bool& tiny_a, bool& tiny_b)
+{
+    const f32x2 csc = pk2(P.cell_scale, P.cell_scale), csh = pk2(P.cell_shift, P.cell_shift);
+    const f32x2 nsq2 = pk2(-P.sqdt2, -P.sqdt2), nhdt = pk2(-P.hdt, -P.hdt), rdt = pk2(P.rdt, P.rdt);
+    const f32x2 nsqdt = pk2(-P.sqdt, -P.sqdt), ndt = pk2(-P.dt, -P.dt), one = pk2(1.0f, 1.0f);
+    f32x2 y = pk2(P.x0, P.x0), d = one;
+    float fmin_a = 1.0f, fmin_b = 1.0f;
+    f32x2 nz[4];
+    for (int n0 = 0; n0 < P.N; n0 += 4) {
+        normals4x2_neg((uint32_t)(n0 >> 2), c1a, c2a, c1b, c2b, P.k0, P.k1, nz);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int n = n0 + q;
+            if (n < P.N) {
+                const int4 tb = g.tab[n];
+                const float v = __int_as_float(tb.w);
+                const f32x2 vv = pk2(v, v);
+                // eval_sigma<true, 0> for both paths
+                const float Sa = ex2_approx(lo2(y)), Sb = ex2_approx(hi2(y));
+                int ia, ib;
+                if (P.log_uniform) {
+                    const f32x2 ci = fma2(y, csc, csh);
+                    ia = min(max(__float2int_rd(lo2(ci)), 0), P.I - 2);
+                    ib = min(max(__float2int_rd(hi2(ci)), 0), P.I - 2);
+                } else {
+                    ia = spot_cell(P, g, lo2(y), Sa);
+                    ib = spot_cell(P, g, hi2(y), Sb);
+                }
+                const float2 aba = g.ab[ia], abb = g.ab[ib];
+                const float ua = __saturatef(fmaf(Sa, aba.x, aba.y));
+                const float ub = __saturatef(fmaf(Sb, abb.x, abb.y));
+                const float2 loa = g.sig2[tb.x + ia], hia = g.sig2[tb.y + ia];
+                const float2 lob = g.sig2[tb.x + ib], hib = g.sig2[tb.y + ib];
+                const f32x2 top = pk2(fmaf(ua, loa.y, loa.x), fmaf(ub, lob.y, lob.x));
+                const f32x2 bot = pk2(fmaf(ua, hia.y, hia.x), fmaf(ub, hib.y, hib.x));
+                const f32x2 sig = fma2(vv, sub2(bot, top), top);
+                const f32x2 ly = pk2(loa.y, lob.y);
+                const f32x2 sl = mul2(pk2(Sa, Sb), mul2(fma2(vv, sub2(pk2(hia.y, hib.y), ly), ly), pk2(aba.x, abb.x)));
+                const f32x2 slope = pk2((Sa >= P.s_lo) && (Sa <= P.s_hi) ? lo2(sl) : 0.0f,
+                                        (Sb >= P.s_lo) && (Sb <= P.s_hi) ? hi2(sl) : 0.0f);
+                // adjoint_factors<0> and tangent_factor<0>
+                const f32x2 h = fma2(nsqdt, nz[q], mul2(ndt, sig));
+                const f32x2 f = fma2(h, slope, one);
+                fmin_a = fminf(fmin_a, fabsf(lo2(f)));
+                fmin_b = fminf(fmin_b, fabsf(hi2(f)));
+                d = mul2(d, f);
+                // euler_step
+                const f32x2 t3 = fma2(mul2(nhdt, sig), sig, rdt);
+                y = add2(y, fma2(sig, mul2(nsq2, nz[q]), t3));
+            }
+        }
+    }
+    ya_out = lo2(y);
+    yb_out = hi2(y);
+    Da = lo2(d);
+    Db = hi2(d);
+    tiny_a = fmin_a < 0x1p-20f;
+    tiny_b = fmin_b < 0x1p-20f;
+}
+
 // Pass 2: regenerates one path (same counters, same arithmetic) and spreads
 // sigma_bar_n = c h_n / D_{n+1}, c = xbar_N D_N, over the corner buckets of
 // its cell with the bilinear weights, through the same run-length register

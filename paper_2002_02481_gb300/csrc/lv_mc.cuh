@@ -397,17 +397,18 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
 // the paths with xbar_N != 0 join the warp's queue with c = xbar_N D_N. At
 // 32 queued paths (and at the end) the warp runs pass 2 (tangent_scatter)
 // on them as a full-warp batch. Buckets go through the same levels 0-3.
-template <int ACC, bool GS, int MODEL>
+template <int ACC, bool GS, int MODEL, int PPL = 1>
 __global__ void __launch_bounds__(128, 6) tangent_kernel(const __grid_constant__ McParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = blockDim.x, W = B >> 5;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
+    constexpr int kQcap = kQueue * PPL;
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS, false, PPL);
     stage_grid<GS>(P, smem, L);
     float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);
-    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
-    float* q_c = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
+    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQcap;
+    float* q_c = reinterpret_cast<float*>(smem + L.qxb) + warp * kQcap;
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     const int nIJ = P.Je * P.I;
     for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
@@ -428,24 +429,66 @@ __global__ void __launch_bounds__(128, 6) tangent_kernel(const __grid_constant__
     AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
     acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
     int q_head = 0, q_count = 0, batches = 0;
-    int tile = claim_tile(P.tile_counter);
+    int tile = claim_tile(P.tile_counter, PPL);
     while (true) {
         const bool more = tile < P.n_tiles;
         if (q_count >= 32 || (!more && q_count > 0)) {
             const int nb = min(32, q_count);
             if (lane < nb) {
-                const int e = (q_head + lane) & (kQueue - 1);
+                const int e = (q_head + lane) & (kQcap - 1);
                 uint32_t c1, c2;
                 path_counter(P, q_rel[e], c1, c2);
                 tangent_scatter<MODEL>(P, g, c1, c2, q_c[e], l1);
             }
-            q_head = (q_head + nb) & (kQueue - 1);
+            q_head = (q_head + nb) & (kQcap - 1);
             q_count -= nb;
             __syncwarp();
             if (++batches % P.flush_every == 0) drain_buckets<ACC>(l1, nIJ, wrow);
             continue;
         }
         if (!more) break;
+        if constexpr (PPL == 2) {
+            // pass 1 on tiles tile, tile + 1: two paths per lane in packed pairs
+            const long long rel_a = (long long)tile * kTile + lane, rel_b = rel_a + kTile;
+            float xa = 0.0f, xb = 0.0f, ca = 0.0f, cb = 0.0f;
+            if (rel_a < P.n_paths) {
+                uint32_t c1a, c2a, c1b, c2b;
+                path_counter(P, rel_a, c1a, c2a);
+                path_counter(P, rel_b, c1b, c2b);
+                float ya, yb, Da, Db, V;
+                bool ta, tb;
+                tangent_forward2(P, g, c1a, c2a, c1b, c2b, ya, yb, Da, Db, ta, tb);
+                payoff<0>(P, ya, V, xa);
+                ca = xa * Da;
+                acc_add<ACC>(acc[0], V);
+                acc_add<ACC>(acc[B], V * V);
+                acc_add<ACC>(acc[2 * B], ca);
+                if (ta && xa != 0.0f) atomicAdd(P.flag, 1u);
+                if (rel_b < P.n_paths) {
+                    payoff<0>(P, yb, V, xb);
+                    cb = xb * Db;
+                    acc_add<ACC>(acc[0], V);
+                    acc_add<ACC>(acc[B], V * V);
+                    acc_add<ACC>(acc[2 * B], cb);
+                    if (tb && xb != 0.0f) atomicAdd(P.flag, 1u);
+                }
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const float x = hh ? xb : xa;
+                const bool live = x != 0.0f;
+                const unsigned bal = __ballot_sync(0xffffffffu, live);
+                if (live) {
+                    const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
+                    q_rel[e] = (int)(hh ? rel_b : rel_a);
+                    q_c[e] = hh ? cb : ca;
+                }
+                q_count += __popc(bal);
+            }
+            __syncwarp();
+            tile = claim_tile(P.tile_counter, PPL);
+            continue;
+        }
         const long long rel = (long long)tile * kTile + lane;
         float xbarN = 0.0f, c = 0.0f;
         if (rel < P.n_paths) {
@@ -465,13 +508,13 @@ __global__ void __launch_bounds__(128, 6) tangent_kernel(const __grid_constant__
         const bool live = xbarN != 0.0f;
         const unsigned bal = __ballot_sync(0xffffffffu, live);
         if (live) {
-            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
+            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
             q_rel[e] = (int)rel;
             q_c[e] = c;
         }
         q_count += __popc(bal);
         __syncwarp();
-        tile = claim_tile(P.tile_counter);
+        tile = claim_tile(P.tile_counter, PPL);
     }
     __syncthreads();
     const double* rows0 = P.warp_rows + (size_t)blockIdx.x * W * nIJ;
@@ -496,17 +539,18 @@ __global__ void __launch_bounds__(128, 6) tangent_kernel(const __grid_constant__
 // live paths are queued and scattered in full-warp batches. Main reading,
 // binary64 level 2. Rows: price sums as usual, buckets d^2 price / (d S0 d
 // sigma_ij) summed over paths.
-template <bool GS>
+template <bool GS, int PPL = 1>
 __global__ void __launch_bounds__(128, 6) vanna_kernel(const __grid_constant__ McParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS);
+    constexpr int kQcap = kQueue * PPL;
+    const SmemLayout L = smem_layout(P.I, P.Je, P.N, B, true, GS, false, PPL);
     stage_grid<GS>(P, smem, L);
     float* l1 = P.l1 + (size_t)blockIdx.x * (P.Je * P.I);
-    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQueue;
-    float* q_c = reinterpret_cast<float*>(smem + L.qxb) + warp * kQueue;
+    int* q_rel = reinterpret_cast<int*>(smem + L.qrel) + warp * kQcap;
+    float* q_c = reinterpret_cast<float*>(smem + L.qxb) + warp * kQcap;
     double* s_red = reinterpret_cast<double*>(smem + L.red);
     const int nIJ = P.Je * P.I;
     for (int e = tid; e < nIJ; e += B) l1[e] = 0.0f;
@@ -520,24 +564,66 @@ __global__ void __launch_bounds__(128, 6) vanna_kernel(const __grid_constant__ M
     AccSlot* acc = reinterpret_cast<AccSlot*>(smem + L.acc) + tid;   // [3][block]: V, V^2, xbar_0
     acc[0] = acc[B] = acc[2 * B] = AccSlot{0.0, 0.0f, 0.0f};
     int q_head = 0, q_count = 0, batches = 0;
-    int tile = claim_tile(P.tile_counter);
+    int tile = claim_tile(P.tile_counter, PPL);
     while (true) {
         const bool more = tile < P.n_tiles;
         if (q_count >= 32 || (!more && q_count > 0)) {
             const int nb = min(32, q_count);
             if (lane < nb) {
-                const int e = (q_head + lane) & (kQueue - 1);
+                const int e = (q_head + lane) & (kQcap - 1);
                 uint32_t c1, c2;
                 path_counter(P, q_rel[e], c1, c2);
                 vanna_scatter(P, g, c1, c2, q_c[e] * P.inv_S0, l1);
             }
-            q_head = (q_head + nb) & (kQueue - 1);
+            q_head = (q_head + nb) & (kQcap - 1);
             q_count -= nb;
             __syncwarp();
             if (++batches % P.flush_every == 0) drain_buckets<0>(l1, nIJ, wrow);
             continue;
         }
         if (!more) break;
+        if constexpr (PPL == 2) {
+            // pass 1 on tiles tile, tile + 1: two paths per lane in packed pairs
+            const long long rel_a = (long long)tile * kTile + lane, rel_b = rel_a + kTile;
+            float xa = 0.0f, xb = 0.0f, ca = 0.0f, cb = 0.0f;
+            if (rel_a < P.n_paths) {
+                uint32_t c1a, c2a, c1b, c2b;
+                path_counter(P, rel_a, c1a, c2a);
+                path_counter(P, rel_b, c1b, c2b);
+                float ya, yb, Da, Db, V;
+                bool ta, tb;
+                tangent_forward2(P, g, c1a, c2a, c1b, c2b, ya, yb, Da, Db, ta, tb);
+                payoff<0>(P, ya, V, xa);
+                ca = xa * Da;
+                acc_add<0>(acc[0], V);
+                acc_add<0>(acc[B], V * V);
+                acc_add<0>(acc[2 * B], ca);
+                if (ta && xa != 0.0f) atomicAdd(P.flag, 1u);
+                if (rel_b < P.n_paths) {
+                    payoff<0>(P, yb, V, xb);
+                    cb = xb * Db;
+                    acc_add<0>(acc[0], V);
+                    acc_add<0>(acc[B], V * V);
+                    acc_add<0>(acc[2 * B], cb);
+                    if (tb && xb != 0.0f) atomicAdd(P.flag, 1u);
+                }
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const float x = hh ? xb : xa;
+                const bool live = x != 0.0f;
+                const unsigned bal = __ballot_sync(0xffffffffu, live);
+                if (live) {
+                    const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
+                    q_rel[e] = (int)(hh ? rel_b : rel_a);
+                    q_c[e] = hh ? cb : ca;
+                }
+                q_count += __popc(bal);
+            }
+            __syncwarp();
+            tile = claim_tile(P.tile_counter, PPL);
+            continue;
+        }
         const long long rel = (long long)tile * kTile + lane;
         float xbarN = 0.0f, c = 0.0f;
         if (rel < P.n_paths) {
@@ -557,13 +643,13 @@ __global__ void __launch_bounds__(128, 6) vanna_kernel(const __grid_constant__ M
         const bool live = xbarN != 0.0f;
         const unsigned bal = __ballot_sync(0xffffffffu, live);
         if (live) {
-            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1);
+            const int e = (q_head + q_count + __popc(bal & ((1u << lane) - 1u))) & (kQcap - 1);
             q_rel[e] = (int)rel;
             q_c[e] = c;
         }
         q_count += __popc(bal);
         __syncwarp();
-        tile = claim_tile(P.tile_counter);
+        tile = claim_tile(P.tile_counter, PPL);
     }
     __syncthreads();
     for (int e = tid; e < nIJ; e += B) row[3 + e] += (double)l1[e];
@@ -640,10 +726,16 @@ cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
 template <int MODEL, bool GS, typename F>
 cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, bool extra, F&& f, int ppl = 1)
 {
-    if (ppl == 2) {        // two paths per lane: the main reading's reverse sweep, k = 4 or 8
-        if constexpr (MODEL == 0) {
+    if (ppl == 2) {        // two paths per lane: the main reading's reverse sweep (k = 4 or 8),
+        if constexpr (MODEL == 0) {    // tangent-ratio adjoint and second-order buckets
             static bool cp[4] = {};
-            if (!greeks || dbg || extra || method != LV_ADJ_REVERSE) return cudaErrorInvalidValue;
+            static bool cv2 = false, ct2[2] = {};
+            if (!greeks || dbg || extra) return cudaErrorInvalidValue;
+            if (method == kMethodVanna)
+                return acc == 0 ? f(vanna_kernel<GS, 2>, cv2) : cudaErrorInvalidValue;
+            if (method == LV_ADJ_TANGENT)
+                return acc ? f(tangent_kernel<1, GS, 0, 2>, ct2[1]) : f(tangent_kernel<0, GS, 0, 2>, ct2[0]);
+            if (method != LV_ADJ_REVERSE) return cudaErrorInvalidValue;
             switch (k * 2 + acc) {
             case 8: return f(adjoint_kernel<4, 0, false, GS, 0, false, 2>, cp[0]);
             case 9: return f(adjoint_kernel<4, 1, false, GS, 0, false, 2>, cp[1]);

@@ -59,6 +59,31 @@ def test_both_level2_modes(lib, acc):
             G.full_parity(surf, opt, lib, accumulation=acc, label=f"acc={acc}", method=T))
 
 
+@pytest.mark.parametrize("case", ["20x10", "30x60 2^18 binary64", "30x60 2^18 Kahan", "edge: 33 paths",
+                                  "edge: put, uneven grid"])
+def test_two_paths_per_lane(case, lib):
+    """Pass 1 on two paths per lane, their binary32 arithmetic in packed
+    pairs (tangent_forward2): the same per-path arithmetic, checked against
+    the oracle path for path in both level-2 modes, with the binary search
+    for the cell (uneven grid) and a ragged last tile."""
+    acc = 0
+    if case == "20x10":
+        surf, opt = W.config_small()
+    elif case.startswith("30x60"):
+        surf, opt = W.config_paper_shape()
+        opt.n_paths = 1 << 18
+        acc = 1 if case.endswith("Kahan") else 0
+    elif case == "edge: 33 paths":
+        _, surf, opt = EDGE[5]
+    else:
+        _, surf, opt = EDGE[2]
+    s = G.make_surface(surf, opt, lib, accumulation=acc, method=T, ppl=2)
+    assert s.get_paths_per_lane(opt.n_steps, opt.n_paths) == 2
+    s.close()
+    _report(f"two paths per lane: {case}",
+            G.full_parity(surf, opt, lib, accumulation=acc, label=case, method=T, ppl=2))
+
+
 def test_matches_the_reverse_sweep_on_the_same_paths(lib):
     """Same paths, same payoffs: the two forms differ only in rounding and
     reduction order."""

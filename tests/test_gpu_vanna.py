@@ -29,8 +29,8 @@ def lib():
     return lv.load()
 
 
-def _parity(surf, opt, lib, label):
-    gs = G.make_surface(surf, opt, lib)
+def _parity(surf, opt, lib, label, ppl=0):
+    gs = G.make_surface(surf, opt, lib, ppl=ppl)
     dec, stats = G.per_path(gs, surf, opt)
     ref = oracle.run_vanna(surf, opt, decisions=dec)
     p, d, vn = gs.price_greeks_vanna(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
@@ -62,6 +62,33 @@ def test_vanna_paper_grid(lib):
     surf, opt = W.config_paper_shape()
     opt.n_paths = 1 << 18
     _parity(surf, opt, lib, "30x60, 2^18 paths")
+
+
+@pytest.mark.parametrize("case", ["20x10", "30x60, 2^18 paths", "edge: 33 paths", "edge: put, uneven grid"])
+def test_vanna_two_paths_per_lane(case, lib):
+    """Pass 1 on two paths per lane, their binary32 arithmetic in packed
+    pairs (tangent_forward2): the same per-path values, so the same parity
+    with the oracle; and the same results as one path per lane up to
+    reduction order."""
+    if case == "20x10":
+        surf, opt = W.config_small()
+    elif case == "30x60, 2^18 paths":
+        surf, opt = W.config_paper_shape()
+        opt.n_paths = 1 << 18
+    elif case == "edge: 33 paths":
+        _, surf, opt = EDGE[5]
+    else:
+        _, surf, opt = EDGE[2]
+    _parity(surf, opt, lib, case + " (two paths per lane)", ppl=2)
+    a = G.make_surface(surf, opt, lib, ppl=1)
+    b = G.make_surface(surf, opt, lib, ppl=2)
+    assert b.get_paths_per_lane(opt.n_steps, opt.n_paths) == 2
+    pa, da, va = a.price_greeks_vanna(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    pb, db, vb = b.price_greeks_vanna(opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
+    assert abs(pb - pa) <= 1e-12 * max(abs(pa), 1e-300) and abs(db - da) <= 1e-9 * max(abs(da), 1e-300)
+    assert np.max(np.abs(vb - va)) <= 1e-6 * max(np.max(np.abs(va)), 1e-300)
+    a.close()
+    b.close()
 
 
 def test_vanna_device_entry_point_and_readings(lib):
