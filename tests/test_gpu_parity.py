@@ -235,13 +235,16 @@ def test_more_than_1024_level2_rows(lib):
     assert np.max(np.abs(v1 - v0)) <= 1e-6 * np.max(np.abs(v0))
 
 
-def test_path_range_sharding(lib):
+@pytest.mark.parametrize("ppl", [1, 2], ids=["one path per lane", "two paths per lane"])
+def test_path_range_sharding(ppl, lib):
     """Sums over [0, P/3), [P/3, P) add up to the sums over [0, P): the
-    path-range split a multi-GPU run would use."""
+    path-range split a multi-GPU run would use (a range that starts off a
+    tile boundary; each rank's range at the benchmark's size runs two paths
+    per lane)."""
     import torch
     surf, opt = W.config_paper_shape()
     P = 1 << 16
-    gs = G.make_surface(surf, opt, lib)
+    gs = G.make_surface(surf, opt, lib, ppl=ppl)
     n = 3 + surf.n_spot * surf.n_time
     whole = torch.zeros(n, dtype=torch.float64, device="cuda")
     a = torch.zeros(n, dtype=torch.float64, device="cuda")
