@@ -167,9 +167,9 @@ lv_status lv_set_launch(lv_surface_t h, int32_t block, int32_t k, int32_t blocks
  * binary32 arithmetic in packed pairs where that keeps the occupancy); 0 keeps
  * the tuned value, or the default: 2 for calls of at least 6,144 paths per SM
  * (933,888 on 152 SMs), where every warp still gets four pairs of tiles, else 1.
- * Two paths per lane exist for the main reading's reverse sweep with
- * checkpoints every 4 or 8 steps, its tangent-ratio adjoint and its
- * second-order buckets; elsewhere the call runs one. The results do not
+ * Two paths per lane exist for the reverse sweep with checkpoints every 4
+ * or 8 steps (every reading of the scheme), the main reading's tangent-ratio
+ * adjoint and its second-order buckets; elsewhere the call runs one. The results do not
  * depend on it beyond reduction-order rounding.
  * lv_get_paths_per_lane reads back the value the next call with n_steps steps
  * and n_paths >= 1 paths will use. */

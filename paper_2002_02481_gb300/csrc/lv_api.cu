@@ -248,10 +248,10 @@ lv_status choose_launch(lv_surface_s* h, int32_t n_steps, bool greeks, int* bloc
     if (dbg) *k = 4;
     const int model = (h->interp == LV_INTERP_LOGS ? 1 : 0) | (h->scheme == LV_SCHEME_S ? 2 : 0);
     if ((model != 0 || extra) && *k > lv::kModelMaxK) *k = lv::kModelMaxK;
-    // two paths per lane: the main reading's reverse sweep with checkpoints every 4 or 8 steps,
-    // its tangent-ratio adjoint and its second-order buckets (no checkpoints)
-    const bool pairs = greeks && !dbg && !extra && model == 0 &&
-                       (vanna || h->adj_method == LV_ADJ_TANGENT || *k == 4 || *k == 8);
+    // two paths per lane: the reverse sweep with checkpoints every 4 or 8 steps (every reading),
+    // the main reading's tangent-ratio adjoint and its second-order buckets (no checkpoints)
+    const bool pairs = greeks && !dbg && !extra &&
+                       ((vanna || h->adj_method == LV_ADJ_TANGENT) ? model == 0 : (*k == 4 || *k == 8));
     if (!pairs) ppl = 1;
     if (ppl_out) *ppl_out = ppl;
     const bool gs = lv::mc_smem_bytes(h->I, h->Je, n_steps, *block, greeks, true, extra, ppl) <= kGridSmemLimit;
@@ -875,7 +875,8 @@ lv_status lv_tune(lv_surface_t h, double S0, double r, double K, double T, int32
     const int ks[] = {4, 8, 16};
     const int keep_b = h->cfg_block, keep_k = h->cfg_k, keep_s = h->cfg_bps, keep_p = h->cfg_ppl;
     // two paths per lane exist for the main reading's reverse sweep at k = 4 and 8
-    const bool ppl2 = h->interp == LV_INTERP_S && h->scheme == LV_SCHEME_LOG;   // both adjoint methods
+    // the reverse sweep under every reading, the tangent-ratio adjoint under the main one
+    const bool ppl2 = h->adj_method == LV_ADJ_REVERSE || (h->interp == LV_INTERP_S && h->scheme == LV_SCHEME_LOG);
     cudaEvent_t e0, e1;
     LV_CUDA(cudaEventCreate(&e0));
     LV_CUDA(cudaEventCreate(&e1));

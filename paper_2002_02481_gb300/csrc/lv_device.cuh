@@ -103,15 +103,15 @@ __device__ __forceinline__ f32x2 pk2(float a, float b)
 
 __device__ __forceinline__ float lo2(f32x2 r)
 {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    float a;
+    asm("mov.b64 {%0, _}, %1;" : "=f"(a) : "l"(r));
     return a;
 }
 
 __device__ __forceinline__ float hi2(f32x2 r)
 {
-    float a, b;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    float b;
+    asm("mov.b64 {_, %0}, %1;" : "=f"(b) : "l"(r));
     return b;
 }
 

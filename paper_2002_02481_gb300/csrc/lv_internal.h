@@ -171,12 +171,12 @@ cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool 
 
 // The kernels of the other models (lv_model1.cu .. lv_model3.cu, one
 // translation unit each so that they compile in parallel); they exist for
-// checkpoint intervals k = 4 and 8.
+// checkpoint intervals k = 4 and 8, at one or two paths per lane.
 #define LV_DECLARE_MODEL(N)                                                                                \
     cudaError_t launch_mc_model##N(const McParams& p, int grid, int block, int k, bool greeks, size_t smem, \
                                    cudaStream_t s);                                                        \
     cudaError_t mc_occupancy_model##N(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem,    \
-                                      int method, bool extra, size_t smem, int* blocks_per_sm);
+                                      int method, bool extra, size_t smem, int* blocks_per_sm, int ppl);
 LV_DECLARE_MODEL(1)
 LV_DECLARE_MODEL(2)
 LV_DECLARE_MODEL(3)

@@ -125,12 +125,11 @@ cudaError_t launch_mc(const McParams& p, int grid, int block, int k, bool greeks
 cudaError_t mc_occupancy(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method, int model,
                          bool extra, size_t smem, int* bps, int ppl)
 {
-    if (model != 0 && ppl != 1) return cudaErrorInvalidValue;
     switch (model) {
     case 0: return occupancy_model_impl<0>(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps, ppl);
-    case 1: return mc_occupancy_model1(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
-    case 2: return mc_occupancy_model2(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
-    case 3: return mc_occupancy_model3(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
+    case 1: return mc_occupancy_model1(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps, ppl);
+    case 2: return mc_occupancy_model2(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps, ppl);
+    case 3: return mc_occupancy_model3(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps, ppl);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -726,23 +726,24 @@ cudaError_t occupancy(K kernel, int block, size_t smem, int* bps)
 template <int MODEL, bool GS, typename F>
 cudaError_t with_kernel_gs(bool greeks, int k, int acc, bool dbg, int method, bool extra, F&& f, int ppl = 1)
 {
-    if (ppl == 2) {        // two paths per lane: the main reading's reverse sweep (k = 4 or 8),
-        if constexpr (MODEL == 0) {    // tangent-ratio adjoint and second-order buckets
-            static bool cp[4] = {};
+    if (ppl == 2) {        // two paths per lane: the reverse sweep (k = 4 or 8) of every reading,
+                           // the main reading's tangent-ratio adjoint and second-order buckets
+        if (!greeks || dbg || extra) return cudaErrorInvalidValue;
+        if constexpr (MODEL == 0) {
             static bool cv2 = false, ct2[2] = {};
-            if (!greeks || dbg || extra) return cudaErrorInvalidValue;
             if (method == kMethodVanna)
                 return acc == 0 ? f(vanna_kernel<GS, 2>, cv2) : cudaErrorInvalidValue;
             if (method == LV_ADJ_TANGENT)
                 return acc ? f(tangent_kernel<1, GS, 0, 2>, ct2[1]) : f(tangent_kernel<0, GS, 0, 2>, ct2[0]);
-            if (method != LV_ADJ_REVERSE) return cudaErrorInvalidValue;
-            switch (k * 2 + acc) {
-            case 8: return f(adjoint_kernel<4, 0, false, GS, 0, false, 2>, cp[0]);
-            case 9: return f(adjoint_kernel<4, 1, false, GS, 0, false, 2>, cp[1]);
-            case 16: return f(adjoint_kernel<8, 0, false, GS, 0, false, 2>, cp[2]);
-            case 17: return f(adjoint_kernel<8, 1, false, GS, 0, false, 2>, cp[3]);
-            default: break;
-            }
+        }
+        if (method != LV_ADJ_REVERSE) return cudaErrorInvalidValue;
+        static bool cp[4] = {};
+        switch (k * 2 + acc) {
+        case 8: return f(adjoint_kernel<4, 0, false, GS, MODEL, false, 2>, cp[0]);
+        case 9: return f(adjoint_kernel<4, 1, false, GS, MODEL, false, 2>, cp[1]);
+        case 16: return f(adjoint_kernel<8, 0, false, GS, MODEL, false, 2>, cp[2]);
+        case 17: return f(adjoint_kernel<8, 1, false, GS, MODEL, false, 2>, cp[3]);
+        default: break;
         }
         return cudaErrorInvalidValue;
     }

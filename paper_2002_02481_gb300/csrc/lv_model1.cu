@@ -12,9 +12,9 @@ cudaError_t launch_mc_model1(const McParams& p, int grid, int block, int k, bool
 }
 
 cudaError_t mc_occupancy_model1(int block, int k, bool greeks, int acc, bool dbg, bool grid_smem, int method,
-                                 bool extra, size_t smem, int* bps)
+                                 bool extra, size_t smem, int* bps, int ppl)
 {
-    return occupancy_model_impl<1>(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps);
+    return occupancy_model_impl<1>(block, k, greeks, acc, dbg, grid_smem, method, extra, smem, bps, ppl);
 }
 
 }  // namespace lv

@@ -171,10 +171,12 @@ def test_two_paths_per_lane_equals_one(lib):
     assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 2
     assert b.get_paths_per_lane(opt.n_steps, 1 << 12) == 1
     b.set_launch(128, 16, 0)
-    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 1
+    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 1       # checkpoints every 16 steps: one
     b.set_launch(128, 4, 0)
     b.set_scheme(lv.LV_SCHEME_S)
-    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 1
+    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 2       # every reading's reverse sweep
+    b.set_adjoint_method(lv.LV_ADJ_TANGENT)
+    assert b.get_paths_per_lane(opt.n_steps, 1 << 22) == 1       # the main reading's tangent ratio only
     with pytest.raises(lv.LVError):
         b.get_paths_per_lane(opt.n_steps, 0)
     with pytest.raises(lv.LVError):

@@ -70,6 +70,37 @@ def test_tangent_ratio_and_kahan(reading, lib):
     G.full_parity(s, o, lib, label=f"{tag} Kahan", accumulation=1, launch=(128, 8, 0))
 
 
+@pytest.mark.parametrize("reading", READINGS, ids=[r[2] for r in READINGS])
+def test_two_paths_per_lane(reading, lib):
+    """Two paths per lane in the forward tiles under every reading (scalar
+    pairs: the packed form is the main reading's): the oracle path for path
+    at k = 4 (binary64) and k = 8 (Kahan), on the paper's grid, an uneven
+    grid with a put and a ragged tile; and the same results as one path per
+    lane up to reduction order."""
+    interp, scheme, tag = reading
+    surf, opt = W.config_paper_shape()
+    opt = W.Option(**{**opt.__dict__, "n_paths": 1 << 17})
+    s, o = _with(surf, opt, interp, scheme)
+    for launch, acc in [((128, 4, 0), 0), ((128, 8, 0), 1)]:
+        g = G.make_surface(s, o, lib, launch=launch, accumulation=acc, ppl=2)
+        assert g.get_paths_per_lane(o.n_steps, o.n_paths) == 2
+        g.close()
+        _report(f"{tag}: two paths per lane {launch} acc={acc}",
+                G.full_parity(s, o, lib, launch=launch, accumulation=acc, ppl=2, label=f"{tag} ppl2"))
+    for name, es, eo in (EDGE[2], EDGE[5]):
+        s2, o2 = _with(es, eo, interp, scheme)
+        G.full_parity(s2, o2, lib, launch=(128, 4, 0), ppl=2, label=f"{tag} ppl2: {name}")
+    a = G.make_surface(s, o, lib, launch=(128, 4, 0), ppl=1)
+    b = G.make_surface(s, o, lib, launch=(128, 4, 0), ppl=2)
+    args = (o.S0, o.r, o.K, o.T, o.n_steps, o.n_paths, o.seed)
+    pa, da, va = a.price_greeks(*args)
+    pb, db, vb = b.price_greeks(*args)
+    assert abs(pb - pa) <= 1e-12 * abs(pa) and abs(db - da) <= 1e-9 * abs(da)
+    assert np.max(np.abs(vb - va)) <= 1e-6 * np.max(np.abs(va))
+    a.close()
+    b.close()
+
+
 def test_large_k_is_capped_and_the_bump_and_book_refuse(lib):
     surf, opt = W.config_small()
     s = lv.Surface.from_workload(surf, lib)
