@@ -461,8 +461,8 @@ __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid&
 // independent dependency chains; each path's arithmetic is exactly that of
 // forward_path (its checkpoints and terminal state are bit-identical), and
 // the per-step time data is loaded once for both. Path b is logged only
-// when log_b (it may lie past the end of the call's range). With PACK (main
-// reading, no logging) the two paths' binary32 arithmetic runs in packed
+// when log_b (it may lie past the end of the call's range). With PACK (the
+// log-Euler readings, no logging) the two paths' binary32 arithmetic runs in packed
 // pairs: the Box-Muller products and shifts, the spot-cell index, the time
 // blend of sigma and the whole log-Euler step; the loads and the
 // transcendental unit stay per path. The Euler step uses
@@ -474,7 +474,7 @@ __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid&
                                               float& yb_out)
 {
     const int nseg = (P.N + KCK - 1) / KCK;
-    if constexpr (PACK && MODEL == 0 && !DBG) {
+    if constexpr (PACK && (MODEL & kModelEulerS) == 0 && !DBG) {   // log-Euler readings
         const f32x2 csc = pk2(P.cell_scale, P.cell_scale), csh = pk2(P.cell_shift, P.cell_shift);
         const f32x2 nsq = pk2(-P.sqdt2, -P.sqdt2), nhdt = pk2(-P.hdt, -P.hdt), rdt = pk2(P.rdt, P.rdt);
         f32x2 y = pk2(P.x0, P.x0);
@@ -503,8 +503,9 @@ __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid&
                         ib = spot_cell(P, g, hi2(y), Sb);
                     }
                     const float2 aba = g.ab[ia], abb = g.ab[ib];
-                    const float ua = __saturatef(fmaf(Sa, aba.x, aba.y));
-                    const float ub = __saturatef(fmaf(Sb, abb.x, abb.y));
+                    // the spot weight is linear in S, or in y = log2 S under the ln-S weight
+                    const float ua = __saturatef(fmaf((MODEL & kModelLogWeight) ? lo2(y) : Sa, aba.x, aba.y));
+                    const float ub = __saturatef(fmaf((MODEL & kModelLogWeight) ? hi2(y) : Sb, abb.x, abb.y));
                     const float2 loa = g.sig2[tb.x + ia], hia = g.sig2[tb.y + ia];
                     const float2 lob = g.sig2[tb.x + ib], hib = g.sig2[tb.y + ib];
                     const f32x2 top = pk2(fmaf(ua, loa.y, loa.x), fmaf(ub, lob.y, lob.x));
@@ -571,7 +572,7 @@ __device__ __forceinline__ void path_counter(const McParams& P, long long rel, u
 // (i+1, j+1) with the bilinear weights. Corner sums are kept in registers
 // while the cell is unchanged and then added to the block's binary32 buckets
 // `l1` (time-major, row j * I) with red.global.add.f32. Returns d V / d x_0.
-// With NEG (main reading, no extra sums) the recompute takes its normals from
+// With NEG (log-Euler readings, no extra sums) the recompute takes its normals from
 // normals4_neg and uses sqdt Z = (-sqdt)(-Z) and sqdt2 Z = (-sqdt2)(-Z),
 // which are exact, so every value is the same bit for bit.
 template <int KCK, int MODEL = 0, bool EXTRA = false, bool NEG = false>
@@ -594,7 +595,7 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
         for (int q = 0; q < KCK; ++q) {
             const int n = m * KCK + q;
             if (n < P.N) {
-                constexpr bool kNeg = NEG && MODEL == 0 && !EXTRA;
+                constexpr bool kNeg = NEG && (MODEL & kModelEulerS) == 0 && !EXTRA;
                 if ((q & 3) == 0) {
                     if (kNeg) normals4_neg((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
                     else normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);

@@ -8,7 +8,9 @@ So the price of a packed kernel (two paths per lane) agreeing with the scalar
 kernel's (one path per lane) to 1e-13 on the same paths checks each path.
 Kernels compared: the forward-only kernel (always packed) and the adjoint at
 two paths per lane (packed forward and paired reverse normals) against the
-adjoint at one path per lane; the tangent-ratio adjoint at two against one."""
+adjoint at one path per lane, under the main reading and under the spot
+weight linear in ln S; the tangent-ratio adjoint (main reading) at two
+against one."""
 import pytest
 
 import workloads as W
@@ -37,25 +39,30 @@ def lib():
     return lv.load()
 
 
+@pytest.mark.parametrize("interp", [lv.LV_INTERP_S, lv.LV_INTERP_LOGS], ids=["weight in S", "weight in ln S"])
 @pytest.mark.parametrize("n_paths", [1, 33, 64, 97, 256])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_packed_pairs_match_scalar_paths(case, n_paths, lib):
+def test_packed_pairs_match_scalar_paths(case, n_paths, interp, lib):
     name, (surf, opt) = case
     opt = W.Option(**{**opt.__dict__, "n_paths": n_paths})
     args = (opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
     one = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=1)
     two = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=2)
+    for s in (one, two):
+        s.set_interpolation(interp)
     p1, _, _ = one.price_greeks(*args)
     p2, _, _ = two.price_greeks(*args)
     pf, _ = two.price(*args)
-    for s in (one, two):
-        s.set_adjoint_method(lv.LV_ADJ_TANGENT)
-    t1, _, _ = one.price_greeks(*args)
-    t2, _, _ = two.price_greeks(*args)
+    got = [("adjoint, two paths per lane", p2), ("forward only", pf)]
+    if interp == lv.LV_INTERP_S:               # the tangent-ratio form pairs the main reading
+        for s in (one, two):
+            s.set_adjoint_method(lv.LV_ADJ_TANGENT)
+        t1, _, _ = one.price_greeks(*args)
+        t2, _, _ = two.price_greeks(*args)
+        got += [("tangent ratio, one path per lane", t1), ("tangent ratio, two paths per lane", t2)]
     assert two.get_paths_per_lane(opt.n_steps, opt.n_paths) == 2
     one.close()
     two.close()
     scale = max(abs(p1), 1e-300)
-    for label, p in (("adjoint, two paths per lane", p2), ("forward only", pf),
-                     ("tangent ratio, one path per lane", t1), ("tangent ratio, two paths per lane", t2)):
+    for label, p in got:
         assert abs(p - p1) <= TOL * scale, (name, n_paths, label, p, p1)

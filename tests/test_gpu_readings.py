@@ -72,8 +72,8 @@ def test_tangent_ratio_and_kahan(reading, lib):
 
 @pytest.mark.parametrize("reading", READINGS, ids=[r[2] for r in READINGS])
 def test_two_paths_per_lane(reading, lib):
-    """Two paths per lane in the forward tiles under every reading (scalar
-    pairs: the packed form is the main reading's): the oracle path for path
+    """Two paths per lane in the forward tiles under every reading (packed
+    pairs under the ln-S weight, scalar pairs for Euler on S): the oracle path for path
     at k = 4 (binary64) and k = 8 (Kahan), on the paper's grid, an uneven
     grid with a put and a ragged tile; and the same results as one path per
     lane up to reduction order."""
