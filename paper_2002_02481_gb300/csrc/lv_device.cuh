@@ -461,12 +461,12 @@ __device__ __forceinline__ float forward_path(const McParams& P, const SmemGrid&
 // independent dependency chains; each path's arithmetic is exactly that of
 // forward_path (its checkpoints and terminal state are bit-identical), and
 // the per-step time data is loaded once for both. Path b is logged only
-// when log_b (it may lie past the end of the call's range). With PACK (the
-// log-Euler readings, no logging) the two paths' binary32 arithmetic runs in packed
+// when log_b (it may lie past the end of the call's range). With PACK (every
+// reading, no logging) the two paths' binary32 arithmetic runs in packed
 // pairs: the Box-Muller products and shifts, the spot-cell index, the time
-// blend of sigma and the whole log-Euler step; the loads and the
-// transcendental unit stay per path. The Euler step uses
-// sqdt2 Z = (-sqdt2)(-Z), exact, so the negated normals need no sign flip.
+// blend of sigma and the whole Euler step (on y = log2 S or on S); the loads
+// and the transcendental unit stay per path. The step uses sqdt2 Z =
+// (-sqdt2)(-Z) (sqdt Z on S), exact, so the negated normals need no sign flip.
 template <int KCK, bool STORE, bool DBG, int MODEL = 0, bool PACK = false>
 __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid& g, uint32_t c1a, uint32_t c2a,
                                               uint32_t c1b, uint32_t c2b, float* cka, float* ckb, size_t cks,
@@ -474,15 +474,18 @@ __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid&
                                               float& yb_out)
 {
     const int nseg = (P.N + KCK - 1) / KCK;
-    if constexpr (PACK && (MODEL & kModelEulerS) == 0 && !DBG) {   // log-Euler readings
+    if constexpr (PACK && !DBG) {
+        // the path state x is y = log2 S (log-Euler) or S (Euler on S)
+        constexpr bool kOnS = (MODEL & kModelEulerS) != 0, kLnW = (MODEL & kModelLogWeight) != 0;
         const f32x2 csc = pk2(P.cell_scale, P.cell_scale), csh = pk2(P.cell_shift, P.cell_shift);
         const f32x2 nsq = pk2(-P.sqdt2, -P.sqdt2), nhdt = pk2(-P.hdt, -P.hdt), rdt = pk2(P.rdt, P.rdt);
-        f32x2 y = pk2(P.x0, P.x0);
+        const f32x2 nsqdt = pk2(-P.sqdt, -P.sqdt);
+        f32x2 x = pk2(P.x0, P.x0);
         f32x2 nz[4];
         for (int m = 0; m < nseg; ++m) {
             if (STORE) {
-                cka[(size_t)m * cks] = lo2(y);
-                ckb[(size_t)m * cks] = hi2(y);
+                cka[(size_t)m * cks] = lo2(x);
+                ckb[(size_t)m * cks] = hi2(x);
             }
 #pragma unroll
             for (int q = 0; q < KCK; ++q) {
@@ -491,8 +494,18 @@ __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid&
                     if ((q & 3) == 0) normals4x2_neg((uint32_t)(n >> 2), c1a, c2a, c1b, c2b, P.k0, P.k1, nz);
                     const int4 tb = g.tab[n];
                     const float v = __int_as_float(tb.w);
-                    // eval_sigma<false, 0> for both paths
-                    const float Sa = ex2_approx(lo2(y)), Sb = ex2_approx(hi2(y));
+                    // eval_sigma<false, MODEL> for both paths
+                    float Sa, Sb;
+                    f32x2 y;
+                    if (kOnS) {
+                        Sa = lo2(x);
+                        Sb = hi2(x);
+                        y = pk2(lg2_approx(fmaxf(Sa, 1e-30f)), lg2_approx(fmaxf(Sb, 1e-30f)));
+                    } else {
+                        y = x;
+                        Sa = ex2_approx(lo2(y));
+                        Sb = ex2_approx(hi2(y));
+                    }
                     int ia, ib;
                     if (P.log_uniform) {
                         const f32x2 ci = fma2(y, csc, csh);
@@ -504,22 +517,26 @@ __device__ __forceinline__ void forward_path2(const McParams& P, const SmemGrid&
                     }
                     const float2 aba = g.ab[ia], abb = g.ab[ib];
                     // the spot weight is linear in S, or in y = log2 S under the ln-S weight
-                    const float ua = __saturatef(fmaf((MODEL & kModelLogWeight) ? lo2(y) : Sa, aba.x, aba.y));
-                    const float ub = __saturatef(fmaf((MODEL & kModelLogWeight) ? hi2(y) : Sb, abb.x, abb.y));
+                    const float ua = __saturatef(fmaf(kLnW ? lo2(y) : Sa, aba.x, aba.y));
+                    const float ub = __saturatef(fmaf(kLnW ? hi2(y) : Sb, abb.x, abb.y));
                     const float2 loa = g.sig2[tb.x + ia], hia = g.sig2[tb.y + ia];
                     const float2 lob = g.sig2[tb.x + ib], hib = g.sig2[tb.y + ib];
                     const f32x2 top = pk2(fmaf(ua, loa.y, loa.x), fmaf(ub, lob.y, lob.x));
                     const f32x2 bot = pk2(fmaf(ua, hia.y, hia.x), fmaf(ub, hib.y, hib.x));
                     const f32x2 sig = fma2(pk2(v, v), sub2(bot, top), top);
-                    // euler_step for both paths
-                    const f32x2 t1 = mul2(nsq, nz[q & 3]);
-                    const f32x2 t3 = fma2(mul2(nhdt, sig), sig, rdt);
-                    y = add2(y, fma2(sig, t1, t3));
+                    if (kOnS) {
+                        // step_state: S (1 + r dt + sigma sqrt(dt) Z), sqrt(dt) Z = (-sqrt(dt))(-Z)
+                        x = fma2(x, fma2(sig, mul2(nsqdt, nz[q & 3]), rdt), x);
+                    } else {
+                        // euler_step: y + fma(sigma, sqdt2 Z, fma(-hdt sigma, sigma, rdt))
+                        const f32x2 t3 = fma2(mul2(nhdt, sig), sig, rdt);
+                        x = add2(x, fma2(sig, mul2(nsq, nz[q & 3]), t3));
+                    }
                 }
             }
         }
-        ya_out = lo2(y);
-        yb_out = hi2(y);
+        ya_out = lo2(x);
+        yb_out = hi2(x);
         return;
     }
     float ya = P.x0, yb = P.x0;
@@ -572,7 +589,7 @@ __device__ __forceinline__ void path_counter(const McParams& P, long long rel, u
 // (i+1, j+1) with the bilinear weights. Corner sums are kept in registers
 // while the cell is unchanged and then added to the block's binary32 buckets
 // `l1` (time-major, row j * I) with red.global.add.f32. Returns d V / d x_0.
-// With NEG (log-Euler readings, no extra sums) the recompute takes its normals from
+// With NEG (no extra sums) the recompute takes its normals from
 // normals4_neg and uses sqdt Z = (-sqdt)(-Z) and sqdt2 Z = (-sqdt2)(-Z),
 // which are exact, so every value is the same bit for bit.
 template <int KCK, int MODEL = 0, bool EXTRA = false, bool NEG = false>
@@ -595,23 +612,30 @@ __device__ __forceinline__ float reverse_path(const McParams& P, const SmemGrid&
         for (int q = 0; q < KCK; ++q) {
             const int n = m * KCK + q;
             if (n < P.N) {
-                constexpr bool kNeg = NEG && (MODEL & kModelEulerS) == 0 && !EXTRA;
+                constexpr bool kNeg = NEG && !EXTRA;
                 if ((q & 3) == 0) {
                     if (kNeg) normals4_neg((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
                     else normals4((uint32_t)(n >> 2), c1, c2, P.k0, P.k1, z);
                 }
                 const int4 tb = g.tab[n];
                 const StepEval ev = eval_sigma<true, MODEL>(P, g, x, tb);
-                if (kNeg) {                    // z holds -Z
-                    hq[q] = fmaf(-P.sqdt, z[q & 3], -ev.sigma * P.dt);
-                    gq[q] = hq[q] * ev.sslope;
+                if (kNeg) {                    // z holds -Z: adjoint_factors with sqrt(dt) Z = (-sqrt(dt))(-Z)
+                    if (MODEL & kModelEulerS) {
+                        const float w = -P.sqdt * z[q & 3];
+                        hq[q] = ev.S * P.inv_S0 * w;
+                        gq[q] = fmaf(w, ev.sigma + ev.sslope, P.rdt);
+                    } else {
+                        hq[q] = fmaf(-P.sqdt, z[q & 3], -ev.sigma * P.dt);
+                        gq[q] = hq[q] * ev.sslope;
+                    }
                 } else {
                     adjoint_factors<MODEL>(P, ev, z[q & 3], hq[q], gq[q]);
                 }
                 if (EXTRA) extra_factors<MODEL>(P, ev, z[q & 3], hq[q], g.tdt[n], aq[EXTRA ? q : 0], tq[EXTRA ? q : 0]);
                 uq[q] = ev.u;
                 iq[q] = ev.i;
-                if (kNeg) x = x + fmaf(ev.sigma, -P.sqdt2 * z[q & 3], fmaf(-P.hdt * ev.sigma, ev.sigma, P.rdt));
+                if (kNeg && (MODEL & kModelEulerS)) x = fmaf(x, fmaf(ev.sigma, -P.sqdt * z[q & 3], P.rdt), x);
+                else if (kNeg) x = x + fmaf(ev.sigma, -P.sqdt2 * z[q & 3], fmaf(-P.hdt * ev.sigma, ev.sigma, P.rdt));
                 else x = step_state<MODEL>(P, x, ev.sigma, z[q & 3]);
             }
         }

@@ -268,7 +268,8 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 uint32_t c1, c2;
                 path_counter(P, rel, c1, c2);
                 float ra = 0.0f, ta = 0.0f;
-                xbar = reverse_path<KCK, MODEL, EXTRA, PPL == 2>(P, g, c1, c2, ckw + slot, cks, xbar, l1, &ra, &ta);
+                xbar = reverse_path<KCK, MODEL, EXTRA, PPL == 2 && (MODEL & kModelEulerS) == 0>(
+                    P, g, c1, c2, ckw + slot, cks, xbar, l1, &ra, &ta);
                 acc_add<ACC>(acc[2 * B], xbar);
                 if (EXTRA) {
                     acc_add<ACC>(acc[3 * B], ra);
@@ -296,8 +297,10 @@ __global__ void __launch_bounds__(128, 5) adjoint_kernel(const __grid_constant__
                 path_counter(P, rel_a, c1a, c2a);
                 path_counter(P, rel_b, c1b, c2b);
                 float ya, yb;
-                forward_path2<KCK, true, false, MODEL, true>(P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b,
-                                                             cks, rel_a, rel_b, false, ya, yb);
+                // packed pairs on the log-Euler readings; Euler on S keeps scalar pairs in
+                // this kernel (packed, it needs 82 registers: 5 blocks per SM instead of 6)
+                forward_path2<KCK, true, false, MODEL, (MODEL & kModelEulerS) == 0>(
+                    P, g, c1a, c2a, c1b, c2b, ckw + slot_a, ckw + slot_b, cks, rel_a, rel_b, false, ya, yb);
                 float V;
                 payoff<MODEL>(P, ya, V, xa);
                 acc_add<ACC>(acc[0], V);

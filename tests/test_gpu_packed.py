@@ -8,9 +8,10 @@ So the price of a packed kernel (two paths per lane) agreeing with the scalar
 kernel's (one path per lane) to 1e-13 on the same paths checks each path.
 Kernels compared: the forward-only kernel (always packed) and the adjoint at
 two paths per lane (packed forward and paired reverse normals) against the
-adjoint at one path per lane, under the main reading and under the spot
-weight linear in ln S; the tangent-ratio adjoint (main reading) at two
-against one."""
+adjoint at one path per lane, under every reading of the scheme (the
+adjoint packs under the log-Euler readings and keeps scalar pairs for Euler
+on S, whose forward-only kernel packs); the tangent-ratio adjoint (main
+reading) at two against one."""
 import pytest
 
 import workloads as W
@@ -39,10 +40,15 @@ def lib():
     return lv.load()
 
 
-@pytest.mark.parametrize("interp", [lv.LV_INTERP_S, lv.LV_INTERP_LOGS], ids=["weight in S", "weight in ln S"])
+READINGS = [(lv.LV_INTERP_S, lv.LV_SCHEME_LOG, "main reading"), (lv.LV_INTERP_LOGS, lv.LV_SCHEME_LOG, "ln-S weight"),
+            (lv.LV_INTERP_S, lv.LV_SCHEME_S, "Euler on S"), (lv.LV_INTERP_LOGS, lv.LV_SCHEME_S, "both")]
+
+
+@pytest.mark.parametrize("reading", READINGS, ids=[r[2] for r in READINGS])
 @pytest.mark.parametrize("n_paths", [1, 33, 64, 97, 256])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_packed_pairs_match_scalar_paths(case, n_paths, interp, lib):
+def test_packed_pairs_match_scalar_paths(case, n_paths, reading, lib):
+    interp, scheme, _ = reading
     name, (surf, opt) = case
     opt = W.Option(**{**opt.__dict__, "n_paths": n_paths})
     args = (opt.S0, opt.r, opt.K, opt.T, opt.n_steps, opt.n_paths, opt.seed)
@@ -50,11 +56,12 @@ def test_packed_pairs_match_scalar_paths(case, n_paths, interp, lib):
     two = G.make_surface(surf, opt, lib, launch=(128, 4, 0), ppl=2)
     for s in (one, two):
         s.set_interpolation(interp)
+        s.set_scheme(scheme)
     p1, _, _ = one.price_greeks(*args)
     p2, _, _ = two.price_greeks(*args)
     pf, _ = two.price(*args)
     got = [("adjoint, two paths per lane", p2), ("forward only", pf)]
-    if interp == lv.LV_INTERP_S:               # the tangent-ratio form pairs the main reading
+    if reading[2] == "main reading":           # the tangent-ratio form pairs the main reading
         for s in (one, two):
             s.set_adjoint_method(lv.LV_ADJ_TANGENT)
         t1, _, _ = one.price_greeks(*args)
