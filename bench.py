@@ -779,12 +779,14 @@ def path_sweep():
     return 0
 
 
-def only(which: str, launch: str, reps: int):
+def only(which: str, launch: str, reps: int, paths: int = 0):
     """One workload alone at a fixed shape (for profiling and quick timing):
     'book' (8 x 64 options, per-option outputs, graph replay), 'vanna' (the
     second-order buckets on the bench workload), 'large' (100 x 100, 1,260
     steps, 2^26 paths) or 'fp64' (the binary64 reference run, 2^20 paths).
-    Prints one JSON line with the kernel (or replay) times."""
+    `paths` > 0 replaces the workload's path count (a smaller case of the same
+    kernel for profiling). Prints one JSON line with the kernel (or replay)
+    times."""
     import torch
 
     from paper_2002_02481_gb300 import lv
@@ -796,7 +798,7 @@ def only(which: str, launch: str, reps: int):
     ev1.record(stream)
     torch.cuda.synchronize()
     vals = [int(v) for v in launch.split(",")] if launch else []
-    out = {"only": which, "launch": vals, "ms": []}
+    out = {"only": which, "launch": vals, "paths": paths or None, "ms": []}
     if which == "book":
         handles = [lv.Surface.from_workload(sf, lib) for sf in W.book_surfaces()]
         book = lv.Book(handles, W.book_items(), lib)
@@ -812,6 +814,8 @@ def only(which: str, launch: str, reps: int):
         book.close()
     else:
         surf, opt = W.config_large() if which == "large" else W.config_paper_shape()
+        if paths > 0:
+            opt = W.Option(**{**opt.__dict__, "n_paths": paths})
         S = lv.Surface.from_workload(surf, lib)
         S.set_stream(stream.cuda_stream)
         if vals:
@@ -841,6 +845,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 100x100 / 1260-step / 2^26-path record")
     ap.add_argument("--only", default="", choices=["", "book", "vanna", "large", "fp64"],
                     help="time one workload alone at a fixed shape (for profiling)")
+    ap.add_argument("--paths", type=int, default=0, help="with --only: the path count (profiling a smaller case)")
     ap.add_argument("--launch", default="",
                     help="fix the adjoint's launch shape as BLOCK,K[,PATHS_PER_LANE] instead of tuning it")
     ap.add_argument("--precision-study", action="store_true",
@@ -855,7 +860,7 @@ def main():
     if args.path_sweep:
         return path_sweep()
     if args.only:
-        return only(args.only, args.launch, max(1, args.steps))
+        return only(args.only, args.launch, max(1, args.steps), args.paths)
     return run_ours(args)
 
 
